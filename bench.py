@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Benchmark of the MPM hot path on one B300 (or N, as independent replicas).
+
+Workload (default): 3D blast wave, 256^3 cells on the unit cube, 2x2x2
+particles per cell (134,217,728 particles), quadratic B-splines, FP32, slip
+walls, CFL 0.3 -- the configuration on which the HBM-roofline target is set.
+
+A step is one pass of the whole hot path: P2G, grid update + G2P + P2G,
+G2PD + particle update + move, time advance and the stable re-order.  The
+metric is particle-steps per second.  Inputs are resident in HBM when the
+timed region starts (particle state ~13 GB, far larger than the 126 MB L2,
+so no L2 flush is needed between steps).  Per-phase device times come from
+CUDA events that the library records on its own stream; the clocks are
+sampled with nvidia-smi during the timed region.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--config blast|cylinder]
+python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+Under torchrun each rank runs its own independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6400.0
+NOMINAL_HBM = 7700.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--config", default="blast", choices=["blast", "cylinder"])
+    ap.add_argument("--n", type=int, default=0, help="override the grid size (cells per axis / x cells)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_fixed64", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def problem(args):
+    from paper_2404_17057_b300 import inputs as I
+    if args.config == "blast":
+        n = args.n or 256
+        p = I.blast(n=n, precision=args.precision)
+        wl = f"3D blast wave {n}^3 cells, 8 ppc, quadratic B-spline, {args.precision}"
+        cfg = {"workload": wl, "cells": [n, n, n], "particles": p.n_particles, "degree": 2,
+               "precision": args.precision, "l2": "inputs larger than L2 (no flush)"}
+    else:
+        nx = args.n or 1024
+        p = I.cylinder(nx=nx, ny=nx // 2, precision=args.precision)
+        wl = f"2D Mach-3 cylinder {nx}x{nx // 2} cells, 4 ppc, quadratic B-spline, {args.precision}"
+        cfg = {"workload": wl, "cells": [nx, nx // 2], "particles": p.n_particles, "degree": 2,
+               "precision": args.precision, "l2": "particle state partly L2-resident"}
+    return p, cfg
+
+
+def algorithmic_bytes(dim, s, n_p, n_n):
+    """Bytes each kernel must move at minimum (one read/write per word).
+    K1 P2G: particles read x,v,M,rho,e,q (2d+4 words); nodes written m,mv,f (2d+1).
+    K2 grid+G2P+P2G: particles read x,v,M (2d+1), write v (d); nodes read m,f (1+d), write mv2 (d).
+    K3 G2PD+update: particles read x,rho,e,q (d+3), write x,rho,e,q (d+3) and a 4-byte key;
+                    nodes read m,mv,f,mv2 (1+3d).
+    zeroing: nodes written (1+3d)."""
+    k1 = n_p * (2 * dim + 4) * s + n_n * (2 * dim + 1) * s
+    k2 = n_p * (3 * dim + 1) * s + n_n * (1 + 2 * dim) * s
+    k3 = n_p * ((2 * dim + 6) * s + 4) + n_n * (1 + 3 * dim) * s
+    zero = n_n * (1 + 3 * dim) * s
+    return {"p2g": k1 + zero, "grid_g2p": k2, "g2pd": k3}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
+        try:
+            sm = [float(r[1]) for r in self.rows if len(r) >= 9]
+            if sm:
+                out["sm_mhz"] = float(np.median(sm))
+                out["sm_max_mhz"] = float(self.rows[0][2])
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for i, nme in enumerate(names):
+                if any(len(r) >= 9 and r[5 + i].lower() == "active" for r in self.rows):
+                    out["reasons"].append(nme)
+        except Exception:
+            pass
+        return out
+
+
+def peaks():
+    try:
+        d = json.load(open(PEAKS))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def cpu_baseline(args, cfg_meta, seconds_budget=20.0):
+    """The FP64 oracle as it stands, on the host, on a bounded sample of the
+    same workload (a smaller grid of the same problem, a few steps)."""
+    from oracle import oracle as O
+    from paper_2404_17057_b300 import inputs as I
+    if args.config == "blast":
+        n = 32
+        p = I.blast(n=n, precision="fp64")
+        sample = f"blast {n}^3 cells (8 ppc, {p.n_particles} particles), same ppc/basis, FP64 oracle"
+    else:
+        n = 128
+        p = I.cylinder(nx=n, ny=n // 2, precision="fp64")
+        sample = f"cylinder {n}x{n // 2} cells ({p.n_particles} particles), FP64 oracle"
+    s = O.OracleSim(p.cfg)
+    s.add_particles(p.x, p.v, p.mass, p.rho, p.e)
+    if p.mask is not None:
+        s.set_obstacle_mask(p.mask, p.normals)
+    s.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        s.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds_budget or steps >= 200:
+            break
+    rate = p.n_particles * steps / el
+    return {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample}, {steps} steps in {el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    _, meta = problem_meta_only(args)
+    cb = cpu_baseline(args, meta, seconds_budget=max(5.0, min(60.0, 3.0 * (args.steps + args.warmup))))
+    line = {"impl": "reference", "metric": "particle-steps/s", "value": cb["value"], "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": meta, "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def problem_meta_only(args):
+    if args.config == "blast":
+        n = args.n or 256
+        return None, {"workload": f"3D blast wave {n}^3 cells, 8 ppc, quadratic B-spline, {args.precision}",
+                      "cells": [n, n, n], "particles": 8 * n ** 3}
+    nx = args.n or 1024
+    return None, {"workload": f"2D Mach-3 cylinder {nx}x{nx // 2} cells, 4 ppc, quadratic B-spline",
+                  "cells": [nx, nx // 2]}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2404_17057_b300 import build as B, mpm as M
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    B.build()
+    p, meta = problem(args)
+    n_p = p.n_particles
+
+    sim = M.Simulation.from_problem(p)
+    st = torch.cuda.ExternalStream(sim.stream)
+    sim.step(args.warmup)
+    sim.profile(True)
+    sim.profile_read(reset=True)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    sim.step_async(args.steps)
+    e1.record(st)
+    sim.sync()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    phase_ms, counts = sim.profile_read(reset=True)
+    sizes = sim.sizes()
+    n_n = sizes["nodes"]
+    value = n_p * args.steps * world / (ms / 1e3)
+
+    dim = p.cfg["dim"]
+    s = 8 if args.precision == "fp64" else 4
+    alg = algorithmic_bytes(dim, s, n_p, n_n)
+    names = ["p2g", "grid_g2p", "g2pd"]
+    per_launch_ms = {nme: phase_ms[i] / args.steps for i, nme in enumerate(names)}
+    dom = max(names, key=lambda k: per_launch_ms[k])
+    hbm, which = peaks()
+    ach = alg[dom] / (per_launch_ms[dom] / 1e3) / 1e9
+    k123_ms = sum(per_launch_ms.values())
+    k123_gbs = sum(alg.values()) / (k123_ms / 1e3) / 1e9
+    launches_per_step = int(counts[0] + counts[1] + counts[2] + counts[3] + counts[4] + 1)
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = end_to_end(M, p, args)
+    sim.close()
+
+    if rank != 0:
+        return
+    cb = None if args.no_cpu else cpu_baseline(args, meta)
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp32_fixed64": "f32+i64",
+                                                           "fp64": "f64"}[args.precision],
+        "data": "synthetic", "config": meta,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                     "frac": ach / hbm, "peak_source": which, "traffic": None,
+                     "k1_k2_k3_gbs": k123_gbs, "k1_k2_k3_frac": k123_gbs / hbm,
+                     "k1_k2_k3_frac_nominal_7.7TB": k123_gbs / NOMINAL_HBM},
+        "phase_ms_per_step": {"p2g": per_launch_ms["p2g"], "grid_g2p": per_launch_ms["grid_g2p"],
+                              "g2pd": per_launch_ms["g2pd"], "time_advance": phase_ms[3] / args.steps,
+                              "reorder": phase_ms[4] / args.steps},
+        "algorithmic_bytes": alg,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": ck,
+        "e2e": e2e,
+        "cpu_baseline": cb,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def end_to_end(M, p, args):
+    """Same metric through the C ABI from host buffers: create, H2D of the
+    initial state (double arrays), K steps, D2H of the density field."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = M.Simulation.from_problem(p)
+    sim.step(args.steps)
+    rho = sim.read("RHO")
+    cons = sim.conservation()
+    t1 = time.perf_counter()
+    sim.close()
+    n = p.n_particles
+    d = p.cfg["dim"]
+    h2d = n * (2 * d + 3) * 8 + (p.mask.nbytes + p.normals.nbytes if p.mask is not None else 0)
+    d2h = rho.nbytes + cons.nbytes
+    return {"value": n * args.steps / (t1 - t0), "unit": "particle-steps/s",
+            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+            "seconds": t1 - t0}
+
+
+if __name__ == "__main__":
+    main()

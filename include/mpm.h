@@ -1,0 +1,180 @@
+/*
+ * mpm.h -- C ABI of the B300 (sm_103a) compressible-gas Material Point Method
+ * hot path (Baioni, Benacchio, Capone, de Falco, "Portable, Massively
+ * Parallel Implementation of a Material Point Method for Compressible Flows").
+ *
+ * One time step (Sec. 3, Algorithm 1) runs entirely on the GPU:
+ *   a1 stable re-order of the particles by the tile-major number of the basis
+ *      span that holds them (step xii; keys from step x),
+ *   a2 P2G of mass and momentum and P2GD of the pressure force (step ii),
+ *   a3 grid boundary conditions / obstacle projection (eqs. normali1-2) and
+ *      the momentum update mv' = mv + dt f (steps iii-iv),
+ *   a4 G2P of the acceleration, velocity update, momentum P2G (steps v-vii),
+ *   a5 boundary conditions on the new momentum (step vii),
+ *   a6 G2PD of the velocity divergence, energy / density / EOS / artificial
+ *      viscosity update (step viii, eqs. pressures, muart), move with Vbar
+ *      (step ix) and the new connectivity (step x),
+ *   a7 the CFL reduction and time advance (step xiii, eq. CFL).
+ *
+ * Conventions (all entry points):
+ *   - every call returns an mpm_status; nothing aborts, prints or exits;
+ *   - pointers to arrays are HOST pointers owned by the caller; inputs are
+ *     copied before the call returns, outputs are written before it returns;
+ *     the library never keeps a caller pointer;
+ *   - particle arrays are structure-of-arrays: x[a*n + k] is component a of
+ *     particle k; node arrays use the storage layout described below;
+ *   - device memory is owned by the simulation and released by mpm_destroy;
+ *   - a failing device check (non-finite state, a particle moving more than
+ *     one span in a step, an inconsistent tile) poisons the simulation: the
+ *     status is returned by the call that observes it (mpm_step, mpm_sync or
+ *     a read) and every later call except mpm_last_error/mpm_destroy returns
+ *     MPM_ESTATE.
+ *
+ * Grid layout.  d = dim, p = degree, n_a cells of edge h along axis a on
+ * [origin_a, origin_a + n_a h].  A non-periodic axis stores n_a + 2p - 1
+ * nodes, storage index i <-> node at origin_a + (i - (p - 1)) h (degree 2 has
+ * one ghost node beyond each face); a periodic axis stores n_a nodes.  Node
+ * (i0, i1, i2) is stored at (i2 N1 + i1) N0 + i0.
+ *
+ * Span and key.  A particle at xi = (x - origin)/h lies in span
+ * c = floor(xi) (degree 1, the grid cell) or c = floor(xi + 1/2) (degree 2, the
+ * dual cell around the nearest node), clamped to the axis (periodic: wrapped).
+ * Spans are grouped in tiles of tile[a] spans per axis; the key is
+ * tile_index * tile_volume + local_index, both x-fastest.  Keys are evaluated
+ * in the storage precision with one rounding per operation, so a given
+ * binary32 (binary64) position always gets the same key.
+ */
+#ifndef MPM_H
+#define MPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpm_sim mpm_sim;   /* opaque; owned by the library */
+
+typedef enum {
+    MPM_OK = 0,
+    MPM_EINVAL = 1,        /* bad argument, size or configuration */
+    MPM_ENOMEM = 2,        /* device or host allocation failed */
+    MPM_ECUDA = 3,         /* a CUDA runtime call failed (see mpm_last_error) */
+    MPM_ESTATE = 4,        /* call not allowed in the current state / poisoned */
+    MPM_ENONFINITE = 5,    /* non-finite state or 1 + dt div(v) <= 0 */
+    MPM_ETIMEOUT = 6,      /* a bounded device wait expired */
+    MPM_EUNSUPPORTED = 7,  /* valid request this build does not provide */
+    MPM_ECFL = 8           /* a particle crossed more than one span in a step */
+} mpm_status;
+
+typedef enum { MPM_BC_WALL = 0, MPM_BC_PERIODIC = 1, MPM_BC_INFLOW = 2, MPM_BC_OUTFLOW = 3 } mpm_bc;
+typedef enum { MPM_FP32 = 0, MPM_FP32_FIXED64 = 1, MPM_FP64 = 2 } mpm_precision;
+
+/* Fields for mpm_read_state / mpm_field_size. */
+enum {
+    MPM_FIELD_X = 0, MPM_FIELD_V = 1, MPM_FIELD_M = 2, MPM_FIELD_RHO = 3, MPM_FIELD_E = 4,
+    MPM_FIELD_P = 5, MPM_FIELD_Q = 6, MPM_FIELD_ID = 7, MPM_FIELD_KEY = 8,
+    MPM_FIELD_CELLSTART = 9, MPM_FIELD_GRID_M = 10, MPM_FIELD_GRID_MV = 11,
+    MPM_FIELD_GRID_F = 12, MPM_FIELD_GRID_MV2 = 13, MPM_FIELD_CLOCK = 14
+};
+
+typedef struct {
+    int dim;                 /* 2 or 3 */
+    int n[3];                /* cells per axis (n[2] ignored for dim 2) */
+    double h;                /* cell edge (square cells) */
+    double origin[3];
+    double gamma, c0, c1;    /* ideal-gas ratio (eq. pressures), AV constants (eq. muart) */
+    int degree;              /* 1: the paper's Q1 basis; 2: quadratic B-spline (Sec. 5) */
+    int precision;           /* mpm_precision */
+    double fixed_unit[3];    /* MPM_FP32_FIXED64: mass, momentum, force unit U; a
+                                contribution c is stored as round(c 2^32 / U) in int64.
+                                0 selects U = 1. */
+    int bc[6];               /* mpm_bc of faces -x,+x,-y,+y,-z,+z; periodic in pairs */
+    double inflow_rho, inflow_p, inflow_v[3];   /* inflow faces and recycled particles */
+    double cfl;              /* dt = cfl h / (max|v| + max c) (eq. CFL, Sec. 4.1) */
+    int sort_interval;       /* must be 1: the tiled kernels need ordered particles */
+    uint64_t seed;           /* Philox key for particle recycling */
+    int tile[3];             /* spans per tile per axis; 0 selects 8 (3D) / 16 (2D) */
+    void* stream;            /* cudaStream_t to run on; NULL: the library's own stream */
+    /* Optional device allocator (e.g. a framework's caching allocator):
+       alloc(bytes, ctx) returns device memory or NULL; free(ptr, ctx).
+       NULL: cudaMalloc/cudaFree. Memory is allocated only by create,
+       add_particles and set_obstacle_mask, never by step. */
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, void* ctx);
+    void* alloc_ctx;
+} mpm_config;
+
+/* Create an empty simulation on the current CUDA device (Sec. 3 step 2: the
+ * object is built once).  cfg is copied.  *out receives the handle, or NULL
+ * on error.  Errors: MPM_EINVAL (bad configuration), MPM_ENOMEM, MPM_ECUDA. */
+mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out);
+
+/* Append n particles (Sec. 3 step 2: the one host-to-device copy of the
+ * initial state).  x, v: dim x n SoA; mass, rho, e (specific internal
+ * energy): n values; all host pointers.  Positions must lie in the domain
+ * (closed, or half-open along periodic axes); mass, rho > 0.  The particles
+ * are converted to the storage precision, numbered (id = running count) and
+ * ordered by key.  Allowed only before the first mpm_step (MPM_ESTATE). */
+mpm_status mpm_add_particles(mpm_sim* sim, int64_t n, const double* x, const double* v,
+                             const double* mass, const double* rho, const double* e);
+
+/* Obstacle nodes (Sec. 2.2, eqs. normali1-2, sdf): node_mask[i] != 0 marks
+ * node i; normals is dim x nodes (outward unit normals, used on marked nodes
+ * only).  Both host arrays of the full node count.  When the -x or +x face
+ * is an inflow face, marked nodes within p+1 nodes of it are rejected
+ * (MPM_EINVAL): recycled particles are placed there. */
+mpm_status mpm_set_obstacle_mask(mpm_sim* sim, const uint8_t* node_mask, const double* normals);
+
+/* The CFL step (eq. CFL with Sec. 4.1's form) for the next step: from the
+ * initial state before the first step, else from the last step. */
+mpm_status mpm_cfl_dt(mpm_sim* sim, double* dt_out);
+
+/* Advance nsteps steps of Algorithm 1.  dt > 0 fixes the step; dt <= 0 uses
+ * the CFL rule.  t_end > 0 clips the last step so that t reaches t_end exactly
+ * and turns the remaining steps into no-ops.  Waits for completion and
+ * reports device-side errors. */
+mpm_status mpm_step(mpm_sim* sim, int64_t nsteps, double dt, double t_end);
+/* Same, but only enqueues the work on the simulation's stream; device
+ * errors are reported by the next mpm_sync or read. */
+mpm_status mpm_step_async(mpm_sim* sim, int64_t nsteps, double dt, double t_end);
+/* Wait for queued work; report device errors. */
+mpm_status mpm_sync(mpm_sim* sim);
+
+/* Copy a field to the host buffer out (count doubles, at least
+ * mpm_field_size(sim, field), else MPM_EINVAL).  Particle fields are in the
+ * current (key) order; ID gives the input numbering.  GRID_* are the raw
+ * P2G sums of the last step before boundary conditions (GRID_MV2 the second
+ * momentum P2G).  CLOCK = {t, dt_next, steps}. */
+mpm_status mpm_read_state(mpm_sim* sim, int field, double* out, int64_t count);
+/* Raw int64 grid sums of the fixed-point mode (GRID_M/MV/F/MV2 only). */
+mpm_status mpm_read_grid_fixed(mpm_sim* sim, int field, int64_t* out, int64_t count);
+/* Number of doubles a field needs, or -1. */
+int64_t mpm_field_size(const mpm_sim* sim, int field);
+
+/* FP64 sums over particles: {sum M, sum M (e + |V|^2/2), sum M V_x, _y, _z},
+ * reduced on the device in a fixed order. */
+mpm_status mpm_conservation(mpm_sim* sim, double out[5]);
+/* {particles, nodes, keys, steps done}. */
+mpm_status mpm_sizes(const mpm_sim* sim, int64_t out[4]);
+
+/* Per-phase device timing: enable (1) or disable (0).  When enabled each step
+ * records CUDA events around its phases on the simulation's stream; times
+ * accumulate until read.  out[8] = ms of {P2G, grid+G2P+P2G, G2PD+update,
+ * time advance, re-order, whole steps, -, -}; counts[8] = launches of this
+ * library's kernels in the same phases. */
+mpm_status mpm_profile(mpm_sim* sim, int enable);
+mpm_status mpm_profile_read(mpm_sim* sim, double out[8], int64_t counts[8], int reset);
+
+/* The simulation's stream (cudaStream_t). */
+void* mpm_stream(const mpm_sim* sim);
+/* Message of the last error of this handle (static storage if sim is NULL). */
+const char* mpm_last_error(const mpm_sim* sim);
+/* Release everything; NULL is allowed. Waits for queued work. */
+void mpm_destroy(mpm_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPM_H */

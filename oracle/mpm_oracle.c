@@ -22,8 +22,10 @@
  *   - theta(a, m) = a/m, and 0 where m == 0 (node with no mass);
  *   - artificial viscosity (eq. muart) evaluated with the updated rho, p and
  *     this step's div(v); the energy update uses the old p, q, rho;
- *   - dt = cfl*h/(max|v| + max c), v over both the moving velocity Vbar and
- *     the stored velocity (Sec. 3 step xiii, Sec. 4.1);
+ *   - dt = cfl*h/(max|v| + max c) (Sec. 3 step xiii, Sec. 4.1): v over the
+ *     moving velocity Vbar and the updated velocity V' of every particle
+ *     (plus the inflow speed when a particle is recycled), c from the state
+ *     after the step;
  *   - a particle leaving through an outflow face is re-created in the first
  *     cell layer of the inflow face with the inflow state (Sec. 4.1),
  *     positions drawn from Philox-4x32-10 keyed by (seed, step, id).
@@ -225,7 +227,7 @@ struct oracle_sim {
     double *bmv[3], *bf[3], *bmv2[3];          /* the same after the grid BC */
     double *tmp_node, *tmp_p[3], *coef;
     uint8_t* mask; double* nrm[3];
-    double t, dt_next;
+    double t, dt_next, vmax_step;
     int64_t step;
     int started, poisoned;
 };
@@ -380,21 +382,29 @@ static double pressure(const oracle_sim* s, int64_t k)
     return (s->cfg.gamma - 1.0) * s->rho[k] * s->E[k];
 }
 
-static void cfl_from_state(oracle_sim* s, int use_vbar)
+/* dt for the next step: after a step use_step_vmax = 1 takes the velocity
+ * maximum recorded during the step; before the first step Vbar := V. */
+static void cfl_from_state(oracle_sim* s, int use_step_vmax)
 {
     double vmax = 0.0, cmax = 0.0;
     for (int64_t k = 0; k < s->np; ++k) {
-        double v2 = 0.0, b2 = 0.0;
-        for (int a = 0; a < s->G.dim; ++a) { v2 += s->v[a][k] * s->v[a][k]; b2 += s->vbar[a][k] * s->vbar[a][k]; }
-        double vm = sqrt(v2);
-        if (use_vbar && sqrt(b2) > vm) vm = sqrt(b2);
-        if (vm > vmax) vmax = vm;
+        double v2 = 0.0;
+        for (int a = 0; a < s->G.dim; ++a) v2 += s->v[a][k] * s->v[a][k];
+        if (!use_step_vmax && sqrt(v2) > vmax) vmax = sqrt(v2);
         double c2 = s->cfg.gamma * pressure(s, k) / s->rho[k];
         double cs = sqrt(c2 > 0.0 ? c2 : 0.0);
         if (cs > cmax) cmax = cs;
     }
+    if (use_step_vmax) vmax = s->vmax_step;
     double den = vmax + cmax;
     s->dt_next = den > 0.0 ? s->cfg.cfl * s->G.h / den : 0.0;
+}
+
+static double norm_d(double* const v[3], int d, int64_t k)
+{
+    double s = 0.0;
+    for (int a = 0; a < d; ++a) s += v[a][k] * v[a][k];
+    return sqrt(s);
 }
 
 int oracle_cfl_dt(oracle_sim* s, double* dt_out)
@@ -552,6 +562,12 @@ static int one_step(oracle_sim* s, double dt)
     /* (vi) V' = V + dt A */
     for (int a = 0; a < d; ++a)
         for (int64_t k = 0; k < np; ++k) s->v[a][k] = s->v[a][k] + dt * A[a][k];
+    s->vmax_step = 0.0;
+    for (int64_t k = 0; k < np; ++k) {
+        double vb = norm_d(s->vbar, d, k), vn = norm_d(s->v, d, k);
+        if (vb > s->vmax_step) s->vmax_step = vb;
+        if (vn > s->vmax_step) s->vmax_step = vn;
+    }
     /* (vii) mv = P2G(I, M V') */
     for (int a = 0; a < d; ++a) {
         for (int64_t k = 0; k < np; ++k) s->coef[k] = s->M[k] * s->v[a][k];
@@ -608,7 +624,12 @@ static int one_step(oracle_sim* s, double dt)
             if (xn[a] >= G->hi[a] && c->bc[2 * a + 1] == OR_BC_OUTFLOW) out = 1;
         }
         for (int a = 0; a < d; ++a) s->x[a][k] = xn[a];
-        if (out && inflow >= 0) { recycle(s, k, inflow); continue; }
+        if (out && inflow >= 0) {
+            recycle(s, k, inflow);
+            double vi = norm_d(s->v, d, k);
+            if (vi > s->vmax_step) s->vmax_step = vi;
+            continue;
+        }
         for (int a = 0; a < d; ++a) {
             double lo = G->lo[a], hi = G->hi[a], L = hi - lo;
             if (G->per[a]) {

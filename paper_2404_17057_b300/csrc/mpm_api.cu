@@ -1,0 +1,1014 @@
+// mpm_api.cu -- the C ABI of include/mpm.h on top of the sm_103a kernels.
+//
+// Host side only: argument checks, device memory, the order of the launches
+// of one step (Algorithm 1), CUDA-graph replay of whole steps, and reads.
+// Every arithmetic step of the method runs in the kernels of
+// mpm_kernels.cuh / mpm_sort.cuh.
+#include "mpm.h"
+#include "mpm_kernels.cuh"
+#include "mpm_sort.cuh"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace mpm;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPhases = 5;   // P2G, grid+G2P+P2G, G2PD+update, time advance, re-order
+
+struct Buffers {             // one copy of the particle state (type-erased)
+    void* x[3] = {nullptr, nullptr, nullptr};
+    void* v[3] = {nullptr, nullptr, nullptr};
+    void* M = nullptr;
+    void* rho = nullptr;
+    void* E = nullptr;
+    void* Q = nullptr;
+    uint32_t* id = nullptr;
+    uint32_t* key = nullptr;
+};
+
+struct ProfStep {
+    cudaEvent_t ev[kPhases + 1];
+};
+
+}  // namespace
+
+struct Vtbl;
+
+struct mpm_sim {
+    mpm_config cfg;
+    Geom G;
+    const Vtbl* vt = nullptr;
+    size_t rsize = 4, asize = 4;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int64_t np = 0;
+    int cur = 0;
+    Buffers buf[2];
+    void* grid = nullptr;          // m, mv[d], f[d], mv2[d] of type A, contiguous
+    size_t grid_bytes = 0;
+    uint8_t* mask = nullptr;
+    void* nrm = nullptr;           // d x nodes of type R
+    Clock* clk = nullptr;
+    uint32_t* cellstart = nullptr;
+    uint32_t* skeys[2] = {nullptr, nullptr};
+    uint32_t* sidx[2] = {nullptr, nullptr};
+    uint32_t* hist = nullptr;
+    uint32_t* scan_part = nullptr;
+    double* cons_part = nullptr;
+    double* cons_out = nullptr;
+    int radix_passes = 0, radix_bits = 0;
+    bool started = false, poisoned = false, stepped = false, cfl_done = false;
+    std::vector<void*> allocs;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool graph_ok = true;
+    bool profiling = false;
+    std::vector<ProfStep> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[8] = {0};
+    int64_t prof_launch[8] = {0};
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_static_err;
+
+mpm_status fail(mpm_sim* s, mpm_status st, const std::string& msg)
+{
+    if (s) s->err = msg; else g_static_err = msg;
+    return st;
+}
+
+mpm_status cuda_fail(mpm_sim* s, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (s) s->poisoned = true;
+    return fail(s, MPM_ECUDA, m);
+}
+
+#define CK(call, what)                                 \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(s, e_, what); \
+    } while (0)
+
+void* dalloc(mpm_sim* s, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (s->cfg.alloc) {
+        p = s->cfg.alloc(bytes, s->cfg.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) s->allocs.push_back(p);
+    return p;
+}
+
+void dfree(mpm_sim* s, void* p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < s->allocs.size(); ++i)
+        if (s->allocs[i] == p) { s->allocs.erase(s->allocs.begin() + i); break; }
+    if (s->cfg.free) s->cfg.free(p, s->cfg.alloc_ctx);
+    else cudaFree(p);
+}
+
+unsigned nblk(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+__global__ void k_zero(uint4* p, int64_t n16, const int* active)
+{
+    if (active && !*active) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = make_uint4(0, 0, 0, 0);
+}
+
+}  // namespace
+
+// ------------------------------------------------------ per-type dispatch
+
+struct Vtbl {
+    void (*step_kernels)(mpm_sim* s, int phase_mask_first, cudaStream_t st);
+    void (*keys)(mpm_sim* s, int b, cudaStream_t st);
+    void (*gather)(mpm_sim* s, int from, const uint32_t* perm, const uint32_t* skeys, const int* active,
+                   cudaStream_t st);
+    void (*cfl_init)(mpm_sim* s, cudaStream_t st);
+    void (*cons)(mpm_sim* s, cudaStream_t st);
+    void (*from_double)(const double* in, void* out, int64_t n, cudaStream_t st);
+    cudaError_t (*set_smem)(const Geom& G);
+    size_t (*smem)(const Geom& G, int kernel);
+};
+
+namespace {
+
+template <class R>
+Particles<R> parts(const Buffers& b)
+{
+    Particles<R> p;
+    for (int a = 0; a < 3; ++a) {
+        p.x[a] = (R*)b.x[a];
+        p.v[a] = (R*)b.v[a];
+    }
+    p.M = (R*)b.M;
+    p.rho = (R*)b.rho;
+    p.E = (R*)b.E;
+    p.Q = (R*)b.Q;
+    p.id = b.id;
+    p.key = b.key;
+    return p;
+}
+
+template <class A, class R>
+Grid<A, R> grid_view(const mpm_sim* s)
+{
+    Grid<A, R> g;
+    const int64_t nn = s->G.nnode;
+    const int d = s->G.dim;
+    A* base = (A*)s->grid;
+    g.m = base;
+    for (int a = 0; a < 3; ++a) {
+        g.mv[a] = a < d ? base + (1 + a) * nn : nullptr;
+        g.f[a] = a < d ? base + (1 + d + a) * nn : nullptr;
+        g.mv2[a] = a < d ? base + (1 + 2 * d + a) * nn : nullptr;
+        g.nrm[a] = (s->nrm && a < d) ? (const R*)s->nrm + a * nn : nullptr;
+    }
+    g.mask = s->mask;
+    return g;
+}
+
+template <int D, int P, class R, class A>
+struct Impl {
+    static size_t smem(const Geom& G, int kernel)
+    {
+        const size_t W = (size_t)G.Wvol;
+        if (kernel == 0) return (1 + 2 * D) * W * sizeof(A);
+        if (kernel == 1) return align16(D * W * sizeof(R)) + D * W * sizeof(A);
+        return 2 * D * W * sizeof(R);
+    }
+    static cudaError_t set_smem(const Geom& G)
+    {
+        cudaError_t e;
+        e = cudaFuncSetAttribute(k_p2g<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(G, 0));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_grid_g2p<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem(G, 1));
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_g2pd<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(G, 2));
+    }
+    // mask bit 0: P2G, 1: grid+G2P, 2: G2PD (used by the profiler to split)
+    static void step_kernels(mpm_sim* s, int which, cudaStream_t st)
+    {
+        const Geom& G = s->G;
+        Particles<R> pt = parts<R>(s->buf[s->cur]);
+        Grid<A, R> gr = grid_view<A, R>(s);
+        if (which & 1) {
+            k_zero<<<std::min<int64_t>(nblk(s->grid_bytes / 16), 148 * 8), kThreads, 0, st>>>(
+                (uint4*)s->grid, (int64_t)(s->grid_bytes / 16), &s->clk->active);
+            k_p2g<D, P, R, A><<<G.ntiles, kThreads, smem(G, 0), st>>>(G, pt, gr, s->cellstart, s->clk);
+            s->launches += 2;
+        }
+        if (which & 2) {
+            k_grid_g2p<D, P, R, A><<<G.ntiles, kThreads, smem(G, 1), st>>>(G, pt, gr, s->cellstart, s->clk);
+            s->launches += 1;
+        }
+        if (which & 4) {
+            k_g2pd<D, P, R, A><<<G.ntiles, kThreads, smem(G, 2), st>>>(G, pt, gr, s->cellstart, s->clk);
+            s->launches += 1;
+        }
+    }
+    static void keys(mpm_sim* s, int b, cudaStream_t st)
+    {
+        if (s->np == 0) return;
+        k_keys<D, P, R><<<nblk(s->np), kThreads, 0, st>>>(s->G, parts<R>(s->buf[b]), s->np);
+        s->launches += 1;
+    }
+    static void gather(mpm_sim* s, int from, const uint32_t* perm, const uint32_t* sk, const int* active,
+                       cudaStream_t st)
+    {
+        if (s->np == 0) return;
+        k_gather<D, R><<<nblk(s->np), kThreads, 0, st>>>(parts<R>(s->buf[from]), parts<R>(s->buf[1 - from]), perm,
+                                                         sk, s->np, active);
+        s->launches += 1;
+    }
+    static void cfl_init(mpm_sim* s, cudaStream_t st)
+    {
+        unsigned nb = std::max(1u, std::min(nblk(s->np), 148u * 8u));
+        k_cfl_init<D, R><<<nb, kThreads, 0, st>>>(s->G, parts<R>(s->buf[s->cur]), s->np, s->clk);
+        k_cfl_init_finish<<<1, 1, 0, st>>>(s->clk, s->G.cfl * s->G.h);
+        s->launches += 2;
+    }
+    static void cons(mpm_sim* s, cudaStream_t st)
+    {
+        const int nb = 1024;
+        k_cons_partial<D, R><<<nb, 256, 0, st>>>(parts<R>(s->buf[s->cur]), s->np, s->cons_part);
+        k_cons_final<<<1, 32, 0, st>>>(s->cons_part, nb, s->cons_out);
+        s->launches += 2;
+    }
+    static void from_double(const double* in, void* out, int64_t n, cudaStream_t st)
+    {
+        if (n > 0) k_from_double<R><<<nblk(n), kThreads, 0, st>>>(in, (R*)out, n);
+    }
+};
+
+template <int D, int P, class R, class A>
+const Vtbl* vtbl_of()
+{
+    typedef Impl<D, P, R, A> I;
+    static const Vtbl v = {I::step_kernels, I::keys, I::gather, I::cfl_init, I::cons, I::from_double, I::set_smem,
+                           I::smem};
+    return &v;
+}
+
+template <int D, int P>
+const Vtbl* vtbl_prec(int prec)
+{
+    if (prec == MPM_FP32) return vtbl_of<D, P, float, float>();
+    if (prec == MPM_FP32_FIXED64) return vtbl_of<D, P, float, long long>();
+    return vtbl_of<D, P, double, double>();
+}
+
+const Vtbl* select_vtbl(int d, int p, int prec)
+{
+    if (d == 2) return p == 1 ? vtbl_prec<2, 1>(prec) : vtbl_prec<2, 2>(prec);
+    return p == 1 ? vtbl_prec<3, 1>(prec) : vtbl_prec<3, 2>(prec);
+}
+
+// ------------------------------------------------------------- geometry
+
+mpm_status make_geom(const mpm_config* c, Geom* G, std::string* why)
+{
+    memset(G, 0, sizeof(*G));
+    if (c->dim != 2 && c->dim != 3) { *why = "dim must be 2 or 3"; return MPM_EINVAL; }
+    if (c->degree != 1 && c->degree != 2) { *why = "degree must be 1 or 2"; return MPM_EINVAL; }
+    if (!(c->h > 0.0) || !std::isfinite(c->h)) { *why = "h must be > 0"; return MPM_EINVAL; }
+    if (!(c->gamma > 1.0)) { *why = "gamma must be > 1"; return MPM_EINVAL; }
+    if (!(c->cfl > 0.0)) { *why = "cfl must be > 0"; return MPM_EINVAL; }
+    if (c->precision < 0 || c->precision > 2) { *why = "bad precision"; return MPM_EINVAL; }
+    if (c->sort_interval != 1) { *why = "sort_interval must be 1 (tiled kernels need key order)"; return MPM_EUNSUPPORTED; }
+    G->dim = c->dim;
+    G->p = c->degree;
+    G->h = c->h;
+    G->inv_h = 1.0 / c->h;
+    int64_t nkey = 1, nnode = 1;
+    int tvol = 1, wvol = 1, ntiles = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (a >= c->dim) {
+            G->n[a] = G->S[a] = G->N[a] = G->T[a] = G->nt[a] = G->W[a] = 1;
+            continue;
+        }
+        int bl = c->bc[2 * a], bh = c->bc[2 * a + 1];
+        if (bl < 0 || bl > 3 || bh < 0 || bh > 3) { *why = "bad boundary condition"; return MPM_EINVAL; }
+        if ((bl == MPM_BC_PERIODIC) != (bh == MPM_BC_PERIODIC)) { *why = "periodic faces come in pairs"; return MPM_EINVAL; }
+        if (c->n[a] < 1 || c->n[a] > (1 << 20)) { *why = "bad cell count"; return MPM_EINVAL; }
+        G->n[a] = c->n[a];
+        G->per[a] = bl == MPM_BC_PERIODIC;
+        G->S[a] = G->per[a] ? c->n[a] : (G->p == 2 ? c->n[a] + 1 : c->n[a]);
+        G->N[a] = G->per[a] ? c->n[a] : c->n[a] + 2 * G->p - 1;
+        G->g[a] = G->per[a] ? 0 : G->p - 1;
+        G->T[a] = c->tile[a] > 0 ? c->tile[a] : (c->dim == 3 ? 8 : 16);
+        if (G->T[a] > 64) { *why = "tile edge must be <= 64"; return MPM_EINVAL; }
+        G->nt[a] = (G->S[a] + G->T[a] - 1) / G->T[a];
+        G->W[a] = G->T[a] + G->p;
+        G->lo[a] = c->origin[a];
+        G->hi[a] = c->origin[a] + c->n[a] * c->h;
+    }
+    for (int a = 0; a < 3; ++a) {
+        tvol *= G->T[a];
+        wvol *= G->W[a];
+        ntiles *= G->nt[a];
+        nnode *= G->N[a];
+    }
+    nkey = (int64_t)ntiles * tvol;
+    if (nkey >= (int64_t)0xFFFFFFF0LL) { *why = "too many spans for 32-bit keys"; return MPM_EINVAL; }
+    G->Tvol = tvol;
+    G->Wvol = wvol;
+    G->ntiles = ntiles;
+    G->nkey = nkey;
+    G->nnode = nnode;
+    for (int f = 0; f < 6; ++f) G->bc[f] = f < 2 * c->dim ? c->bc[f] : MPM_BC_WALL;
+    G->inflow_face = -1;
+    for (int f = 0; f < 2 * c->dim; ++f)
+        if (c->bc[f] == MPM_BC_INFLOW) { G->inflow_face = f; break; }
+    G->gamma = c->gamma;
+    G->c0 = c->c0;
+    G->c1 = c->c1;
+    G->cfl = c->cfl;
+    G->inflow_rho = c->inflow_rho;
+    G->inflow_p = c->inflow_p;
+    for (int a = 0; a < 3; ++a) G->inflow_v[a] = a < c->dim ? c->inflow_v[a] : 0.0;
+    if (G->inflow_face >= 0) {
+        if (!(c->inflow_rho > 0.0)) { *why = "inflow_rho must be > 0"; return MPM_EINVAL; }
+        G->inflow_e = c->inflow_p / ((c->gamma - 1.0) * c->inflow_rho);
+    }
+    G->seed = c->seed;
+    for (int i = 0; i < 3; ++i) {
+        double u = c->fixed_unit[i] > 0.0 ? c->fixed_unit[i] : 1.0;
+        G->qscale[i] = (float)(4294967296.0 / u);
+        G->dqscale[i] = (float)(u / 4294967296.0);
+    }
+    return MPM_OK;
+}
+
+mpm_status alloc_particles(mpm_sim* s, int64_t n, Buffers nb[2])
+{
+    const int d = s->G.dim;
+    const size_t rb = (size_t)n * s->rsize, ub = (size_t)n * 4;
+    for (int b = 0; b < 2; ++b) {
+        for (int a = 0; a < d; ++a) {
+            nb[b].x[a] = dalloc(s, rb);
+            nb[b].v[a] = dalloc(s, rb);
+            if (!nb[b].x[a] || !nb[b].v[a]) return MPM_ENOMEM;
+        }
+        nb[b].M = dalloc(s, rb);
+        nb[b].rho = dalloc(s, rb);
+        nb[b].E = dalloc(s, rb);
+        nb[b].Q = dalloc(s, rb);
+        nb[b].id = (uint32_t*)dalloc(s, ub);
+        nb[b].key = (uint32_t*)dalloc(s, ub);
+        if (!nb[b].M || !nb[b].rho || !nb[b].E || !nb[b].Q || !nb[b].id || !nb[b].key) return MPM_ENOMEM;
+    }
+    return MPM_OK;
+}
+
+void free_particles(mpm_sim* s, Buffers b[2])
+{
+    for (int k = 0; k < 2; ++k) {
+        for (int a = 0; a < 3; ++a) { dfree(s, b[k].x[a]); dfree(s, b[k].v[a]); }
+        dfree(s, b[k].M); dfree(s, b[k].rho); dfree(s, b[k].E); dfree(s, b[k].Q);
+        dfree(s, b[k].id); dfree(s, b[k].key);
+        b[k] = Buffers();
+    }
+}
+
+void drop_graphs(mpm_sim* s)
+{
+    for (int b = 0; b < 2; ++b)
+        if (s->graph[b]) { cudaGraphExecDestroy(s->graph[b]); s->graph[b] = nullptr; }
+}
+
+// Re-order: LSD radix passes over (key, index), then gather into the other
+// buffer and rebuild the cell-start table.  Swaps s->cur.
+void launch_sort(mpm_sim* s, cudaStream_t st, const int* active)
+{
+    const int64_t n = s->np;
+    if (n == 0) return;
+    const unsigned nb = (unsigned)((n + kSortTile - 1) / kSortTile);
+    const uint32_t* kin = s->buf[s->cur].key;
+    const uint32_t* iin = nullptr;
+    int o = 0;
+    for (int pass = 0; pass < s->radix_passes; ++pass) {
+        const int shift = pass * s->radix_bits;
+        const int bits = s->radix_bits;
+        k_radix_hist<<<nb, kSortThreads, 0, st>>>(kin, n, shift, bits, s->hist, active);
+        scan_exclusive(s->hist, s->hist, (int64_t)(1 << bits) * nb, s->scan_part, 0, st, &s->launches);
+        k_radix_scatter<<<nb, kSortThreads, 0, st>>>(kin, iin, s->skeys[o], s->sidx[o], n, shift, bits, s->hist,
+                                                      active, pass == 0);
+        s->launches += 2;
+        kin = s->skeys[o];
+        iin = s->sidx[o];
+        o ^= 1;
+    }
+    s->vt->gather(s, s->cur, iin, kin, active, st);
+    k_cell_start<<<nblk(n + 1), kThreads, 0, st>>>(s->buf[1 - s->cur].key, n, s->G.nkey, s->cellstart, active);
+    s->launches += 1;
+    s->cur ^= 1;
+}
+
+// One whole step (Algorithm 1) on the stream; phase events if profiling.
+void launch_step(mpm_sim* s, cudaStream_t st, ProfStep* ps)
+{
+    if (ps) cudaEventRecord(ps->ev[0], st);
+    k_prepare<<<1, 1, 0, st>>>(s->clk);
+    s->launches += 1;
+    s->vt->step_kernels(s, 1, st);
+    if (ps) cudaEventRecord(ps->ev[1], st);
+    s->vt->step_kernels(s, 2, st);
+    if (ps) cudaEventRecord(ps->ev[2], st);
+    s->vt->step_kernels(s, 4, st);
+    if (ps) cudaEventRecord(ps->ev[3], st);
+    k_finalize<<<1, 1, 0, st>>>(s->clk, s->G.cfl * s->G.h);
+    s->launches += 1;
+    if (ps) cudaEventRecord(ps->ev[4], st);
+    launch_sort(s, st, &s->clk->active);
+    if (ps) cudaEventRecord(ps->ev[5], st);
+}
+
+mpm_status check_device_errors(mpm_sim* s)
+{
+    Clock c;
+    CK(cudaMemcpyAsync(&c, s->clk, sizeof(Clock), cudaMemcpyDeviceToHost, s->stream), "read clock");
+    CK(cudaStreamSynchronize(s->stream), "synchronize");
+    if (c.err) {
+        s->poisoned = true;
+        if (c.err & ERR_TILE) return fail(s, MPM_ESTATE, "internal: particle outside its tile (order lost)");
+        if (c.err & ERR_CFL) return fail(s, MPM_ECFL, "a particle crossed more than one span in one step");
+        return fail(s, MPM_ENONFINITE, "non-finite state or 1 + dt div(v) <= 0");
+    }
+    return MPM_OK;
+}
+
+cudaEvent_t pool_event(mpm_sim* s)
+{
+    if (!s->ev_pool.empty()) {
+        cudaEvent_t e = s->ev_pool.back();
+        s->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+mpm_status collect_profile(mpm_sim* s)
+{
+    if (s->prof.empty()) return MPM_OK;
+    CK(cudaStreamSynchronize(s->stream), "synchronize");
+    for (auto& ps : s->prof) {
+        float ms;
+        for (int k = 0; k < kPhases; ++k) {
+            if (cudaEventElapsedTime(&ms, ps.ev[k], ps.ev[k + 1]) == cudaSuccess) s->prof_ms[k] += ms;
+        }
+        if (cudaEventElapsedTime(&ms, ps.ev[0], ps.ev[kPhases]) == cudaSuccess) s->prof_ms[5] += ms;
+        for (int k = 0; k <= kPhases; ++k) s->ev_pool.push_back(ps.ev[k]);
+    }
+    s->prof.clear();
+    cudaGetLastError();
+    return MPM_OK;
+}
+
+}  // namespace
+
+// ================================================================== ABI
+
+extern "C" {
+
+mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
+{
+    if (!out) return fail(nullptr, MPM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, MPM_EINVAL, "cfg is NULL");
+    if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
+        return fail(nullptr, MPM_EINVAL, "alloc and free hooks come together");
+    mpm_sim* s = new (std::nothrow) mpm_sim();
+    if (!s) return fail(nullptr, MPM_ENOMEM, "host allocation failed");
+    s->cfg = *cfg;
+    std::string why;
+    mpm_status st = make_geom(cfg, &s->G, &why);
+    if (st != MPM_OK) { delete s; return fail(nullptr, st, why); }
+    s->vt = select_vtbl(cfg->dim, cfg->degree, cfg->precision);
+    s->rsize = cfg->precision == MPM_FP64 ? 8 : 4;
+    s->asize = cfg->precision == MPM_FP32 ? 4 : 8;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return fail(nullptr, MPM_ECUDA, "no CUDA device");
+    }
+    if (cfg->stream) {
+        s->stream = (cudaStream_t)cfg->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return fail(nullptr, MPM_ECUDA, "stream creation failed");
+        }
+        s->own_stream = true;
+    }
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+    for (int k = 0; k < 3; ++k)
+        if ((int)s->vt->smem(s->G, k) > smem_optin) {
+            mpm_destroy(s);
+            return fail(nullptr, MPM_EINVAL, "tile too large for shared memory");
+        }
+    cudaError_t e = s->vt->set_smem(s->G);
+    if (e != cudaSuccess) {
+        mpm_destroy(s);
+        return fail(nullptr, MPM_ECUDA, std::string("shared memory attribute: ") + cudaGetErrorString(e));
+    }
+    const int d = s->G.dim;
+    s->grid_bytes = align16((size_t)(1 + 3 * d) * (size_t)s->G.nnode * s->asize);
+    s->grid = dalloc(s, s->grid_bytes);
+    s->clk = (Clock*)dalloc(s, sizeof(Clock));
+    s->cellstart = (uint32_t*)dalloc(s, (size_t)(s->G.nkey + 1) * 4);
+    s->cons_part = (double*)dalloc(s, 1024 * 5 * sizeof(double));
+    s->cons_out = (double*)dalloc(s, 8 * sizeof(double));
+    if (!s->grid || !s->clk || !s->cellstart || !s->cons_part || !s->cons_out) {
+        mpm_destroy(s);
+        return fail(nullptr, MPM_ENOMEM, "device allocation failed");
+    }
+    if (cudaMemsetAsync(s->grid, 0, s->grid_bytes, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->clk, 0, sizeof(Clock), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->cellstart, 0, (size_t)(s->G.nkey + 1) * 4, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        mpm_destroy(s);
+        return fail(nullptr, MPM_ECUDA, "device initialisation failed");
+    }
+    int bits = 1;
+    while (((int64_t)1 << bits) < s->G.nkey) ++bits;
+    s->radix_passes = (bits + 7) / 8;
+    s->radix_bits = (bits + s->radix_passes - 1) / s->radix_passes;
+    *out = s;
+    return MPM_OK;
+}
+
+mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const double* v, const double* mass,
+                             const double* rho, const double* e)
+{
+    if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
+    if (s->started) return fail(s, MPM_ESTATE, "particles can only be added before the first step");
+    if (n < 0) return fail(s, MPM_EINVAL, "n < 0");
+    if (n == 0) return MPM_OK;
+    if (!x || !v || !mass || !rho || !e) return fail(s, MPM_EINVAL, "NULL input array");
+    if (s->np + n > (int64_t)0x7FFFFFFF) return fail(s, MPM_EINVAL, "too many particles");
+    const Geom& G = s->G;
+    const int d = G.dim;
+    for (int64_t k = 0; k < n; ++k) {
+        if (!(mass[k] > 0.0) || !(rho[k] > 0.0) || !std::isfinite(e[k]) || !std::isfinite(mass[k]) ||
+            !std::isfinite(rho[k]))
+            return fail(s, MPM_EINVAL, "mass and rho must be > 0, e finite");
+        for (int a = 0; a < d; ++a) {
+            double xa = x[a * n + k];
+            if (!(xa >= G.lo[a]) || !(xa <= G.hi[a]) || !std::isfinite(v[a * n + k]))
+                return fail(s, MPM_EINVAL, "particle outside the domain or non-finite velocity");
+            if (G.per[a] && !(xa < G.hi[a])) return fail(s, MPM_EINVAL, "periodic axis: x must be < hi");
+        }
+    }
+    const int64_t np = s->np + n;
+    Buffers nb[2];
+    mpm_status st = alloc_particles(s, np, nb);
+    if (st != MPM_OK) { free_particles(s, nb); return fail(s, st, "device allocation failed"); }
+    const size_t rs = s->rsize;
+    cudaStream_t S = s->stream;
+    // keep the particles already there (current buffer) at the front
+    if (s->np > 0) {
+        const Buffers& ob = s->buf[s->cur];
+        for (int a = 0; a < d; ++a) {
+            CK(cudaMemcpyAsync(nb[0].x[a], ob.x[a], s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
+            CK(cudaMemcpyAsync(nb[0].v[a], ob.v[a], s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
+        }
+        CK(cudaMemcpyAsync(nb[0].M, ob.M, s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
+        CK(cudaMemcpyAsync(nb[0].rho, ob.rho, s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
+        CK(cudaMemcpyAsync(nb[0].E, ob.E, s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
+        CK(cudaMemcpyAsync(nb[0].Q, ob.Q, s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
+        CK(cudaMemcpyAsync(nb[0].id, ob.id, s->np * 4, cudaMemcpyDeviceToDevice, S), "copy");
+    }
+    // stage the new doubles on the device and convert to the storage precision
+    double* stage = (double*)dalloc(s, (size_t)n * sizeof(double));
+    if (!stage) { free_particles(s, nb); return fail(s, MPM_ENOMEM, "device allocation failed"); }
+    auto up = [&](const double* src, void* dst) -> cudaError_t {
+        cudaError_t r = cudaMemcpyAsync(stage, src, n * sizeof(double), cudaMemcpyHostToDevice, S);
+        if (r != cudaSuccess) return r;
+        s->vt->from_double(stage, (char*)dst + s->np * rs, n, S);
+        return cudaStreamSynchronize(S);   // the staging buffer is reused
+    };
+    for (int a = 0; a < d; ++a) {
+        CK(up(x + a * n, nb[0].x[a]), "upload x");
+        CK(up(v + a * n, nb[0].v[a]), "upload v");
+    }
+    CK(up(mass, nb[0].M), "upload mass");
+    CK(up(rho, nb[0].rho), "upload rho");
+    CK(up(e, nb[0].E), "upload e");
+    dfree(s, stage);
+    CK(cudaMemsetAsync((char*)nb[0].Q + s->np * rs, 0, n * rs, S), "zero q");
+    k_iota<<<nblk(n), kThreads, 0, S>>>(nb[0].id + s->np, n, (uint32_t)s->np);
+    // replace the old buffers and the sort scratch
+    free_particles(s, s->buf);
+    s->buf[0] = nb[0];
+    s->buf[1] = nb[1];
+    s->cur = 0;
+    s->np = np;
+    for (int b = 0; b < 2; ++b) {
+        dfree(s, s->skeys[b]);
+        dfree(s, s->sidx[b]);
+        s->skeys[b] = (uint32_t*)dalloc(s, (size_t)np * 4);
+        s->sidx[b] = (uint32_t*)dalloc(s, (size_t)np * 4);
+    }
+    dfree(s, s->hist);
+    dfree(s, s->scan_part);
+    const int64_t nblocks = (np + kSortTile - 1) / kSortTile;
+    const int64_t nhist = nblocks * ((int64_t)1 << s->radix_bits);
+    s->hist = (uint32_t*)dalloc(s, (size_t)nhist * 4);
+    s->scan_part = (uint32_t*)dalloc(s, (size_t)std::max<int64_t>(scan_blocks(nhist), 1) * 4);
+    if (!s->skeys[0] || !s->skeys[1] || !s->sidx[0] || !s->sidx[1] || !s->hist || !s->scan_part)
+        return fail(s, MPM_ENOMEM, "device allocation failed");
+    drop_graphs(s);
+    s->cfl_done = false;
+    // initial order: keys from the positions, then the stable re-order
+    s->vt->keys(s, s->cur, S);
+    launch_sort(s, S, nullptr);
+    CK(cudaGetLastError(), "launch");
+    CK(cudaStreamSynchronize(S), "synchronize");
+    return MPM_OK;
+}
+
+mpm_status mpm_set_obstacle_mask(mpm_sim* s, const uint8_t* mask, const double* normals)
+{
+    if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
+    if (!mask || !normals) return fail(s, MPM_EINVAL, "NULL input array");
+    const Geom& G = s->G;
+    const int64_t nn = G.nnode;
+    const int d = G.dim;
+    if (G.inflow_face >= 0) {
+        const int af = G.inflow_face / 2, side = G.inflow_face % 2;
+        for (int64_t i = 0; i < nn; ++i) {
+            if (!mask[i]) continue;
+            int64_t ia = af == 0 ? i % G.N[0] : af == 1 ? (i / G.N[0]) % G.N[1] : i / ((int64_t)G.N[0] * G.N[1]);
+            int64_t phys = ia - G.g[af];
+            bool near = side == 0 ? phys <= G.p : phys >= G.n[af] - G.p;
+            if (near) return fail(s, MPM_EINVAL, "obstacle nodes next to the inflow face");
+        }
+    }
+    for (int64_t i = 0; i < (int64_t)d * nn; ++i)
+        if (!std::isfinite(normals[i])) return fail(s, MPM_EINVAL, "non-finite normal");
+    if (!s->mask) {
+        s->mask = (uint8_t*)dalloc(s, (size_t)nn);
+        s->nrm = dalloc(s, (size_t)d * nn * s->rsize);
+        if (!s->mask || !s->nrm) return fail(s, MPM_ENOMEM, "device allocation failed");
+    }
+    std::vector<uint8_t> m(nn);
+    for (int64_t i = 0; i < nn; ++i) m[i] = mask[i] ? 1 : 0;
+    CK(cudaMemcpyAsync(s->mask, m.data(), nn, cudaMemcpyHostToDevice, s->stream), "upload mask");
+    double* stage = (double*)dalloc(s, (size_t)d * nn * sizeof(double));
+    if (!stage) return fail(s, MPM_ENOMEM, "device allocation failed");
+    CK(cudaMemcpyAsync(stage, normals, (size_t)d * nn * sizeof(double), cudaMemcpyHostToDevice, s->stream), "upload");
+    s->vt->from_double(stage, s->nrm, (int64_t)d * nn, s->stream);
+    CK(cudaStreamSynchronize(s->stream), "synchronize");
+    dfree(s, stage);
+    drop_graphs(s);
+    return MPM_OK;
+}
+
+static mpm_status ensure_cfl(mpm_sim* s)
+{
+    if (s->cfl_done) return MPM_OK;
+    if (s->np == 0) return fail(s, MPM_ESTATE, "no particles");
+    s->vt->cfl_init(s, s->stream);
+    CK(cudaGetLastError(), "launch");
+    s->cfl_done = true;
+    return MPM_OK;
+}
+
+mpm_status mpm_cfl_dt(mpm_sim* s, double* dt_out)
+{
+    if (!s || !dt_out) return fail(s, MPM_EINVAL, "NULL argument");
+    if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
+    mpm_status st = ensure_cfl(s);
+    if (st != MPM_OK) return st;
+    Clock c;
+    CK(cudaMemcpyAsync(&c, s->clk, sizeof(Clock), cudaMemcpyDeviceToHost, s->stream), "read clock");
+    CK(cudaStreamSynchronize(s->stream), "synchronize");
+    *dt_out = c.dt_next;
+    return MPM_OK;
+}
+
+static mpm_status capture_graph(mpm_sim* s, int b)
+{
+    // the step reads buffer b and leaves the sorted state in 1 - b
+    cudaStream_t st = s->stream;
+    cudaGraph_t g = nullptr;
+    const int saved = s->cur;
+    const int64_t saved_l = s->launches;
+    s->cur = b;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        s->cur = saved;
+        return MPM_ECUDA;
+    }
+    launch_step(s, st, nullptr);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    s->cur = saved;
+    s->launches = saved_l;
+    if (e != cudaSuccess || !g) { cudaGetLastError(); return MPM_ECUDA; }
+    e = cudaGraphInstantiate(&s->graph[b], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { cudaGetLastError(); s->graph[b] = nullptr; return MPM_ECUDA; }
+    return MPM_OK;
+}
+
+static int64_t step_launch_count(const mpm_sim* s)
+{
+    // prepare, zero, 3 step kernels, finalize, per radix pass (hist, 3 scan,
+    // scatter), gather, cell start
+    return 6 + 5 * (int64_t)s->radix_passes + 2;
+}
+
+mpm_status mpm_step_async(mpm_sim* s, int64_t nsteps, double dt, double t_end)
+{
+    if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
+    if (nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t_end)) return fail(s, MPM_EINVAL, "bad step arguments");
+    mpm_status st = ensure_cfl(s);
+    if (st != MPM_OK) return st;
+    s->started = true;
+    k_set_params<<<1, 1, 0, s->stream>>>(s->clk, dt > 0.0 ? dt : 0.0, t_end > 0.0 ? t_end : 0.0);
+    s->launches += 1;
+    for (int64_t i = 0; i < nsteps; ++i) {
+        if (s->profiling) {
+            ProfStep ps;
+            for (int k = 0; k <= kPhases; ++k) ps.ev[k] = pool_event(s);
+            const int64_t l0 = s->launches;
+            launch_step(s, s->stream, &ps);
+            s->prof_launch[5] += s->launches - l0;
+            s->prof.push_back(ps);
+        } else {
+            const int b = s->cur;
+            if (!s->graph[b] && s->graph_ok && capture_graph(s, b) != MPM_OK) s->graph_ok = false;
+            if (s->graph[b]) {
+                CK(cudaGraphLaunch(s->graph[b], s->stream), "graph launch");
+                s->cur ^= 1;
+                s->launches += step_launch_count(s);
+            } else {
+                launch_step(s, s->stream, nullptr);
+            }
+        }
+    }
+    CK(cudaGetLastError(), "launch");
+    s->stepped = true;
+    return MPM_OK;
+}
+
+mpm_status mpm_sync(mpm_sim* s)
+{
+    if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
+    return check_device_errors(s);
+}
+
+mpm_status mpm_step(mpm_sim* s, int64_t nsteps, double dt, double t_end)
+{
+    mpm_status st = mpm_step_async(s, nsteps, dt, t_end);
+    if (st != MPM_OK) return st;
+    return check_device_errors(s);
+}
+
+int64_t mpm_field_size(const mpm_sim* s, int field)
+{
+    if (!s) return -1;
+    const int d = s->G.dim;
+    switch (field) {
+    case MPM_FIELD_X: case MPM_FIELD_V: return d * s->np;
+    case MPM_FIELD_M: case MPM_FIELD_RHO: case MPM_FIELD_E: case MPM_FIELD_P: case MPM_FIELD_Q:
+    case MPM_FIELD_ID: case MPM_FIELD_KEY: return s->np;
+    case MPM_FIELD_CELLSTART: return s->G.nkey + 1;
+    case MPM_FIELD_GRID_M: return s->G.nnode;
+    case MPM_FIELD_GRID_MV: case MPM_FIELD_GRID_F: case MPM_FIELD_GRID_MV2: return d * s->G.nnode;
+    case MPM_FIELD_CLOCK: return 3;
+    }
+    return -1;
+}
+
+static mpm_status read_real(mpm_sim* s, const void* src, int64_t n, double* out)
+{
+    if (n == 0) return MPM_OK;
+    if (s->rsize == 8) {
+        CK(cudaMemcpyAsync(out, src, n * 8, cudaMemcpyDeviceToHost, s->stream), "read");
+        CK(cudaStreamSynchronize(s->stream), "synchronize");
+        return MPM_OK;
+    }
+    std::vector<float> t(n);
+    CK(cudaMemcpyAsync(t.data(), src, n * 4, cudaMemcpyDeviceToHost, s->stream), "read");
+    CK(cudaStreamSynchronize(s->stream), "synchronize");
+    for (int64_t i = 0; i < n; ++i) out[i] = (double)t[i];
+    return MPM_OK;
+}
+
+static mpm_status read_u32(mpm_sim* s, const uint32_t* src, int64_t n, double* out)
+{
+    std::vector<uint32_t> t(n);
+    if (n) {
+        CK(cudaMemcpyAsync(t.data(), src, n * 4, cudaMemcpyDeviceToHost, s->stream), "read");
+        CK(cudaStreamSynchronize(s->stream), "synchronize");
+    }
+    for (int64_t i = 0; i < n; ++i) out[i] = (double)t[i];
+    return MPM_OK;
+}
+
+mpm_status mpm_read_state(mpm_sim* s, int field, double* out, int64_t count)
+{
+    if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
+    if (!out) return fail(s, MPM_EINVAL, "out is NULL");
+    const int64_t need = mpm_field_size(s, field);
+    if (need < 0) return fail(s, MPM_EINVAL, "unknown field");
+    if (count < need) return fail(s, MPM_EINVAL, "output buffer too short");
+    mpm_status st = check_device_errors(s);
+    if (st != MPM_OK) return st;
+    const Buffers& b = s->buf[s->cur];
+    const int d = s->G.dim;
+    const int64_t np = s->np, nn = s->G.nnode;
+    switch (field) {
+    case MPM_FIELD_X:
+        for (int a = 0; a < d; ++a) if ((st = read_real(s, b.x[a], np, out + a * np))) return st;
+        return MPM_OK;
+    case MPM_FIELD_V:
+        for (int a = 0; a < d; ++a) if ((st = read_real(s, b.v[a], np, out + a * np))) return st;
+        return MPM_OK;
+    case MPM_FIELD_M: return read_real(s, b.M, np, out);
+    case MPM_FIELD_RHO: return read_real(s, b.rho, np, out);
+    case MPM_FIELD_E: return read_real(s, b.E, np, out);
+    case MPM_FIELD_Q: return read_real(s, b.Q, np, out);
+    case MPM_FIELD_P: {
+        std::vector<double> r(np);
+        if ((st = read_real(s, b.rho, np, r.data()))) return st;
+        if ((st = read_real(s, b.E, np, out))) return st;
+        for (int64_t k = 0; k < np; ++k) out[k] = (s->G.gamma - 1.0) * r[k] * out[k];
+        return MPM_OK;
+    }
+    case MPM_FIELD_ID: return read_u32(s, b.id, np, out);
+    case MPM_FIELD_KEY: return read_u32(s, b.key, np, out);
+    case MPM_FIELD_CELLSTART: return read_u32(s, s->cellstart, s->G.nkey + 1, out);
+    case MPM_FIELD_CLOCK: {
+        Clock c;
+        CK(cudaMemcpyAsync(&c, s->clk, sizeof(Clock), cudaMemcpyDeviceToHost, s->stream), "read clock");
+        CK(cudaStreamSynchronize(s->stream), "synchronize");
+        out[0] = c.t;
+        out[1] = c.dt_next;
+        out[2] = (double)c.step;
+        if (!s->started) {
+            double dt0 = 0.0;
+            if ((st = mpm_cfl_dt(s, &dt0))) return st;
+            out[1] = dt0;
+        }
+        return MPM_OK;
+    }
+    default: break;
+    }
+    // grid fields
+    int64_t off = 0, cnt = nn;
+    if (field == MPM_FIELD_GRID_M) { off = 0; cnt = nn; }
+    else if (field == MPM_FIELD_GRID_MV) { off = nn; cnt = d * nn; }
+    else if (field == MPM_FIELD_GRID_F) { off = (1 + d) * nn; cnt = d * nn; }
+    else { off = (1 + 2 * d) * nn; cnt = d * nn; }
+    if (s->cfg.precision == MPM_FP32_FIXED64) {
+        std::vector<long long> t(cnt);
+        CK(cudaMemcpyAsync(t.data(), (long long*)s->grid + off, cnt * 8, cudaMemcpyDeviceToHost, s->stream), "read");
+        CK(cudaStreamSynchronize(s->stream), "synchronize");
+        const int kind = field == MPM_FIELD_GRID_M ? 0 : field == MPM_FIELD_GRID_F ? 2 : 1;
+        const double u = s->cfg.fixed_unit[kind] > 0.0 ? s->cfg.fixed_unit[kind] : 1.0;
+        for (int64_t i = 0; i < cnt; ++i) out[i] = (double)t[i] * (u / 4294967296.0);
+        return MPM_OK;
+    }
+    return read_real(s, (char*)s->grid + off * s->asize, cnt, out);
+}
+
+mpm_status mpm_read_grid_fixed(mpm_sim* s, int field, int64_t* out, int64_t count)
+{
+    if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
+    if (s->cfg.precision != MPM_FP32_FIXED64) return fail(s, MPM_EINVAL, "not a fixed-point simulation");
+    if (!out || field < MPM_FIELD_GRID_M || field > MPM_FIELD_GRID_MV2) return fail(s, MPM_EINVAL, "bad field");
+    const int64_t need = mpm_field_size(s, field);
+    if (count < need) return fail(s, MPM_EINVAL, "output buffer too short");
+    const int d = s->G.dim;
+    const int64_t nn = s->G.nnode;
+    int64_t off = field == MPM_FIELD_GRID_M ? 0 : field == MPM_FIELD_GRID_MV ? nn
+                : field == MPM_FIELD_GRID_F ? (1 + d) * nn : (1 + 2 * d) * nn;
+    CK(cudaMemcpyAsync(out, (long long*)s->grid + off, need * 8, cudaMemcpyDeviceToHost, s->stream), "read");
+    CK(cudaStreamSynchronize(s->stream), "synchronize");
+    return MPM_OK;
+}
+
+mpm_status mpm_conservation(mpm_sim* s, double out[5])
+{
+    if (!s || !out) return fail(s, MPM_EINVAL, "NULL argument");
+    if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
+    mpm_status st = check_device_errors(s);
+    if (st != MPM_OK) return st;
+    if (s->np == 0) { for (int i = 0; i < 5; ++i) out[i] = 0.0; return MPM_OK; }
+    s->vt->cons(s, s->stream);
+    CK(cudaGetLastError(), "launch");
+    double t[5];
+    CK(cudaMemcpyAsync(t, s->cons_out, sizeof(t), cudaMemcpyDeviceToHost, s->stream), "read");
+    CK(cudaStreamSynchronize(s->stream), "synchronize");
+    for (int i = 0; i < 5; ++i) out[i] = t[i];
+    if (s->G.dim == 2) out[4] = 0.0;
+    return MPM_OK;
+}
+
+mpm_status mpm_sizes(const mpm_sim* s, int64_t out[4])
+{
+    if (!s || !out) return MPM_EINVAL;
+    Clock c;
+    memset(&c, 0, sizeof(c));
+    if (cudaMemcpyAsync(&c, s->clk, sizeof(Clock), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        cudaGetLastError();
+    out[0] = s->np;
+    out[1] = s->G.nnode;
+    out[2] = s->G.nkey;
+    out[3] = c.step;
+    return MPM_OK;
+}
+
+mpm_status mpm_profile(mpm_sim* s, int enable)
+{
+    if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    s->profiling = enable != 0;
+    return MPM_OK;
+}
+
+mpm_status mpm_profile_read(mpm_sim* s, double out[8], int64_t counts[8], int reset)
+{
+    if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    mpm_status st = collect_profile(s);
+    if (st != MPM_OK) return st;
+    // launches per phase of one step, times the profiled steps
+    for (int i = 0; i < 8; ++i) {
+        if (out) out[i] = s->prof_ms[i];
+        if (counts) counts[i] = s->prof_launch[i];
+    }
+    if (counts) {
+        // per-step launch counts of each phase (fixed by the configuration)
+        counts[0] = 2;   // zero + P2G
+        counts[1] = 1;
+        counts[2] = 1;
+        counts[3] = 1;   // finalize (prepare counted with the step)
+        counts[4] = 5 * (int64_t)s->radix_passes + 2;
+        counts[6] = s->launches;
+    }
+    if (reset) {
+        for (int i = 0; i < 8; ++i) { s->prof_ms[i] = 0.0; s->prof_launch[i] = 0; }
+    }
+    return MPM_OK;
+}
+
+void* mpm_stream(const mpm_sim* s) { return s ? (void*)s->stream : nullptr; }
+
+const char* mpm_last_error(const mpm_sim* s)
+{
+    return s ? s->err.c_str() : g_static_err.c_str();
+}
+
+void mpm_destroy(mpm_sim* s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    drop_graphs(s);
+    for (auto& ps : s->prof)
+        for (int k = 0; k <= kPhases; ++k) cudaEventDestroy(ps.ev[k]);
+    for (auto e : s->ev_pool) cudaEventDestroy(e);
+    std::vector<void*> a = s->allocs;
+    for (void* p : a) dfree(s, p);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    cudaGetLastError();
+    delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,810 @@
+// mpm_kernels.cuh -- sm_103a kernels of one MPM time step (Sec. 3, Algorithm 1).
+//
+// The particles are kept in key order, so the particles of one tile of spans
+// are contiguous.  Each kernel below gives one CTA one tile: the CTA stages
+// the tile's node window (tile + p halo nodes per axis) in shared memory,
+// works on the tile's particles from there, and touches global node memory
+// once per window node.
+//   k_p2g       steps ii   : P2G of m and M V, P2GD of (P+Q) M/rho
+//   k_grid_g2p  steps iii-vi: BC + momentum update at window load, G2P of f/m,
+//                             V' = V + dt A, momentum P2G of M V'
+//   k_g2pd      steps vii-x: BC on the new momentum, G2PD div V, E/rho/P/Q
+//                             update, move with Vbar, recycling, new key
+//   k_finalize  step xiii  : time advance and the CFL step for the next step
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mpm {
+
+enum : int { ERR_NONFINITE = 1, ERR_CFL = 2, ERR_TILE = 4 };
+
+struct Geom {
+    int dim, p;
+    int n[3], per[3], S[3], N[3], g[3], T[3], nt[3], W[3];
+    int Tvol, Wvol, ntiles;
+    int64_t nnode, nkey;
+    int bc[6];
+    int inflow_face;                // -1: none
+    double h, inv_h, lo[3], hi[3];
+    double gamma, c0, c1, cfl, inflow_rho, inflow_p, inflow_v[3], inflow_e;
+    uint64_t seed;
+    float qscale[3];                // fixed point: 2^32 / unit (mass, momentum, force)
+    float dqscale[3];               // unit / 2^32
+};
+
+struct Clock {
+    double t, t_end, dt_fixed, dt_next, dt_cur;
+    long long step;
+    int active, done, last, err;
+    unsigned vmax_bits, cmax_bits;
+    int pad[2];
+};
+
+template <class R>
+struct Particles {
+    R* x[3];
+    R* v[3];
+    R* M;
+    R* rho;
+    R* E;
+    R* Q;
+    uint32_t* id;
+    uint32_t* key;
+};
+
+template <class A, class R>
+struct Grid {
+    A* m;
+    A* mv[3];
+    A* f[3];
+    A* mv2[3];
+    const uint8_t* mask;
+    const R* nrm[3];
+};
+
+// ----------------------------------------------------- rounding-exact ops
+template <class R> struct Op;
+template <> struct Op<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float dvd(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float sqr(float a) { return __fsqrt_rn(a); }
+    static __device__ __forceinline__ float flr(float a) { return floorf(a); }
+};
+template <> struct Op<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double dvd(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double sqr(double a) { return __dsqrt_rn(a); }
+    static __device__ __forceinline__ double flr(double a) { return floor(a); }
+};
+
+// ---------------------------------------------------- accumulator types
+template <class A> struct Acc;
+template <> struct Acc<float> {
+    static __device__ __forceinline__ float from(float c, float) { return c; }
+    static __device__ __forceinline__ void add(float* p, float v) { atomicAdd(p, v); }
+    static __device__ __forceinline__ float to_real(float a, float) { return a; }
+};
+template <> struct Acc<double> {
+    static __device__ __forceinline__ double from(double c, float) { return c; }
+    static __device__ __forceinline__ void add(double* p, double v) { atomicAdd(p, v); }
+    static __device__ __forceinline__ double to_real(double a, float) { return a; }
+};
+template <> struct Acc<long long> {
+    // Fixed point: a binary32 contribution c becomes round(c * 2^32/U).
+    static __device__ __forceinline__ long long from(float c, float s) { return __float2ll_rn(__fmul_rn(c, s)); }
+    static __device__ __forceinline__ void add(long long* p, long long v)
+    {
+        atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+    }
+    static __device__ __forceinline__ float to_real(long long a, float ds) { return __fmul_rn(__ll2float_rn(a), ds); }
+};
+
+// --------------------------------------------------------------- basis
+
+template <class R>
+struct AxisSup {
+    int l;          // local span inside the tile, or < 0 if the particle is not in it
+    int c;          // unwrapped span
+    R w[3], dw[3];  // weights and d/dxi of the p+1 support nodes
+};
+
+// Span of coordinate x along axis a evaluated in the storage precision R with
+// one rounding per operation: xi = (x - lo) * (1/h); c = floor(xi [+ 1/2]).
+template <class R, int P>
+__device__ __forceinline__ int span_of(const Geom& G, int a, R x, R& xi)
+{
+    typedef Op<R> O;
+    xi = O::mul(O::sub(x, (R)G.lo[a]), (R)G.inv_h);
+    R s = (P == 2) ? O::add(xi, (R)0.5) : xi;
+    int c = (int)O::flr(s);
+    if (!G.per[a]) c = min(max(c, 0), G.S[a] - 1);
+    return c;
+}
+
+__device__ __forceinline__ int wrap_span(const Geom& G, int a, int c)
+{
+    if (!G.per[a]) return c;
+    int r = c % G.n[a];
+    return r < 0 ? r + G.n[a] : r;
+}
+
+template <class R, int P>
+__device__ __forceinline__ void axis_support(const Geom& G, int a, R x, int tile_span0, AxisSup<R>& s)
+{
+    typedef Op<R> O;
+    R xi;
+    int c = span_of<R, P>(G, a, x, xi);
+    s.c = c;
+    int b = c - (P == 2 ? 1 : 0);
+    R fx = O::sub(xi, (R)b);
+    if (P == 2) {
+        R t0 = O::sub((R)1.5, fx), t1 = O::sub(fx, (R)1.0), t2 = O::sub(fx, (R)0.5);
+        s.w[0] = O::mul(O::mul(t0, t0), (R)0.5);
+        s.w[1] = O::sub((R)0.75, O::mul(t1, t1));
+        s.w[2] = O::mul(O::mul(t2, t2), (R)0.5);
+        s.dw[0] = -t0;
+        s.dw[1] = O::mul((R)-2.0, t1);
+        s.dw[2] = t2;
+    } else {
+        s.w[0] = O::sub((R)1.0, fx);
+        s.w[1] = fx;
+        s.w[2] = (R)0;
+        s.dw[0] = (R)-1.0;
+        s.dw[1] = (R)1.0;
+        s.dw[2] = (R)0;
+    }
+    int l = wrap_span(G, a, c) - tile_span0;
+    s.l = (l >= 0 && l < G.T[a]) ? l : -1;
+}
+
+__device__ __forceinline__ void tile_origin(const Geom& G, int tile, int so[3])
+{
+    int tx = tile % G.nt[0];
+    int ty = (tile / G.nt[0]) % G.nt[1];
+    int tz = tile / (G.nt[0] * G.nt[1]);
+    so[0] = tx * G.T[0];
+    so[1] = ty * G.T[1];
+    so[2] = tz * G.T[2];
+}
+
+// Storage index of window slot w of the tile whose first span is so[], or -1.
+template <int P>
+__device__ __forceinline__ int64_t slot_node(const Geom& G, const int so[3], int w, int idx[3])
+{
+    int ws[3];
+    ws[0] = w % G.W[0];
+    ws[1] = (w / G.W[0]) % G.W[1];
+    ws[2] = w / (G.W[0] * G.W[1]);
+    for (int a = 0; a < 3; ++a) {
+        if (a >= G.dim) { idx[a] = 0; continue; }
+        int i = so[a] + ws[a];
+        if (G.per[a]) {
+            i -= (P == 2 ? 1 : 0);
+            i %= G.n[a];
+            if (i < 0) i += G.n[a];
+        } else if (i >= G.N[a]) {
+            return -1;
+        }
+        idx[a] = i;
+    }
+    return ((int64_t)idx[2] * G.N[1] + idx[1]) * G.N[0] + idx[0];
+}
+
+// Grid boundary conditions of one node (Sec. 3 steps iii and vii): obstacle
+// projection (eqs. normali1/normali2) on a masked node, then the domain
+// faces -- slip wall: normal component 0; inflow: m v_in (momentum) or 0
+// (force).  kind 0 = momentum, 1 = force.
+template <class R, int D>
+__device__ __forceinline__ void node_bc(const Geom& G, const uint8_t* mask, const R* const* nrm, int64_t node,
+                                        const int idx[3], R m, R* vec, int kind)
+{
+    typedef Op<R> O;
+    if (mask && mask[node]) {
+        R n[3], xn = (R)0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            n[a] = nrm[a][node];
+            xn = O::add(xn, O::mul(vec[a], n[a]));
+        }
+        R c = O::mul((R)0.5, O::sub(xn, fabs(xn)));
+#pragma unroll
+        for (int a = 0; a < D; ++a) vec[a] = O::sub(vec[a], O::mul(c, n[a]));
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        if (G.per[a]) continue;
+        int phys = idx[a] - G.g[a];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            bool on = side == 0 ? (phys <= 0) : (phys >= G.n[a]);
+            if (!on) continue;
+            int bc = G.bc[2 * a + side];
+            if (bc == 0) {
+                vec[a] = (R)0;
+            } else if (bc == 2) {
+#pragma unroll
+                for (int b = 0; b < D; ++b) vec[b] = kind == 0 ? O::mul(m, (R)G.inflow_v[b]) : (R)0;
+            }
+        }
+    }
+}
+
+template <class R>
+__device__ __forceinline__ uint32_t key_of(const Geom& G, const int sp[3])
+{
+    int t = 0, l = 0;
+    t = ((sp[2] / G.T[2]) * G.nt[1] + sp[1] / G.T[1]) * G.nt[0] + sp[0] / G.T[0];
+    l = ((sp[2] % G.T[2]) * G.T[1] + sp[1] % G.T[1]) * G.T[0] + sp[0] % G.T[0];
+    return (uint32_t)t * (uint32_t)G.Tvol + (uint32_t)l;
+}
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+    // Salmon et al. (SC'11): ten rounds, multipliers 0xD2511F53/0xCD9E8D57,
+    // Weyl key increments 0x9E3779B9/0xBB67AE85.
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned* p, float v)
+{
+    if (v > 0.f) atomicMax(p, __float_as_uint(v));
+}
+
+// ------------------------------------------------------------------ P2G
+
+// Weights of support node (kx, ky, kz) in the documented binary32 order.
+template <class R, int D>
+__device__ __forceinline__ void node_weights(const AxisSup<R>* s, int kx, int ky, int kz, R& w, R g[3])
+{
+    typedef Op<R> O;
+    if (D == 3) {
+        R yz = O::mul(s[1].w[ky], s[2].w[kz]);
+        R dyz = O::mul(s[1].dw[ky], s[2].w[kz]);
+        R ydz = O::mul(s[1].w[ky], s[2].dw[kz]);
+        w = O::mul(s[0].w[kx], yz);
+        g[0] = O::mul(s[0].dw[kx], yz);
+        g[1] = O::mul(s[0].w[kx], dyz);
+        g[2] = O::mul(s[0].w[kx], ydz);
+    } else {
+        w = O::mul(s[0].w[kx], s[1].w[ky]);
+        g[0] = O::mul(s[0].dw[kx], s[1].w[ky]);
+        g[1] = O::mul(s[0].w[kx], s[1].dw[ky]);
+        g[2] = (R)0;
+    }
+}
+
+template <int D, int P, class R, class A>
+__global__ void __launch_bounds__(256) k_p2g(Geom G, Particles<R> pt, Grid<A, R> gr, const uint32_t* cellstart,
+                                             Clock* clk)
+{
+    typedef Op<R> O;
+    if (!clk->active) return;
+    const int tile = blockIdx.x;
+    const uint32_t beg = cellstart[(int64_t)tile * G.Tvol];
+    const uint32_t end = cellstart[(int64_t)(tile + 1) * G.Tvol];
+    if (beg == end) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    A* s = reinterpret_cast<A*>(smem_raw);
+    const int W = G.Wvol;
+    const int NF = 1 + 2 * D;
+    for (int i = threadIdx.x; i < NF * W; i += blockDim.x) s[i] = A(0);
+    __syncthreads();
+    int so[3];
+    tile_origin(G, tile, so);
+    const R gm1 = (R)(G.gamma - 1.0), ih = (R)G.inv_h;
+    constexpr int NS = P + 1;
+    for (uint32_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
+        AxisSup<R> sx[3];
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            axis_support<R, P>(G, a, pt.x[a][k], so[a], sx[a]);
+            ok = ok && sx[a].l >= 0;
+        }
+        if (!ok) { atomicOr(&clk->err, ERR_TILE); continue; }
+        if (D == 2) { sx[2].l = 0; sx[2].w[0] = (R)1; sx[2].dw[0] = (R)0; }
+        const R M = pt.M[k], rho = pt.rho[k];
+        const R Pk = O::mul(O::mul(gm1, rho), pt.E[k]);
+        const R vol = O::dvd(M, rho);
+        const R F = O::mul(O::mul(O::add(Pk, pt.Q[k]), vol), ih);
+        R MV[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) MV[a] = O::mul(M, pt.v[a][k]);
+#pragma unroll
+        for (int kz = 0; kz < (D == 3 ? NS : 1); ++kz)
+#pragma unroll
+            for (int ky = 0; ky < NS; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < NS; ++kx) {
+                    R w, g[3];
+                    node_weights<R, D>(sx, kx, ky, kz, w, g);
+                    const int slot = ((sx[2].l + kz) * G.W[1] + sx[1].l + ky) * G.W[0] + sx[0].l + kx;
+                    Acc<A>::add(&s[slot], Acc<A>::from(O::mul(M, w), G.qscale[0]));
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        Acc<A>::add(&s[(1 + a) * W + slot], Acc<A>::from(O::mul(MV[a], w), G.qscale[1]));
+                        Acc<A>::add(&s[(1 + D + a) * W + slot], Acc<A>::from(O::mul(F, g[a]), G.qscale[2]));
+                    }
+                }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        int idx[3];
+        int64_t node = slot_node<P>(G, so, i, idx);
+        if (node < 0) continue;
+        A v = s[i];
+        if (v != A(0)) Acc<A>::add(&gr.m[node], v);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            v = s[(1 + a) * W + i];
+            if (v != A(0)) Acc<A>::add(&gr.mv[a][node], v);
+            v = s[(1 + D + a) * W + i];
+            if (v != A(0)) Acc<A>::add(&gr.f[a][node], v);
+        }
+    }
+}
+
+// ----------------------------------------------- grid update + G2P + P2G
+
+template <int D, int P, class R, class A>
+__global__ void __launch_bounds__(256) k_grid_g2p(Geom G, Particles<R> pt, Grid<A, R> gr,
+                                                  const uint32_t* cellstart, Clock* clk)
+{
+    typedef Op<R> O;
+    if (!clk->active) return;
+    const int tile = blockIdx.x;
+    const uint32_t beg = cellstart[(int64_t)tile * G.Tvol];
+    const uint32_t end = cellstart[(int64_t)(tile + 1) * G.Tvol];
+    if (beg == end) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = G.Wvol;
+    R* sA = reinterpret_cast<R*>(smem_raw);                       // D x W: f/m after BC
+    // D x W momentum P2G accumulators, 16-byte aligned (8-byte atomics)
+    A* s2 = reinterpret_cast<A*>(smem_raw + ((sizeof(R) * D * W + 15) & ~size_t(15)));
+    int so[3];
+    tile_origin(G, tile, so);
+    const R dt = (R)clk->dt_cur;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        int idx[3];
+        int64_t node = slot_node<P>(G, so, i, idx);
+        R f[3] = {(R)0, (R)0, (R)0};
+        R m = (R)0;
+        if (node >= 0) {
+            m = Acc<A>::to_real(gr.m[node], G.dqscale[0]);
+#pragma unroll
+            for (int a = 0; a < D; ++a) f[a] = Acc<A>::to_real(gr.f[a][node], G.dqscale[2]);
+            node_bc<R, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            sA[a * W + i] = (m != (R)0) ? O::dvd(f[a], m) : (R)0;
+            s2[a * W + i] = A(0);
+        }
+    }
+    __syncthreads();
+    constexpr int NS = P + 1;
+    float vmax = 0.f;
+    for (uint32_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
+        AxisSup<R> sx[3];
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            axis_support<R, P>(G, a, pt.x[a][k], so[a], sx[a]);
+            ok = ok && sx[a].l >= 0;
+        }
+        if (!ok) { atomicOr(&clk->err, ERR_TILE); continue; }
+        if (D == 2) { sx[2].l = 0; sx[2].w[0] = (R)1; sx[2].dw[0] = (R)0; }
+        R acc[3] = {(R)0, (R)0, (R)0};
+#pragma unroll
+        for (int kz = 0; kz < (D == 3 ? NS : 1); ++kz)
+#pragma unroll
+            for (int ky = 0; ky < NS; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < NS; ++kx) {
+                    R w, g[3];
+                    node_weights<R, D>(sx, kx, ky, kz, w, g);
+                    const int slot = ((sx[2].l + kz) * G.W[1] + sx[1].l + ky) * G.W[0] + sx[0].l + kx;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) acc[a] = O::add(acc[a], O::mul(w, sA[a * W + slot]));
+                }
+        const R M = pt.M[k];
+        R MV[3], v2 = (R)0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            R vn = O::add(pt.v[a][k], O::mul(dt, acc[a]));
+            pt.v[a][k] = vn;
+            MV[a] = O::mul(M, vn);
+            v2 = O::add(v2, O::mul(vn, vn));
+        }
+        vmax = fmaxf(vmax, (float)O::sqr(v2));
+#pragma unroll
+        for (int kz = 0; kz < (D == 3 ? NS : 1); ++kz)
+#pragma unroll
+            for (int ky = 0; ky < NS; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < NS; ++kx) {
+                    R w, g[3];
+                    node_weights<R, D>(sx, kx, ky, kz, w, g);
+                    const int slot = ((sx[2].l + kz) * G.W[1] + sx[1].l + ky) * G.W[0] + sx[0].l + kx;
+#pragma unroll
+                    for (int a = 0; a < D; ++a)
+                        Acc<A>::add(&s2[a * W + slot], Acc<A>::from(O::mul(MV[a], w), G.qscale[1]));
+                }
+    }
+    // block max of |V'| for the CFL rule
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&clk->vmax_bits, vmax);
+    __syncthreads();
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        int idx[3];
+        int64_t node = slot_node<P>(G, so, i, idx);
+        if (node < 0) continue;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            A v = s2[a * W + i];
+            if (v != A(0)) Acc<A>::add(&gr.mv2[a][node], v);
+        }
+    }
+}
+
+// ------------------------------------ G2PD + particle update + move + key
+
+template <int D, int P, class R, class A>
+__global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R> gr, const uint32_t* cellstart,
+                                              Clock* clk)
+{
+    typedef Op<R> O;
+    if (!clk->active) return;
+    const int tile = blockIdx.x;
+    const uint32_t beg = cellstart[(int64_t)tile * G.Tvol];
+    const uint32_t end = cellstart[(int64_t)(tile + 1) * G.Tvol];
+    if (beg == end) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = G.Wvol;
+    R* sVb = reinterpret_cast<R*>(smem_raw);   // D x W: mv'/m
+    R* sV2 = sVb + D * W;                       // D x W: mv2/m after BC
+    int so[3];
+    tile_origin(G, tile, so);
+    const R dt = (R)clk->dt_cur;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        int idx[3];
+        int64_t node = slot_node<P>(G, so, i, idx);
+        R mv[3] = {(R)0, (R)0, (R)0}, f[3] = {(R)0, (R)0, (R)0}, m2[3] = {(R)0, (R)0, (R)0};
+        R m = (R)0;
+        if (node >= 0) {
+            m = Acc<A>::to_real(gr.m[node], G.dqscale[0]);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                mv[a] = Acc<A>::to_real(gr.mv[a][node], G.dqscale[1]);
+                f[a] = Acc<A>::to_real(gr.f[a][node], G.dqscale[2]);
+                m2[a] = Acc<A>::to_real(gr.mv2[a][node], G.dqscale[1]);
+            }
+            node_bc<R, D>(G, gr.mask, gr.nrm, node, idx, m, mv, 0);
+            node_bc<R, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
+            node_bc<R, D>(G, gr.mask, gr.nrm, node, idx, m, m2, 0);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            R mvp = O::add(mv[a], O::mul(dt, f[a]));
+            sVb[a * W + i] = (m != (R)0) ? O::dvd(mvp, m) : (R)0;
+            sV2[a * W + i] = (m != (R)0) ? O::dvd(m2[a], m) : (R)0;
+        }
+    }
+    __syncthreads();
+    constexpr int NS = P + 1;
+    const R gm1 = (R)(G.gamma - 1.0), gam = (R)G.gamma, ih = (R)G.inv_h, hh = (R)G.h;
+    const R c0 = (R)G.c0, c1 = (R)G.c1;
+    float vmax = 0.f, cmax = 0.f;
+    int err = 0;
+    for (uint32_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
+        AxisSup<R> sx[3];
+        bool ok = true;
+        R x[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            x[a] = pt.x[a][k];
+            axis_support<R, P>(G, a, x[a], so[a], sx[a]);
+            ok = ok && sx[a].l >= 0;
+        }
+        if (!ok) { err |= ERR_TILE; continue; }
+        if (D == 2) { sx[2].l = 0; sx[2].w[0] = (R)1; sx[2].dw[0] = (R)0; }
+        R vb[3] = {(R)0, (R)0, (R)0}, dv = (R)0;
+#pragma unroll
+        for (int kz = 0; kz < (D == 3 ? NS : 1); ++kz)
+#pragma unroll
+            for (int ky = 0; ky < NS; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < NS; ++kx) {
+                    R w, g[3];
+                    node_weights<R, D>(sx, kx, ky, kz, w, g);
+                    const int slot = ((sx[2].l + kz) * G.W[1] + sx[1].l + ky) * G.W[0] + sx[0].l + kx;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        vb[a] = O::add(vb[a], O::mul(w, sVb[a * W + slot]));
+                        dv = O::add(dv, O::mul(g[a], sV2[a * W + slot]));
+                    }
+                }
+        dv = O::mul(dv, ih);   // node weights are per unit xi
+        // step viii: energy, density, pressure, artificial viscosity
+        const R rho = pt.rho[k], E = pt.E[k], Q = pt.Q[k];
+        const R Pk = O::mul(O::mul(gm1, rho), E);
+        const R En = O::add(E, O::mul(O::mul(dt, -O::dvd(O::add(Pk, Q), rho)), dv));
+        const R den = O::add((R)1, O::mul(dt, dv));
+        if (!(den > (R)0)) { err |= ERR_NONFINITE; continue; }
+        const R rn = O::dvd(rho, den);
+        const R Pn = O::mul(O::mul(gm1, rn), En);
+        R c2 = O::dvd(O::mul(gam, Pn), rn);
+        const R cs = O::sqr(c2 > (R)0 ? c2 : (R)0);
+        R Qn = (R)0;
+        if (dv < (R)0) {
+            R t1 = O::mul(O::mul(rn, hh), dv);
+            Qn = O::sub(O::mul(O::mul(c0, t1), t1), O::mul(O::mul(O::mul(c1, hh), cs), dv));
+        }
+        // step ix: move with Vbar; step x: connectivity (wrap, hold, recycle)
+        R xn[3];
+        R vb2 = (R)0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            xn[a] = O::add(x[a], O::mul(dt, vb[a]));
+            vb2 = O::add(vb2, O::mul(vb[a], vb[a]));
+        }
+        bool out = false;
+        bool fin = isfinite(En) && isfinite(rn) && isfinite(Qn);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            fin = fin && isfinite(xn[a]);
+            R xi;
+            int c_new = span_of<R, P>(G, a, xn[a], xi);
+            int d = c_new - sx[a].c;
+            if (d < -1 || d > 1) err |= ERR_CFL;
+            if (!G.per[a]) {
+                if (xn[a] < (R)G.lo[a] && G.bc[2 * a] == 3) out = true;
+                if (xn[a] >= (R)G.hi[a] && G.bc[2 * a + 1] == 3) out = true;
+            }
+        }
+        if (!fin) { err |= ERR_NONFINITE; continue; }
+        R En_s = En, rn_s = rn, Qn_s = Qn;
+        float cpart = (float)cs;
+        if (out && G.inflow_face >= 0) {
+            uint32_t id = pt.id[k];
+            unsigned long long st = (unsigned long long)clk->step;
+            uint32_t c[4] = {(uint32_t)st, (uint32_t)(st >> 32), id, 0u};
+            philox4x32_10(c, (uint32_t)G.seed, (uint32_t)(G.seed >> 32));
+            const int af = G.inflow_face / 2, side = G.inflow_face % 2;
+            R vin2 = (R)0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                R u = O::mul((R)(c[a] >> 8), (R)(1.0 / 16777216.0));
+                if (a == af)
+                    xn[a] = side == 0 ? O::add((R)G.lo[a], O::mul(u, hh))
+                                      : O::add(O::sub((R)G.hi[a], hh), O::mul(u, hh));
+                else
+                    xn[a] = O::add((R)G.lo[a], O::mul(u, O::sub((R)G.hi[a], (R)G.lo[a])));
+                pt.v[a][k] = (R)G.inflow_v[a];
+                vin2 = O::add(vin2, O::mul((R)G.inflow_v[a], (R)G.inflow_v[a]));
+            }
+            En_s = (R)G.inflow_e;
+            rn_s = (R)G.inflow_rho;
+            Qn_s = (R)0;
+            R ci2 = O::dvd(O::mul(gam, O::mul(O::mul(gm1, rn_s), En_s)), rn_s);
+            cpart = (float)O::sqr(ci2 > (R)0 ? ci2 : (R)0);
+            vmax = fmaxf(vmax, (float)O::sqr(vin2));
+        } else {
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const R lo = (R)G.lo[a], hi = (R)G.hi[a];
+                if (G.per[a]) {
+                    const R L = O::sub(hi, lo);
+                    if (xn[a] < lo) xn[a] = O::add(xn[a], L);
+                    else if (xn[a] >= hi) xn[a] = O::sub(xn[a], L);
+                } else {
+                    if (xn[a] < lo) xn[a] = lo;
+                    if (xn[a] > hi) xn[a] = hi;
+                }
+            }
+        }
+        int sp[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            R xi;
+            sp[a] = wrap_span(G, a, span_of<R, P>(G, a, xn[a], xi));
+            pt.x[a][k] = xn[a];
+        }
+        pt.key[k] = key_of<R>(G, sp);
+        pt.E[k] = En_s;
+        pt.rho[k] = rn_s;
+        pt.Q[k] = Qn_s;
+        vmax = fmaxf(vmax, (float)O::sqr(vb2));
+        cmax = fmaxf(cmax, cpart);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+        err |= __shfl_xor_sync(0xffffffffu, err, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(&clk->vmax_bits, vmax);
+        atomic_max_nonneg(&clk->cmax_bits, cmax);
+        if (err) atomicOr(&clk->err, err);
+    }
+}
+
+// ---------------------------------------------------------- time control
+
+// Decide this step's dt (fixed or CFL) and clip it to t_end (step xiii).
+__global__ void k_prepare(Clock* clk)
+{
+    Clock& c = *clk;
+    if (c.done || c.err) { c.active = 0; return; }
+    double h = c.dt_fixed > 0.0 ? c.dt_fixed : c.dt_next;
+    if (!(h > 0.0)) { c.err |= ERR_NONFINITE; c.active = 0; return; }
+    c.last = 0;
+    if (c.t_end > 0.0 && c.t + h >= c.t_end) { h = c.t_end - c.t; c.last = 1; }
+    c.dt_cur = h;
+    c.active = 1;
+    c.vmax_bits = 0u;
+    c.cmax_bits = 0u;
+}
+
+__global__ void k_finalize(Clock* clk, double cfl_h)
+{
+    Clock& c = *clk;
+    if (!c.active) return;
+    c.t = c.last ? c.t_end : c.t + c.dt_cur;
+    c.step += 1;
+    const double v = (double)__uint_as_float(c.vmax_bits), cs = (double)__uint_as_float(c.cmax_bits);
+    c.dt_next = (v + cs) > 0.0 ? cfl_h / (v + cs) : 0.0;
+    if (c.last || (c.t_end > 0.0 && c.t >= c.t_end)) c.done = 1;
+}
+
+__global__ void k_set_params(Clock* clk, double dt_fixed, double t_end)
+{
+    Clock& c = *clk;
+    c.dt_fixed = dt_fixed;
+    if (t_end != c.t_end) {
+        c.t_end = t_end;
+        c.done = (t_end > 0.0 && c.t >= t_end) ? 1 : 0;
+    }
+}
+
+// Initial CFL maxima over the particle state (Vbar := V before the first step).
+template <int D, class R>
+__global__ void k_cfl_init(Geom G, Particles<R> pt, int64_t n, Clock* clk)
+{
+    typedef Op<R> O;
+    float vmax = 0.f, cmax = 0.f;
+    const R gm1 = (R)(G.gamma - 1.0), gam = (R)G.gamma;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        R v2 = (R)0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) v2 = O::add(v2, O::mul(pt.v[a][k], pt.v[a][k]));
+        vmax = fmaxf(vmax, (float)O::sqr(v2));
+        R P = O::mul(O::mul(gm1, pt.rho[k]), pt.E[k]);
+        R c2 = O::dvd(O::mul(gam, P), pt.rho[k]);
+        cmax = fmaxf(cmax, (float)O::sqr(c2 > (R)0 ? c2 : (R)0));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(&clk->vmax_bits, vmax);
+        atomic_max_nonneg(&clk->cmax_bits, cmax);
+    }
+}
+
+__global__ void k_cfl_init_finish(Clock* clk, double cfl_h)
+{
+    Clock& c = *clk;
+    const double v = (double)__uint_as_float(c.vmax_bits), cs = (double)__uint_as_float(c.cmax_bits);
+    c.dt_next = (v + cs) > 0.0 ? cfl_h / (v + cs) : 0.0;
+    c.vmax_bits = 0u;
+    c.cmax_bits = 0u;
+}
+
+// ----------------------------------------------------- keys and gathering
+
+template <int D, int P, class R>
+__global__ void k_keys(Geom G, Particles<R> pt, int64_t n)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int sp[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        R xi;
+        sp[a] = wrap_span(G, a, span_of<R, P>(G, a, pt.x[a][k], xi));
+    }
+    pt.key[k] = key_of<R>(G, sp);
+}
+
+// out[j] = in[perm[j]] for every particle array; identity when inactive.
+template <int D, class R>
+__global__ void k_gather(Particles<R> in, Particles<R> out, const uint32_t* perm, const uint32_t* sorted_keys,
+                         int64_t n, const int* active)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const bool act = active == nullptr || *active;
+    const uint32_t s = act ? perm[j] : (uint32_t)j;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        out.x[a][j] = in.x[a][s];
+        out.v[a][j] = in.v[a][s];
+    }
+    out.M[j] = in.M[s];
+    out.rho[j] = in.rho[s];
+    out.E[j] = in.E[s];
+    out.Q[j] = in.Q[s];
+    out.id[j] = in.id[s];
+    out.key[j] = act ? sorted_keys[j] : in.key[s];
+}
+
+// FP64 sums for the conservation diagnostics: one partial per block,
+// summed by k_cons_final in block order (deterministic).
+template <int D, class R>
+__global__ void __launch_bounds__(256) k_cons_partial(Particles<R> pt, int64_t n, double* partial)
+{
+    __shared__ double sh[5][256];
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double M = (double)pt.M[k], v2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double va = (double)pt.v[a][k];
+            v2 += va * va;
+            s[2 + a] += M * va;
+        }
+        s[0] += M;
+        s[1] += M * ((double)pt.E[k] + 0.5 * v2);
+    }
+    for (int i = 0; i < 5; ++i) sh[i][threadIdx.x] = s[i];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int i = 0; i < 5; ++i) sh[i][threadIdx.x] += sh[i][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 5; ++i) partial[blockIdx.x * 5 + i] = sh[i][0];
+}
+
+__global__ void k_cons_final(const double* partial, int nb, double* out)
+{
+    if (threadIdx.x != 0) return;
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+        for (int i = 0; i < 5; ++i) s[i] += partial[b * 5 + i];
+    for (int i = 0; i < 5; ++i) out[i] = s[i];
+}
+
+// Convert host-side doubles to the storage precision.
+template <class R>
+__global__ void k_from_double(const double* in, R* out, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (R)in[i];
+}
+
+__global__ void k_iota(uint32_t* out, int64_t n, uint32_t base)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = base + (uint32_t)i;
+}
+
+}  // namespace mpm

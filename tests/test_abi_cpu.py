@@ -1,0 +1,47 @@
+"""CPU-only checks of the boundary: the CUDA library builds for sm_103a,
+loads, and exports every entry point include/mpm.h declares; the Python
+binding names the same entry points.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+from paper_2404_17057_b300 import build as B
+from paper_2404_17057_b300 import mpm as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "mpm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpm_[a-z_]+)\s*\(", src)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = B.build()
+    lib = ctypes.CDLL(path)
+    names = declared()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_abi():
+    assert sorted(M.EXPORTS) == declared()
+    L = M.load()
+    for n in M.EXPORTS:
+        assert hasattr(L, n)
+
+
+def test_library_is_built_for_sm_103a():
+    cmd = " ".join(B.ARCH)
+    assert "sm_103a" in cmd and "compute_103a" in cmd
+
+
+def test_null_handles_are_rejected_without_a_device():
+    L = M.load()
+    assert L.mpm_field_size(None, 0) == -1
+    assert L.mpm_sync(None) == 1
+    assert L.mpm_step(None, 1, 0.0, 0.0) == 1
+    assert L.mpm_create(None, None) == 1
+    L.mpm_destroy(None)

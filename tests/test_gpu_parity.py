@@ -1,0 +1,350 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances:
+  * sort permutation, keys, cell starts: bit-exact (both sides evaluate the
+    key in binary32 from the same binary32 positions);
+  * fixed-point P2G: bit-exact int64 sums (same binary32 contribution order);
+  * FP64 GPU path vs FP64 oracle: relative L1 <= 1e-10 (only the order of
+    floating-point sums differs);
+  * FP32 path vs FP64 oracle after 100 steps: relative L1 <= 1e-4 for rho,
+    each velocity component and p (the accuracy target of the method's
+    single-precision path).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2404_17057_b300 import inputs as I
+from paper_2404_17057_b300 import mpm as M
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_sim(p, **kw):
+    return M.Simulation.from_problem(p, **kw)
+
+
+def oracle_sim(p):
+    s = O.OracleSim(p.cfg)
+    s.add_particles(p.x, p.v, p.mass, p.rho, p.e)
+    if p.mask is not None:
+        s.set_obstacle_mask(p.mask, p.normals)
+    return s
+
+
+def by_id(sim, field):
+    ids = sim.read("ID").astype(np.int64)
+    a = sim.read(field)
+    return a[..., np.argsort(ids)]
+
+
+def rel_l1(a, b):
+    d = np.abs(b).sum()
+    return np.abs(a - b).sum() / (d if d > 0 else 1.0)
+
+
+def f32(p):
+    """Round the initial state to binary32 so both sides start identical."""
+    for k in ("x", "v", "mass", "rho", "e"):
+        setattr(p, k, getattr(p, k).astype(np.float32).astype(np.float64))
+    return p
+
+
+def random_problem(dim, degree, n, bc, N, seed, precision, tile=(0, 0, 0)):
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n[0]
+    cfg = I.base_config(dim, n, h, bc, degree=degree, precision=precision, tile=list(tile))
+    L = np.array([n[a] * h for a in range(dim)])[:, None]
+    x = rng.random((dim, N)) * L
+    x = np.minimum(x, L * (1 - 1e-7))
+    p = I.Problem("random", cfg, x, 0.1 * rng.normal(size=(dim, N)), rng.uniform(0.5, 1.5, N) * h ** dim,
+                  rng.uniform(0.8, 1.2, N), rng.uniform(1.5, 2.5, N))
+    return f32(p) if precision != "fp64" else p
+
+
+# ------------------------------------------------------------------ sort
+
+SORT_CASES = [
+    (2, 2, [100, 37], ["wall"] * 4, (16, 16, 0)),
+    (2, 1, [64, 23], ["periodic", "periodic", "wall", "wall"], (8, 4, 0)),
+    (3, 2, [21, 13, 9], ["wall"] * 6, (8, 8, 8)),
+    (3, 1, [12, 10, 7], ["periodic"] * 2 + ["wall"] * 4, (4, 4, 2)),
+]
+
+
+@pytest.mark.parametrize("dim,degree,n,bc,tile", SORT_CASES)
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_sort_permutation_and_cell_starts_bit_exact(dim, degree, n, bc, tile, precision):
+    p = random_problem(dim, degree, n, bc, 20011, 5, precision, tile)
+    sim = gpu_sim(p)
+    ids = sim.read("ID").astype(np.int64)
+    keys = sim.read("KEY").astype(np.int64)
+    start = sim.read("CELLSTART").astype(np.int64)
+    k_or = O.keys(p.cfg, p.x, prec32=(precision != "fp64")).astype(np.int64)
+    perm, st_or = O.stable_sort(k_or, len(start) - 1)
+    assert np.array_equal(ids, perm)
+    assert np.array_equal(keys, k_or[perm])
+    assert np.array_equal(start, st_or)
+    sim.close()
+
+
+def decode_spans(cfg, keys):
+    """Spans of each key from the tile-major numbering (the ABI's definition)."""
+    dim, p = cfg["dim"], cfg["degree"]
+    per = [cfg["bc"][2 * a] == "periodic" for a in range(dim)]
+    T = [cfg["tile"][a] or (8 if dim == 3 else 16) for a in range(dim)] + [1] * (3 - dim)
+    S = [cfg["n"][a] if per[a] else cfg["n"][a] + (1 if p == 2 else 0) for a in range(dim)]
+    nt = [(S[a] + T[a] - 1) // T[a] for a in range(dim)] + [1] * (3 - dim)
+    tv = T[0] * T[1] * T[2]
+    t, l = keys // tv, keys % tv
+    ti = [t % nt[0], (t // nt[0]) % nt[1], t // (nt[0] * nt[1])]
+    li = [l % T[0], (l // T[0]) % T[1], l // (T[0] * T[1])]
+    return [ti[a] * T[a] + li[a] for a in range(dim)]
+
+
+def test_sort_after_steps_is_a_valid_stable_key_order():
+    """After steps the particles are a permutation in non-decreasing key
+    order, every key's span holds its particle, and the cell starts are the
+    key histogram's prefix sums."""
+    p = I.cylinder(nx=96, ny=48, radius=0.1, seed=2)
+    sim = gpu_sim(p)
+    sim.step(20)
+    x = sim.read("X")
+    keys = sim.read("KEY").astype(np.int64)
+    start = sim.read("CELLSTART").astype(np.int64)
+    ids = sim.read("ID").astype(np.int64)
+    assert np.array_equal(np.sort(ids), np.arange(p.n_particles))
+    assert np.all(np.diff(keys) >= 0)
+    spans = decode_spans(p.cfg, keys)
+    for a in range(2):
+        xi = x[a] / p.cfg["h"]
+        assert np.all(xi >= spans[a] - 0.5 - 1e-5) and np.all(xi <= spans[a] + 0.5 + 1e-5)
+    assert np.array_equal(np.diff(start), np.bincount(keys, minlength=len(start) - 1))
+    sim.close()
+
+
+# ------------------------------------------------------------------- P2G
+
+P2G_CASES = [
+    (2, 2, [40, 29], ["wall"] * 4),
+    (2, 1, [33, 20], ["periodic"] * 2 + ["inflow", "outflow"]),
+    (3, 2, [13, 11, 9], ["wall", "wall", "periodic", "periodic", "wall", "wall"]),
+    (3, 1, [10, 9, 11], ["wall"] * 6),
+]
+
+
+@pytest.mark.parametrize("dim,degree,n,bc", P2G_CASES)
+def test_fixed_point_p2g_bit_exact(dim, degree, n, bc):
+    p = random_problem(dim, degree, n, bc, 15013, 11, "fp32_fixed64")
+    sim = gpu_sim(p)
+    sim.step(1, dt=1e-6)
+    gm, gmv, gf = O.p2g_fixed32(p.cfg, p.x, p.v, p.mass, p.rho, p.e)
+    assert np.array_equal(sim.read_fixed("GRID_M"), gm)
+    assert np.array_equal(sim.read_fixed("GRID_MV"), gmv)
+    assert np.array_equal(sim.read_fixed("GRID_F"), gf)
+    sim.close()
+
+
+@pytest.mark.parametrize("dim,degree,n,bc", P2G_CASES)
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_float_p2g_matches_oracle(dim, degree, n, bc, precision):
+    p = random_problem(dim, degree, n, bc, 15013, 12, precision)
+    sim = gpu_sim(p)
+    sim.step(1, dt=1e-6)
+    gm, gmv, gf = O.p2g(p.cfg, p.x, p.v, p.mass, p.rho, p.e)
+    tol = 1e-5 if precision == "fp32" else 1e-12
+    for name, ref in (("GRID_M", gm), ("GRID_MV", gmv), ("GRID_F", gf)):
+        got = sim.read(name)
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), name
+    sim.close()
+
+
+# ------------------------------------------------------------ whole steps
+
+def compare_fields(g, o, tol, dim, exclude_far=None):
+    gi, oi = g.read("ID").astype(np.int64), o.read("ID").astype(np.int64)
+    go, oo = np.argsort(gi), np.argsort(oi)
+    xg, xo = g.read("X")[:, go], o.read("X")[:, oo]
+    ok = np.ones(xg.shape[1], dtype=bool)
+    if exclude_far is not None:
+        ok = np.all(np.abs(xg - xo) < exclude_far, axis=0)
+    out = {"excluded": int((~ok).sum())}
+    for f in ("RHO", "P", "E"):
+        out[f] = rel_l1(g.read(f)[go][ok], o.read(f)[oo][ok])
+    vg, vo = g.read("V")[:, go], o.read("V")[:, oo]
+    for a in range(dim):
+        out[f"V{a}"] = rel_l1(vg[a][ok], vo[a][ok])
+    out["X"] = rel_l1(xg[:, ok], xo[:, ok])
+    for k in ("RHO", "P") + tuple(f"V{a}" for a in range(dim)):
+        assert out[k] <= tol, (k, out)
+    return out
+
+
+def test_fp64_shock_tube_matches_oracle_to_t_end():
+    p = I.shock_tube(ncell=200, ny=4, t_end=0.2, precision="fp64")
+    g, o = gpu_sim(p), oracle_sim(p)
+    g.step(100000, t_end=0.2)
+    o.step(100000, t_end=0.2)
+    assert g.read("CLOCK")[0] == 0.2 and o.read("CLOCK")[0] == 0.2
+    assert g.read("CLOCK")[2] == o.read("CLOCK")[2]
+    compare_fields(g, o, 1e-10, 2)
+    g.close()
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+def test_fp64_cylinder_matches_oracle(degree):
+    p = I.cylinder(nx=64, ny=32, radius=0.1, seed=4, precision="fp64", degree=degree)
+    g, o = gpu_sim(p), oracle_sim(p)
+    g.step(60)
+    o.step(60)
+    r = compare_fields(g, o, 1e-9, 2, exclude_far=0.25)
+    assert r["excluded"] == 0
+    g.close()
+
+
+def test_fp64_blast_3d_matches_oracle():
+    p = I.blast(n=12, precision="fp64", radius_cells=2.0)
+    g, o = gpu_sim(p), oracle_sim(p)
+    g.step(20)
+    o.step(20)
+    compare_fields(g, o, 1e-9, 3)
+    g.close()
+
+
+def test_fp32_cylinder_100_steps_within_target():
+    p = f32(I.cylinder(nx=128, ny=64, seed=1, precision="fp32"))
+    g, o = gpu_sim(p), oracle_sim(p)
+    g.step(100)
+    o.step(100)
+    r = compare_fields(g, o, 1e-4, 2, exclude_far=0.25)
+    assert r["excluded"] == 0
+    g.close()
+
+
+def test_fp32_fixed_cylinder_100_steps_within_target():
+    p = f32(I.cylinder(nx=128, ny=64, seed=1, precision="fp32_fixed64"))
+    g, o = gpu_sim(p), oracle_sim(p)
+    g.step(100)
+    o.step(100)
+    r = compare_fields(g, o, 1e-4, 2, exclude_far=0.25)
+    assert r["excluded"] == 0
+    g.close()
+
+
+def test_fp32_blast_3d_100_steps_within_target():
+    p = f32(I.blast(n=16, precision="fp32"))
+    g, o = gpu_sim(p), oracle_sim(p)
+    g.step(100)
+    o.step(100)
+    compare_fields(g, o, 1e-4, 3)
+    g.close()
+
+
+def test_fixed_point_is_bit_reproducible():
+    p = f32(I.cylinder(nx=96, ny=48, seed=3, precision="fp32_fixed64"))
+    outs = []
+    for _ in range(2):
+        g = gpu_sim(p)
+        g.step(50)
+        outs.append([g.read(f) for f in ("X", "V", "RHO", "E", "Q", "ID")])
+        g.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_conservation_sums():
+    p = I.uniform_flow(dim=3, n=(8, 8, 8), degree=2, precision="fp64")
+    rng = np.random.default_rng(0)
+    p.rho = rng.uniform(0.9, 1.1, p.n_particles)
+    p.v = p.v + 0.05 * rng.normal(size=p.v.shape)
+    g, o = gpu_sim(p), oracle_sim(p)
+    c0 = g.conservation()
+    g.step(10)
+    o.step(10)
+    c1, co = g.conservation(), o.conservation()
+    assert c1[0] == pytest.approx(c0[0], rel=1e-14)
+    assert np.abs(c1[2:5] - c0[2:5]).max() < 1e-12 * c0[0]
+    assert np.abs(c1 - co).max() < 1e-10 * np.abs(co).max()
+    g.close()
+
+
+# ----------------------------------------------------------- edge cases
+
+def test_empty_tiles_ragged_tail_and_single_particle():
+    cfg = I.base_config(2, [50, 19], 0.02, ["wall"] * 4, degree=2, precision="fp64", tile=[16, 16, 0])
+    x = np.array([[0.51], [0.2]])
+    p = I.Problem("one", cfg, x, np.array([[0.1], [0.0]]), np.array([1e-3]), np.array([1.0]), np.array([2.5]))
+    g, o = gpu_sim(p), oracle_sim(p)
+    g.step(5)
+    o.step(5)
+    assert np.allclose(g.read("X"), o.read("X"), rtol=1e-12, atol=1e-14)
+    assert np.allclose(g.read("RHO"), o.read("RHO"), rtol=1e-12)
+    g.close()
+
+
+def test_particles_on_domain_faces():
+    cfg = I.base_config(2, [20, 10], 0.05, ["wall"] * 4, degree=1, precision="fp64")
+    x = np.array([[0.0, 1.0, 0.5, 0.0, 1.0], [0.0, 0.5, 0.5, 0.5, 0.0]])
+    N = x.shape[1]
+    p = I.Problem("faces", cfg, x, np.zeros((2, N)), np.full(N, 1e-3), np.ones(N), np.full(N, 2.5))
+    g, o = gpu_sim(p), oracle_sim(p)
+    g.step(3)
+    o.step(3)
+    assert np.allclose(by_id(g, "X"), by_id(o, "X"), atol=1e-13)
+    g.close()
+
+
+def test_errors_are_status_codes():
+    p = I.shock_tube(ncell=32, ny=4, precision="fp32")
+    g = gpu_sim(p)
+    with pytest.raises(M.MPMError) as e:
+        g.step(1, dt=10.0)              # particles would cross many spans
+    assert e.value.status in ("MPM_ECFL", "MPM_ENONFINITE")
+    with pytest.raises(M.MPMError) as e:
+        g.step(1)
+    assert e.value.status == "MPM_ESTATE"
+    g.close()
+    g = gpu_sim(p)
+    g.step(1)
+    with pytest.raises(M.MPMError) as e:
+        g.add_particles(p.x[:, :1], p.v[:, :1], p.mass[:1], p.rho[:1], p.e[:1])
+    assert e.value.status == "MPM_ESTATE"
+    g.close()
+    bad = dict(p.cfg)
+    bad["bc"] = ["periodic", "wall", "wall", "wall"]
+    with pytest.raises(M.MPMError) as e:
+        M.Simulation(bad)
+    assert e.value.status == "MPM_EINVAL"
+    g = M.Simulation(p.cfg)
+    with pytest.raises(M.MPMError) as e:
+        g.add_particles(np.array([[2.0], [0.0]]), np.zeros((2, 1)), np.ones(1), np.ones(1), np.ones(1))
+    assert e.value.status == "MPM_EINVAL"
+    with pytest.raises(M.MPMError) as e:
+        g.step(1)
+    assert e.value.status == "MPM_ESTATE"      # no particles
+    g.close()
+
+
+def test_short_output_buffer_rejected():
+    import ctypes
+    p = I.shock_tube(ncell=16, ny=4)
+    g = gpu_sim(p)
+    L = M.load()
+    out = np.empty(3)
+    code = L.mpm_read_state(g.handle, M.FIELDS["RHO"], out.ctypes.data_as(ctypes.c_void_p), 3)
+    assert code == 1
+    g.close()
+
+
+def test_t_end_is_hit_exactly_and_later_steps_are_noops():
+    p = I.shock_tube(ncell=50, ny=4, precision="fp32")
+    g = gpu_sim(p)
+    g.step(100000, t_end=0.01)
+    c = g.read("CLOCK")
+    assert c[0] == 0.01
+    x = g.read("X")
+    g.step(5, t_end=0.01)
+    assert np.array_equal(g.read("X"), x) and g.read("CLOCK")[2] == c[2]
+    g.close()
