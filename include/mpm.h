@@ -94,8 +94,11 @@ typedef struct {
     double inflow_rho, inflow_p, inflow_v[3];   /* inflow faces and recycled particles */
     double cfl;              /* dt = cfl h / (max|v| + max c) (eq. CFL, Sec. 4.1) */
     int sort_interval;       /* must be 1: the tiled kernels need ordered particles */
-    uint64_t seed;           /* Philox key for particle recycling */
-    int tile[3];             /* spans per tile per axis; 0 selects 8 (3D) / 16 (2D) */
+    uint64_t seed;           /* Philox-4x32-10 key of particle recycling: a particle
+                                leaving through an outflow face for the g-th time draws
+                                from counter (g, 0, id, 0) */
+    int tile[3];             /* spans per tile per axis, powers of two <= 64; 0 selects
+                                32 x 4 x 4 (3D) / 32 x 8 (2D) */
     void* stream;            /* cudaStream_t to run on; NULL: the library's own stream */
     /* Optional device allocator (e.g. a framework's caching allocator):
        alloc(bytes, ctx) returns device memory or NULL; free(ptr, ctx).

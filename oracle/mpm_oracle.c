@@ -64,7 +64,8 @@ static int geom_init(const oracle_config* c, geom* G)
         G->S[a] = G->per[a] ? c->n[a] : (G->p == 2 ? c->n[a] + 1 : c->n[a]);
         G->N[a] = G->per[a] ? c->n[a] : c->n[a] + 2 * G->p - 1;
         G->g[a] = G->per[a] ? 0 : G->p - 1;
-        G->T[a] = c->tile[a] > 0 ? c->tile[a] : (c->dim == 3 ? 8 : 16);
+        static const int def3[3] = {32, 4, 4}, def2[3] = {32, 8, 1};
+        G->T[a] = c->tile[a] > 0 ? c->tile[a] : (c->dim == 3 ? def3[a] : def2[a]);
         G->nt[a] = (G->S[a] + G->T[a] - 1) / G->T[a];
         G->lo[a] = c->origin[a];
         G->hi[a] = c->origin[a] + c->n[a] * c->h;
@@ -221,6 +222,7 @@ struct oracle_sim {
     int64_t np;
     double *x[3], *v[3], *vbar[3], *M, *rho, *E, *Q;
     int64_t* id;
+    uint32_t* gen;       /* times each particle has been recycled */
     uint32_t* key;
     int64_t* cellstart;
     double *gm, *gmv[3], *gf[3], *gmv2[3];     /* raw P2G sums of the last step */
@@ -238,8 +240,8 @@ static void free_particles(oracle_sim* s)
 {
     for (int a = 0; a < 3; ++a) { free(s->x[a]); free(s->v[a]); free(s->vbar[a]); free(s->tmp_p[a]);
                                   s->x[a] = s->v[a] = s->vbar[a] = s->tmp_p[a] = NULL; }
-    free(s->M); free(s->rho); free(s->E); free(s->Q); free(s->id); free(s->key); free(s->coef);
-    s->M = s->rho = s->E = s->Q = s->coef = NULL; s->id = NULL; s->key = NULL;
+    free(s->M); free(s->rho); free(s->E); free(s->Q); free(s->id); free(s->key); free(s->coef); free(s->gen);
+    s->M = s->rho = s->E = s->Q = s->coef = NULL; s->id = NULL; s->key = NULL; s->gen = NULL;
 }
 
 void oracle_destroy(oracle_sim* s)
@@ -303,7 +305,8 @@ int oracle_add_particles(oracle_sim* s, int64_t n, const double* x, const double
     nc = realloc(s->coef, np * sizeof(double) + 8); if (nc) s->coef = nc;
     int64_t* nid = realloc(s->id, np * sizeof(int64_t) + 8); if (nid) s->id = nid;
     uint32_t* nk = realloc(s->key, np * sizeof(uint32_t) + 8); if (nk) s->key = nk;
-    int ok = nM && nR && nE && nQ && nc && nid && nk;
+    uint32_t* ng = realloc(s->gen, np * sizeof(uint32_t) + 8); if (ng) s->gen = ng;
+    int ok = nM && nR && nE && nQ && nc && nid && nk && ng;
     for (int a = 0; a < 3; ++a) {
         nx[a] = realloc(s->x[a], np * sizeof(double) + 8); if (nx[a]) s->x[a] = nx[a];
         nv[a] = realloc(s->v[a], np * sizeof(double) + 8); if (nv[a]) s->v[a] = nv[a];
@@ -319,7 +322,7 @@ int oracle_add_particles(oracle_sim* s, int64_t n, const double* x, const double
             s->v[a][j] = (a < G->dim) ? v[a * n + k] : 0.0;
             s->vbar[a][j] = s->v[a][j];
         }
-        s->M[j] = mass[k]; s->rho[j] = rho[k]; s->E[j] = e[k]; s->Q[j] = 0.0; s->id[j] = j;
+        s->M[j] = mass[k]; s->rho[j] = rho[k]; s->E[j] = e[k]; s->Q[j] = 0.0; s->id[j] = j; s->gen[j] = 0;
     }
     s->np = np;
     return sort_particles(s);
@@ -440,12 +443,14 @@ static int first_inflow_face(const oracle_sim* s)
 }
 
 /* Particle recycling (Sec. 4.1, cylinder case): new position in the first
- * cell layer of the inflow face, other coordinates uniform; inflow state. */
+ * cell layer of the inflow face, other coordinates uniform; inflow state.
+ * The draw is keyed by the particle's own recycle count, so a particle that
+ * leaves one step earlier or later lands at the same place. */
 static void recycle(oracle_sim* s, int64_t k, int face)
 {
     const geom* G = &s->G; const oracle_config* c = &s->cfg;
-    uint32_t ctr[4] = { (uint32_t)s->step, (uint32_t)((uint64_t)s->step >> 32),
-                        (uint32_t)s->id[k], (uint32_t)((uint64_t)s->id[k] >> 32) };
+    uint32_t ctr[4] = { s->gen[k], 0u, (uint32_t)s->id[k], (uint32_t)((uint64_t)s->id[k] >> 32) };
+    s->gen[k] += 1;
     uint32_t key[2] = { (uint32_t)c->seed, (uint32_t)(c->seed >> 32) }, r[4];
     oracle_philox4x32_10(ctr, key, r);
     int af = face / 2, side = face % 2;
@@ -514,6 +519,8 @@ static int sort_particles(oracle_sim* s)
     uint32_t* tk = (uint32_t*)tmp;
     for (int64_t j = 0; j < n; ++j) tk[j] = s->key[perm[j]];
     memcpy(s->key, tk, (size_t)n * sizeof(uint32_t));
+    for (int64_t j = 0; j < n; ++j) tk[j] = s->gen[perm[j]];
+    memcpy(s->gen, tk, (size_t)n * sizeof(uint32_t));
     free(perm); free(tmp);
     return OR_OK;
 }

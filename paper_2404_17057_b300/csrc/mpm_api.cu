@@ -6,9 +6,12 @@
 // mpm_kernels.cuh / mpm_sort.cuh.
 #include "mpm.h"
 #include "mpm_kernels.cuh"
+#include "mpm_fast.cuh"
 #include "mpm_sort.cuh"
 
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include <cmath>
 #include <cstdio>
@@ -32,6 +35,7 @@ struct Buffers {             // one copy of the particle state (type-erased)
     void* Q = nullptr;
     uint32_t* id = nullptr;
     uint32_t* key = nullptr;
+    uint32_t* gen = nullptr;
 };
 
 struct ProfStep {
@@ -169,6 +173,7 @@ Particles<R> parts(const Buffers& b)
     p.Q = (R*)b.Q;
     p.id = b.id;
     p.key = b.key;
+    p.gen = b.gen;
     return p;
 }
 
@@ -176,7 +181,7 @@ template <class A, class R>
 Grid<A, R> grid_view(const mpm_sim* s)
 {
     Grid<A, R> g;
-    const int64_t nn = s->G.nnode;
+    const int64_t nn = s->G.nnode_p;
     const int d = s->G.dim;
     A* base = (A*)s->grid;
     g.m = base;
@@ -192,9 +197,17 @@ Grid<A, R> grid_view(const mpm_sim* s)
 
 template <int D, int P, class R, class A>
 struct Impl {
+    // The single-precision float-atomic path runs the span-per-thread kernels
+    // of mpm_fast.cuh; the fixed-point and FP64 paths the generic ones.
+    static constexpr bool kFast = std::is_same<R, float>::value && std::is_same<A, float>::value;
     static size_t smem(const Geom& G, int kernel)
     {
         const size_t W = (size_t)G.Wvol;
+        if (kFast) {
+            if (kernel == 0) return (1 + 2 * D) * W * sizeof(float);
+            if (kernel == 1) return 16 * W + D * W * sizeof(float) + (kSpanThreads / 32) * D * kStageCap * sizeof(float);
+            return (D == 3 ? 2 : 1) * 16 * W;
+        }
         if (kernel == 0) return (1 + 2 * D) * W * sizeof(A);
         if (kernel == 1) return align16(D * W * sizeof(R)) + D * W * sizeof(A);
         return 2 * D * W * sizeof(R);
@@ -202,14 +215,29 @@ struct Impl {
     static cudaError_t set_smem(const Geom& G)
     {
         cudaError_t e;
-        e = cudaFuncSetAttribute(k_p2g<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(G, 0));
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_grid_g2p<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem(G, 1));
-        if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k_g2pd<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(G, 2));
+        if constexpr (kFast) {
+            for (int per = 0; per < 2; ++per) {
+                e = cudaFuncSetAttribute(per ? (const void*)k_p2g_span<D, P, true> : (const void*)k_p2g_span<D, P, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(G, 0));
+                if (e != cudaSuccess) return e;
+                e = cudaFuncSetAttribute(per ? (const void*)k_grid_g2p_span<D, P, true>
+                                             : (const void*)k_grid_g2p_span<D, P, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(G, 1));
+                if (e != cudaSuccess) return e;
+            }
+            return cudaFuncSetAttribute(k_g2pd_fast<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem(G, 2));
+        } else {
+            e = cudaFuncSetAttribute(k_p2g<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(G, 0));
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_grid_g2p<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem(G, 1));
+            if (e != cudaSuccess) return e;
+            return cudaFuncSetAttribute(k_g2pd<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem(G, 2));
+        }
     }
-    // mask bit 0: P2G, 1: grid+G2P, 2: G2PD (used by the profiler to split)
+    // which bit 0: zero + P2G, bit 1: grid + G2P + P2G, bit 2: G2PD + update
     static void step_kernels(mpm_sim* s, int which, cudaStream_t st)
     {
         const Geom& G = s->G;
@@ -218,15 +246,42 @@ struct Impl {
         if (which & 1) {
             k_zero<<<std::min<int64_t>(nblk(s->grid_bytes / 16), 148 * 8), kThreads, 0, st>>>(
                 (uint4*)s->grid, (int64_t)(s->grid_bytes / 16), &s->clk->active);
-            k_p2g<D, P, R, A><<<G.ntiles, kThreads, smem(G, 0), st>>>(G, pt, gr, s->cellstart, s->clk);
+            if constexpr (kFast) {
+                FieldPtrs o = {};
+                o.p[0] = (float*)gr.m;
+                for (int a = 0; a < D; ++a) {
+                    o.p[1 + a] = (float*)gr.mv[a];
+                    o.p[1 + D + a] = (float*)gr.f[a];
+                }
+                if (G.per[0] | G.per[1] | G.per[2])
+                    k_p2g_span<D, P, true><<<G.ntiles, kSpanThreads, smem(G, 0), st>>>(G, pt, o, s->cellstart, s->clk);
+                else
+                    k_p2g_span<D, P, false><<<G.ntiles, kSpanThreads, smem(G, 0), st>>>(G, pt, o, s->cellstart, s->clk);
+            } else {
+                k_p2g<D, P, R, A><<<G.ntiles, kThreads, smem(G, 0), st>>>(G, pt, gr, s->cellstart, s->clk);
+            }
             s->launches += 2;
         }
         if (which & 2) {
-            k_grid_g2p<D, P, R, A><<<G.ntiles, kThreads, smem(G, 1), st>>>(G, pt, gr, s->cellstart, s->clk);
+            if constexpr (kFast) {
+                FieldPtrs o = {};
+                for (int a = 0; a < D; ++a) o.p[a] = (float*)gr.mv2[a];
+                if (G.per[0] | G.per[1] | G.per[2])
+                    k_grid_g2p_span<D, P, true><<<G.ntiles, kSpanThreads, smem(G, 1), st>>>(G, pt, gr, o, s->cellstart,
+                                                                                             s->clk);
+                else
+                    k_grid_g2p_span<D, P, false><<<G.ntiles, kSpanThreads, smem(G, 1), st>>>(G, pt, gr, o, s->cellstart,
+                                                                                              s->clk);
+            } else {
+                k_grid_g2p<D, P, R, A><<<G.ntiles, kThreads, smem(G, 1), st>>>(G, pt, gr, s->cellstart, s->clk);
+            }
             s->launches += 1;
         }
         if (which & 4) {
-            k_g2pd<D, P, R, A><<<G.ntiles, kThreads, smem(G, 2), st>>>(G, pt, gr, s->cellstart, s->clk);
+            if constexpr (kFast)
+                k_g2pd_fast<D, P><<<G.ntiles, 256, smem(G, 2), st>>>(G, pt, gr, s->cellstart, s->clk);
+            else
+                k_g2pd<D, P, R, A><<<G.ntiles, kThreads, smem(G, 2), st>>>(G, pt, gr, s->cellstart, s->clk);
             s->launches += 1;
         }
     }
@@ -316,11 +371,14 @@ mpm_status make_geom(const mpm_config* c, Geom* G, std::string* why)
         if (c->n[a] < 1 || c->n[a] > (1 << 20)) { *why = "bad cell count"; return MPM_EINVAL; }
         G->n[a] = c->n[a];
         G->per[a] = bl == MPM_BC_PERIODIC;
+        if (G->per[a] && G->p == 2 && c->n[a] < 2) { *why = "a periodic axis needs 2 cells for degree 2"; return MPM_EINVAL; }
         G->S[a] = G->per[a] ? c->n[a] : (G->p == 2 ? c->n[a] + 1 : c->n[a]);
         G->N[a] = G->per[a] ? c->n[a] : c->n[a] + 2 * G->p - 1;
         G->g[a] = G->per[a] ? 0 : G->p - 1;
-        G->T[a] = c->tile[a] > 0 ? c->tile[a] : (c->dim == 3 ? 8 : 16);
-        if (G->T[a] > 64) { *why = "tile edge must be <= 64"; return MPM_EINVAL; }
+        static const int def3[3] = {32, 4, 4}, def2[3] = {32, 8, 1};
+        G->T[a] = c->tile[a] > 0 ? c->tile[a] : (c->dim == 3 ? def3[a] : def2[a]);
+        if (G->T[a] > 64 || (G->T[a] & (G->T[a] - 1))) { *why = "tile edges must be powers of two <= 64"; return MPM_EINVAL; }
+        while ((1 << G->tsh[a]) < G->T[a]) ++G->tsh[a];
         G->nt[a] = (G->S[a] + G->T[a] - 1) / G->T[a];
         G->W[a] = G->T[a] + G->p;
         G->lo[a] = c->origin[a];
@@ -334,11 +392,14 @@ mpm_status make_geom(const mpm_config* c, Geom* G, std::string* why)
     }
     nkey = (int64_t)ntiles * tvol;
     if (nkey >= (int64_t)0xFFFFFFF0LL) { *why = "too many spans for 32-bit keys"; return MPM_EINVAL; }
+    if (tvol < 32) { *why = "a tile must hold at least 32 spans"; return MPM_EINVAL; }
     G->Tvol = tvol;
     G->Wvol = wvol;
     G->ntiles = ntiles;
     G->nkey = nkey;
     G->nnode = nnode;
+    G->pitch = (G->N[0] + 3) & ~3;
+    G->nnode_p = (int64_t)G->pitch * G->N[1] * G->N[2];
     for (int f = 0; f < 6; ++f) G->bc[f] = f < 2 * c->dim ? c->bc[f] : MPM_BC_WALL;
     G->inflow_face = -1;
     for (int f = 0; f < 2 * c->dim; ++f)
@@ -379,7 +440,8 @@ mpm_status alloc_particles(mpm_sim* s, int64_t n, Buffers nb[2])
         nb[b].Q = dalloc(s, rb);
         nb[b].id = (uint32_t*)dalloc(s, ub);
         nb[b].key = (uint32_t*)dalloc(s, ub);
-        if (!nb[b].M || !nb[b].rho || !nb[b].E || !nb[b].Q || !nb[b].id || !nb[b].key) return MPM_ENOMEM;
+        nb[b].gen = (uint32_t*)dalloc(s, ub);
+        if (!nb[b].M || !nb[b].rho || !nb[b].E || !nb[b].Q || !nb[b].id || !nb[b].key || !nb[b].gen) return MPM_ENOMEM;
     }
     return MPM_OK;
 }
@@ -389,7 +451,7 @@ void free_particles(mpm_sim* s, Buffers b[2])
     for (int k = 0; k < 2; ++k) {
         for (int a = 0; a < 3; ++a) { dfree(s, b[k].x[a]); dfree(s, b[k].v[a]); }
         dfree(s, b[k].M); dfree(s, b[k].rho); dfree(s, b[k].E); dfree(s, b[k].Q);
-        dfree(s, b[k].id); dfree(s, b[k].key);
+        dfree(s, b[k].id); dfree(s, b[k].key); dfree(s, b[k].gen);
         b[k] = Buffers();
     }
 }
@@ -540,7 +602,7 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
         return fail(nullptr, MPM_ECUDA, std::string("shared memory attribute: ") + cudaGetErrorString(e));
     }
     const int d = s->G.dim;
-    s->grid_bytes = align16((size_t)(1 + 3 * d) * (size_t)s->G.nnode * s->asize);
+    s->grid_bytes = align16((size_t)(1 + 3 * d) * (size_t)s->G.nnode_p * s->asize);
     s->grid = dalloc(s, s->grid_bytes);
     s->clk = (Clock*)dalloc(s, sizeof(Clock));
     s->cellstart = (uint32_t*)dalloc(s, (size_t)(s->G.nkey + 1) * 4);
@@ -607,6 +669,7 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
         CK(cudaMemcpyAsync(nb[0].E, ob.E, s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
         CK(cudaMemcpyAsync(nb[0].Q, ob.Q, s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
         CK(cudaMemcpyAsync(nb[0].id, ob.id, s->np * 4, cudaMemcpyDeviceToDevice, S), "copy");
+        CK(cudaMemcpyAsync(nb[0].gen, ob.gen, s->np * 4, cudaMemcpyDeviceToDevice, S), "copy");
     }
     // stage the new doubles on the device and convert to the storage precision
     double* stage = (double*)dalloc(s, (size_t)n * sizeof(double));
@@ -626,6 +689,7 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
     CK(up(e, nb[0].E), "upload e");
     dfree(s, stage);
     CK(cudaMemsetAsync((char*)nb[0].Q + s->np * rs, 0, n * rs, S), "zero q");
+    CK(cudaMemsetAsync(nb[0].gen + s->np, 0, n * 4, S), "zero gen");
     k_iota<<<nblk(n), kThreads, 0, S>>>(nb[0].id + s->np, n, (uint32_t)s->np);
     // replace the old buffers and the sort scratch
     free_particles(s, s->buf);
@@ -677,18 +741,27 @@ mpm_status mpm_set_obstacle_mask(mpm_sim* s, const uint8_t* mask, const double* 
     }
     for (int64_t i = 0; i < (int64_t)d * nn; ++i)
         if (!std::isfinite(normals[i])) return fail(s, MPM_EINVAL, "non-finite normal");
+    const int64_t np_ = G.nnode_p;
     if (!s->mask) {
-        s->mask = (uint8_t*)dalloc(s, (size_t)nn);
-        s->nrm = dalloc(s, (size_t)d * nn * s->rsize);
+        s->mask = (uint8_t*)dalloc(s, (size_t)np_);
+        s->nrm = dalloc(s, (size_t)d * np_ * s->rsize);
         if (!s->mask || !s->nrm) return fail(s, MPM_ENOMEM, "device allocation failed");
     }
-    std::vector<uint8_t> m(nn);
-    for (int64_t i = 0; i < nn; ++i) m[i] = mask[i] ? 1 : 0;
-    CK(cudaMemcpyAsync(s->mask, m.data(), nn, cudaMemcpyHostToDevice, s->stream), "upload mask");
-    double* stage = (double*)dalloc(s, (size_t)d * nn * sizeof(double));
+    // expand to the device layout (rows padded to G.pitch)
+    std::vector<uint8_t> m(np_, 0);
+    std::vector<double> nv((size_t)d * np_, 0.0);
+    for (int64_t i = 0; i < nn; ++i) {
+        const int64_t row = i / G.N[0], x0 = i % G.N[0];
+        const int64_t j = row * G.pitch + x0;
+        m[j] = mask[i] ? 1 : 0;
+        for (int a = 0; a < d; ++a) nv[(size_t)a * np_ + j] = normals[(size_t)a * nn + i];
+    }
+    CK(cudaMemcpyAsync(s->mask, m.data(), np_, cudaMemcpyHostToDevice, s->stream), "upload mask");
+    double* stage = (double*)dalloc(s, (size_t)d * np_ * sizeof(double));
     if (!stage) return fail(s, MPM_ENOMEM, "device allocation failed");
-    CK(cudaMemcpyAsync(stage, normals, (size_t)d * nn * sizeof(double), cudaMemcpyHostToDevice, s->stream), "upload");
-    s->vt->from_double(stage, s->nrm, (int64_t)d * nn, s->stream);
+    CK(cudaMemcpyAsync(stage, nv.data(), (size_t)d * np_ * sizeof(double), cudaMemcpyHostToDevice, s->stream),
+       "upload");
+    s->vt->from_double(stage, s->nrm, (int64_t)d * np_, s->stream);
     CK(cudaStreamSynchronize(s->stream), "synchronize");
     dfree(s, stage);
     drop_graphs(s);
@@ -890,22 +963,29 @@ mpm_status mpm_read_state(mpm_sim* s, int field, double* out, int64_t count)
     }
     default: break;
     }
-    // grid fields
-    int64_t off = 0, cnt = nn;
-    if (field == MPM_FIELD_GRID_M) { off = 0; cnt = nn; }
-    else if (field == MPM_FIELD_GRID_MV) { off = nn; cnt = d * nn; }
-    else if (field == MPM_FIELD_GRID_F) { off = (1 + d) * nn; cnt = d * nn; }
-    else { off = (1 + 2 * d) * nn; cnt = d * nn; }
+    // grid fields: copy the padded rows, then drop the padding
+    const int64_t npd = s->G.nnode_p;
+    const int comps = field == MPM_FIELD_GRID_M ? 1 : d;
+    int64_t off = field == MPM_FIELD_GRID_M ? 0 : field == MPM_FIELD_GRID_MV ? npd
+                : field == MPM_FIELD_GRID_F ? (1 + d) * npd : (1 + 2 * d) * npd;
+    std::vector<double> tmp((size_t)comps * npd);
     if (s->cfg.precision == MPM_FP32_FIXED64) {
-        std::vector<long long> t(cnt);
-        CK(cudaMemcpyAsync(t.data(), (long long*)s->grid + off, cnt * 8, cudaMemcpyDeviceToHost, s->stream), "read");
+        std::vector<long long> t((size_t)comps * npd);
+        CK(cudaMemcpyAsync(t.data(), (long long*)s->grid + off, t.size() * 8, cudaMemcpyDeviceToHost, s->stream),
+           "read");
         CK(cudaStreamSynchronize(s->stream), "synchronize");
         const int kind = field == MPM_FIELD_GRID_M ? 0 : field == MPM_FIELD_GRID_F ? 2 : 1;
         const double u = s->cfg.fixed_unit[kind] > 0.0 ? s->cfg.fixed_unit[kind] : 1.0;
-        for (int64_t i = 0; i < cnt; ++i) out[i] = (double)t[i] * (u / 4294967296.0);
-        return MPM_OK;
+        for (size_t i = 0; i < t.size(); ++i) tmp[i] = (double)t[i] * (u / 4294967296.0);
+    } else {
+        if ((st = read_real(s, (char*)s->grid + off * s->asize, (int64_t)tmp.size(), tmp.data()))) return st;
     }
-    return read_real(s, (char*)s->grid + off * s->asize, cnt, out);
+    for (int c = 0; c < comps; ++c)
+        for (int64_t i = 0; i < nn; ++i) {
+            const int64_t row = i / s->G.N[0], x0 = i % s->G.N[0];
+            out[(size_t)c * nn + i] = tmp[(size_t)c * npd + row * s->G.pitch + x0];
+        }
+    return MPM_OK;
 }
 
 mpm_status mpm_read_grid_fixed(mpm_sim* s, int field, int64_t* out, int64_t count)
@@ -917,11 +997,18 @@ mpm_status mpm_read_grid_fixed(mpm_sim* s, int field, int64_t* out, int64_t coun
     const int64_t need = mpm_field_size(s, field);
     if (count < need) return fail(s, MPM_EINVAL, "output buffer too short");
     const int d = s->G.dim;
-    const int64_t nn = s->G.nnode;
-    int64_t off = field == MPM_FIELD_GRID_M ? 0 : field == MPM_FIELD_GRID_MV ? nn
-                : field == MPM_FIELD_GRID_F ? (1 + d) * nn : (1 + 2 * d) * nn;
-    CK(cudaMemcpyAsync(out, (long long*)s->grid + off, need * 8, cudaMemcpyDeviceToHost, s->stream), "read");
+    const int64_t nn = s->G.nnode, npd = s->G.nnode_p;
+    const int comps = field == MPM_FIELD_GRID_M ? 1 : d;
+    int64_t off = field == MPM_FIELD_GRID_M ? 0 : field == MPM_FIELD_GRID_MV ? npd
+                : field == MPM_FIELD_GRID_F ? (1 + d) * npd : (1 + 2 * d) * npd;
+    std::vector<long long> t((size_t)comps * npd);
+    CK(cudaMemcpyAsync(t.data(), (long long*)s->grid + off, t.size() * 8, cudaMemcpyDeviceToHost, s->stream), "read");
     CK(cudaStreamSynchronize(s->stream), "synchronize");
+    for (int c = 0; c < comps; ++c)
+        for (int64_t i = 0; i < nn; ++i) {
+            const int64_t row = i / s->G.N[0], x0 = i % s->G.N[0];
+            out[(size_t)c * nn + i] = t[(size_t)c * npd + row * s->G.pitch + x0];
+        }
     return MPM_OK;
 }
 

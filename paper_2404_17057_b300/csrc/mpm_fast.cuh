@@ -1,0 +1,719 @@
+// mpm_fast.cuh -- single-precision kernels of the step, organised for sm_103a.
+//
+// P2G-type work (steps ii and vi of Algorithm 1) is a scatter: every particle
+// adds (p+1)^d values per field to the grid.  All particles of one basis span
+// share their support nodes, and the particles are stored span by span, so
+// here one thread owns one span: it sums its particles' contributions in
+// registers (tensor products of 1D weights, two fields per packed f32x2 FMA)
+// and adds each node of the span once into the tile's shared-memory window.
+// A warp owns one x-row of 32 spans, so those adds never collide or share a
+// bank.  The window then goes to global memory once, as 16-byte vector
+// reductions along the (padded, 16-byte aligned) node rows.
+//
+// G2P-type work (the gathers of steps iv-viii) keeps one thread per particle:
+// lanes of one span read the same node records (a broadcast), and the sums
+// are factored along the axes (x first, then y, then z).
+#pragma once
+#include "mpm_kernels.cuh"
+
+namespace mpm {
+
+constexpr int kSpanThreads = 128;   // threads of the span-per-thread kernels
+constexpr int kStageCap = 512;      // particles per warp staged for coalesced stores
+
+template <int P>
+__device__ __forceinline__ void weights1d(float fx, float* w, float* dw)
+{
+    if (P == 2) {
+        const float t0 = 1.5f - fx, t1 = fx - 1.0f, t2 = fx - 0.5f;
+        w[0] = 0.5f * t0 * t0;
+        w[1] = 0.75f - t1 * t1;
+        w[2] = 0.5f * t2 * t2;
+        dw[0] = -t0;
+        dw[1] = -2.0f * t1;
+        dw[2] = t2;
+    } else {
+        w[0] = 1.0f - fx;
+        w[1] = fx;
+        dw[0] = -1.0f;
+        dw[1] = 1.0f;
+    }
+}
+
+// Span and weights along one axis; the span uses the same rounding rule as
+// the sort key, so it always matches the particle's place in the order.
+// Returns the local span inside the tile, or -1.
+template <int P>
+__device__ __forceinline__ int axis_fast(const Geom& G, int a, float x, int so, float* w, float* dw)
+{
+    float xi;
+    const int c = span_of<float, P>(G, a, x, xi);
+    const float fx = __fsub_rn(xi, (float)(c - (P == 2 ? 1 : 0)));
+    weights1d<P>(fx, w, dw);
+    const int l = wrap_span(G, a, c) - so;
+    return (l >= 0 && l < G.T[a]) ? l : -1;
+}
+
+// Offset and weights of a particle along one axis when its span is known
+// (the thread's span, first support node cb): no float<->int conversion on
+// the critical path.  The span of the particle was computed with the same
+// rounding when it was sorted; the range test catches an inconsistent order
+// (fx may sit one ulp outside the nominal interval at a span edge).
+template <int P, bool PER>
+__device__ __forceinline__ bool axis_known(float x, float lo, float ih, float cb, float n, float* w, float* dw)
+{
+    const float xi = __fmul_rn(__fsub_rn(x, lo), ih);
+    float fx = xi - cb;
+    // degree 2, periodic: a particle at xi in [n - 1/2, n) belongs to span 0
+    // (its nearest node wraps to 0); seen from span 0 its offset is fx + n
+    if (PER && P == 2 && fx > 0.5f * n + 0.75f) fx -= n;
+    weights1d<P>(fx, w, dw);
+    return P == 2 ? (fx > 0.499f && fx < 1.501f) : (fx > -0.001f && fx < 1.001f);
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+struct FieldPtrs {
+    float* p[7];
+};
+
+// Add a tile's shared-memory window (nf fields of W floats) into global node
+// rows.  Rows are padded to a multiple of 4 nodes and tiles start on a
+// multiple of 4 spans, so x-chunks of 4 nodes are 16-byte aligned.
+template <int D, int P>
+__device__ __forceinline__ void flush_window(const Geom& G, const int so[3], const float* sm, int nf,
+                                             const FieldPtrs& dst)
+{
+    const int W0 = G.W[0], W1 = G.W[1], W2 = G.W[2], W = G.Wvol;
+    const int nch = (W0 + 3) >> 2;
+    const int nrow = W1 * W2;
+    const bool vec = !G.per[0] && (G.T[0] % 4 == 0);
+    for (int t = threadIdx.x; t < nf * nrow * nch; t += blockDim.x) {
+        const int q = t % nch;
+        const int r = (t / nch) % nrow;
+        const int f = t / (nch * nrow);
+        const int wy = r % W1, wz = r / W1;
+        int iy = so[1] + wy, iz = D == 3 ? so[2] + wz : 0;
+        if (G.per[1]) {
+            iy -= (P == 2 ? 1 : 0);
+            iy %= G.n[1];
+            if (iy < 0) iy += G.n[1];
+        } else if (iy >= G.N[1]) {
+            continue;
+        }
+        if (D == 3) {
+            if (G.per[2]) {
+                iz -= (P == 2 ? 1 : 0);
+                iz %= G.n[2];
+                if (iz < 0) iz += G.n[2];
+            } else if (iz >= G.N[2]) {
+                continue;
+            }
+        }
+        const float* src = sm + f * W + (wz * W1 + wy) * W0;
+        float* row = dst.p[f] + ((int64_t)iz * G.N[1] + iy) * G.pitch;
+        const int x0 = 4 * q;
+        if (vec) {
+            const int gx = so[0] + x0;
+            if (gx >= G.pitch) continue;
+            float4 v;
+            v.x = src[x0];
+            v.y = x0 + 1 < W0 ? src[x0 + 1] : 0.f;
+            v.z = x0 + 2 < W0 ? src[x0 + 2] : 0.f;
+            v.w = x0 + 3 < W0 ? src[x0 + 3] : 0.f;
+            if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
+                atomicAdd(reinterpret_cast<float4*>(row + gx), v);
+        } else {
+            for (int j = x0; j < min(x0 + 4, W0); ++j) {
+                int gx = so[0] + j;
+                if (G.per[0]) {
+                    gx -= (P == 2 ? 1 : 0);
+                    gx %= G.n[0];
+                    if (gx < 0) gx += G.n[0];
+                } else if (gx >= G.N[0]) {
+                    continue;
+                }
+                const float v = src[j];
+                if (v != 0.f) atomicAdd(row + gx, v);
+            }
+        }
+    }
+}
+
+// Particle state one P2G step reads, loaded one particle ahead.
+template <int D>
+struct PState {
+    float x[3], v[3], M, rho, E, Q;
+};
+
+template <int D, bool FORCE>
+__device__ __forceinline__ void load_state(const Particles<float>& pt, uint32_t k, PState<D>& s)
+{
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        s.x[a] = pt.x[a][k];
+        s.v[a] = pt.v[a][k];
+    }
+    s.M = pt.M[k];
+    if (FORCE) {
+        s.rho = pt.rho[k];
+        s.E = pt.E[k];
+        s.Q = pt.Q[k];
+    }
+}
+
+// ---------------------------------------------------------------- K1: P2G
+
+// A row is 32 consecutive spans (one x-row for the default tiles).  Each row
+// is handled by two warps: group 0 sums m and M V, group 1 the force
+// (P + Q) M/rho grad(phi); both read the same particles.
+template <int D, int P, bool PER>
+__global__ void __launch_bounds__(kSpanThreads, 3) k_p2g_span(Geom G, Particles<float> pt, FieldPtrs out,
+                                                              const uint32_t* __restrict__ cs, Clock* clk)
+{
+    if (!clk->active) return;
+    const int tile = blockIdx.x;
+    const int64_t kb = (int64_t)tile * G.Tvol;
+    if (cs[kb] == cs[kb + G.Tvol]) return;
+    extern __shared__ __align__(16) float sm[];
+    constexpr int NS = P + 1, NF = 1 + 2 * D, NYZ = (D == 3) ? NS * NS : NS, NN = NYZ * NS;
+    const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
+    for (int i = threadIdx.x; i < NF * W; i += blockDim.x) sm[i] = 0.f;
+    __syncthreads();
+    int so[3];
+    tile_origin(G, tile, so);
+    const float gm1 = (float)(G.gamma - 1.0), ih = (float)G.inv_h;
+    float lo[3], nper[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (float)G.lo[a];
+        nper[a] = G.per[a] ? (float)G.n[a] : 3.0e38f;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int group = warp & 1;
+    const int nrows = G.Tvol >> 5, rstep = blockDim.x >> 6;
+    int err = 0;
+    for (int r = warp >> 1; r < nrows; r += rstep) {
+        const int s = (r << 5) + lane;
+        const uint32_t b = cs[kb + s], e = cs[kb + s + 1];
+        if (b == e) continue;
+        const int lx = s & (G.T[0] - 1);
+        const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
+        const int lz = s >> (G.tsh[0] + G.tsh[1]);
+        const int base = (lz * W1 + ly) * W0 + lx;
+        const float cb0 = (float)(so[0] + lx - (P == 2 ? 1 : 0));
+        const float cb1 = (float)(so[1] + ly - (P == 2 ? 1 : 0));
+        const float cb2 = (float)(so[2] + lz - (P == 2 ? 1 : 0));
+        if (group == 0) {
+            // 3D: q0 = {m, mv_x}, q1 = {mv_y, mv_z}; 2D: q0 = {m, mv_x}, q3 = mv_y
+            float2 q0[NN], q1[D == 3 ? NN : 1];
+            float q3[D == 3 ? 1 : NN];
+#pragma unroll
+            for (int i = 0; i < NN; ++i) {
+                q0[i] = f2(0.f, 0.f);
+                if (D == 3) q1[i] = f2(0.f, 0.f); else q3[i] = 0.f;
+            }
+            float nx[3], nv[3], nM;
+#pragma unroll
+            for (int a = 0; a < D; ++a) { nx[a] = pt.x[a][b]; nv[a] = pt.v[a][b]; }
+            nM = pt.M[b];
+            for (uint32_t k = b; k < e; ++k) {
+                float x[3], v[3];
+#pragma unroll
+                for (int a = 0; a < D; ++a) { x[a] = nx[a]; v[a] = nv[a]; }
+                const float M = nM;
+                if (k + 1 < e) {
+#pragma unroll
+                    for (int a = 0; a < D; ++a) { nx[a] = pt.x[a][k + 1]; nv[a] = pt.v[a][k + 1]; }
+                    nM = pt.M[k + 1];
+                }
+                float w[3][3], dw[3][3];
+                bool ok = axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
+                ok &= axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+                if (D == 3) ok &= axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
+                if (!ok) { err = 1; continue; }
+                float2 c0[NS], c1[NS];
+                float c3[NS];
+                const float mv0 = M * v[0], mv1 = M * v[1], mv2 = D == 3 ? M * v[2] : 0.f;
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    const float wa = w[0][a];
+                    c0[a] = f2(M * wa, mv0 * wa);
+                    if (D == 3) c1[a] = f2(mv1 * wa, mv2 * wa); else c3[a] = mv1 * wa;
+                }
+#pragma unroll
+                for (int j = 0; j < NYZ; ++j) {
+                    const float yz = D == 3 ? w[1][j % NS] * w[2][j / NS] : w[1][j];
+                    const float2 yy = f2(yz, yz);
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) {
+                        const int i = j * NS + a;
+                        q0[i] = __ffma2_rn(c0[a], yy, q0[i]);
+                        if (D == 3) q1[i] = __ffma2_rn(c1[a], yy, q1[i]);
+                        else q3[i] = fmaf(c3[a], yz, q3[i]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NYZ; ++j)
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    const int i = j * NS + a;
+                    const int slot = base + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0 + a;
+                    atomicAdd(&sm[slot], q0[i].x);
+                    atomicAdd(&sm[W + slot], q0[i].y);
+                    if (D == 3) {
+                        atomicAdd(&sm[2 * W + slot], q1[i].x);
+                        atomicAdd(&sm[3 * W + slot], q1[i].y);
+                    } else {
+                        atomicAdd(&sm[2 * W + slot], q3[i]);
+                    }
+                }
+        } else {
+            // 3D: q2 = {f_y, f_z}, q3 = f_x; 2D: q2 = {f_x, f_y}
+            float2 q2[NN];
+            float q3[D == 3 ? NN : 1];
+#pragma unroll
+            for (int i = 0; i < NN; ++i) {
+                q2[i] = f2(0.f, 0.f);
+                if (D == 3) q3[i] = 0.f;
+            }
+            float nx[3], nM, nr, nE, nQ;
+#pragma unroll
+            for (int a = 0; a < D; ++a) nx[a] = pt.x[a][b];
+            nM = pt.M[b]; nr = pt.rho[b]; nE = pt.E[b]; nQ = pt.Q[b];
+            for (uint32_t k = b; k < e; ++k) {
+                float x[3];
+#pragma unroll
+                for (int a = 0; a < D; ++a) x[a] = nx[a];
+                const float M = nM, rho = nr, E = nE, Q = nQ;
+                if (k + 1 < e) {
+#pragma unroll
+                    for (int a = 0; a < D; ++a) nx[a] = pt.x[a][k + 1];
+                    nM = pt.M[k + 1]; nr = pt.rho[k + 1]; nE = pt.E[k + 1]; nQ = pt.Q[k + 1];
+                }
+                float w[3][3], dw[3][3];
+                bool ok = axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
+                ok &= axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+                if (D == 3) ok &= axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
+                if (!ok) { err = 1; continue; }
+                const float F = fmaf(gm1 * rho, E, Q) * __fdividef(M, rho) * ih;
+                if (D == 3) {
+                    float Fx[NS], Fd[NS];
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) { Fx[a] = F * w[0][a]; Fd[a] = F * dw[0][a]; }
+#pragma unroll
+                    for (int j = 0; j < NYZ; ++j) {
+                        const int bb = j % NS, c = j / NS;
+                        const float yz = w[1][bb] * w[2][c];
+                        const float2 dd = f2(dw[1][bb] * w[2][c], w[1][bb] * dw[2][c]);
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) {
+                            const int i = j * NS + a;
+                            q2[i] = __ffma2_rn(f2(Fx[a], Fx[a]), dd, q2[i]);
+                            q3[i] = fmaf(Fd[a], yz, q3[i]);
+                        }
+                    }
+                } else {
+                    float2 cf[NS];
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) cf[a] = f2(F * dw[0][a], F * w[0][a]);
+#pragma unroll
+                    for (int j = 0; j < NYZ; ++j) {
+                        const float2 yd = f2(w[1][j], dw[1][j]);
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) q2[j * NS + a] = __ffma2_rn(cf[a], yd, q2[j * NS + a]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NYZ; ++j)
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    const int i = j * NS + a;
+                    const int slot = base + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0 + a;
+                    if (D == 3) {
+                        atomicAdd(&sm[4 * W + slot], q3[i]);      // f_x
+                        atomicAdd(&sm[5 * W + slot], q2[i].x);    // f_y
+                        atomicAdd(&sm[6 * W + slot], q2[i].y);    // f_z
+                    } else {
+                        atomicAdd(&sm[3 * W + slot], q2[i].x);    // f_x
+                        atomicAdd(&sm[4 * W + slot], q2[i].y);    // f_y
+                    }
+                }
+        }
+    }
+    if (err) atomicOr(&clk->err, ERR_TILE);
+    __syncthreads();
+    flush_window<D, P>(G, so, sm, NF, out);
+}
+
+// ----------------------------------------- K2: grid update + G2P + P2G
+
+template <int D, int P, bool PER>
+__global__ void __launch_bounds__(kSpanThreads, 3) k_grid_g2p_span(Geom G, Particles<float> pt,
+                                                                   Grid<float, float> gr, FieldPtrs out,
+                                                                   const uint32_t* __restrict__ cs, Clock* clk)
+{
+    if (!clk->active) return;
+    const int tile = blockIdx.x;
+    const int64_t kb = (int64_t)tile * G.Tvol;
+    if (cs[kb] == cs[kb + G.Tvol]) return;
+    extern __shared__ __align__(16) float sm[];
+    constexpr int NS = P + 1, NYZ = (D == 3) ? NS * NS : NS, NN = NYZ * NS;
+    const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
+    float4* sA = reinterpret_cast<float4*>(sm);              // W records: f/m after BC
+    float* s2 = sm + 4 * W;                                   // D x W: momentum P2G
+    float* stage = s2 + D * W;                                // per warp: D x kStageCap
+    int so[3];
+    tile_origin(G, tile, so);
+    const float dt = (float)clk->dt_cur;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        int idx[3];
+        const int64_t node = slot_node<P>(G, so, i, idx);
+        float f[3] = {0.f, 0.f, 0.f}, m = 0.f;
+        if (node >= 0) {
+            m = gr.m[node];
+#pragma unroll
+            for (int a = 0; a < D; ++a) f[a] = gr.f[a][node];
+            node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
+        }
+        const float im = m != 0.f ? __frcp_rn(m) : 0.f;
+        sA[i] = make_float4(f[0] * im, f[1] * im, D == 3 ? f[2] * im : 0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < D; ++a) s2[a * W + i] = 0.f;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* wst = stage + warp * D * kStageCap;
+    float vmax = 0.f;
+    int err = 0;
+    const float ih = (float)G.inv_h;
+    float lo[3], nper[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (float)G.lo[a];
+        nper[a] = G.per[a] ? (float)G.n[a] : 3.0e38f;
+    }
+    // a warp covers 32 consecutive spans per round; their particles are one range
+    for (int s0 = warp * 32; s0 < G.Tvol; s0 += blockDim.x) {
+        const int s = s0 + lane;
+        const bool has = s < G.Tvol;
+        const uint32_t rb = cs[kb + s0], re = cs[kb + min(s0 + 32, G.Tvol)];
+        const bool staged = (re - rb) <= (uint32_t)kStageCap;
+        const uint32_t b = has ? cs[kb + s] : 0u, e = has ? cs[kb + s + 1] : 0u;
+        // 3D: r0 = {mv2_x, mv2_y}, r1 = mv2_z; 2D: r0 = {mv2_x, mv2_y}
+        float2 r0[NN];
+        float r1[D == 3 ? NN : 1];
+#pragma unroll
+        for (int i = 0; i < NN; ++i) {
+            r0[i] = f2(0.f, 0.f);
+            if (D == 3) r1[i] = 0.f;
+        }
+        const int lx = s & (G.T[0] - 1);
+        const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
+        const int lz = s >> (G.tsh[0] + G.tsh[1]);
+        const int base = (lz * W1 + ly) * W0 + lx;
+        const float cb0 = (float)(so[0] + lx - (P == 2 ? 1 : 0));
+        const float cb1 = (float)(so[1] + ly - (P == 2 ? 1 : 0));
+        const float cb2 = (float)(so[2] + lz - (P == 2 ? 1 : 0));
+        PState<D> nx;
+        if (b != e) load_state<D, false>(pt, b, nx);
+        for (uint32_t k = b; k < e; ++k) {
+            const PState<D> cur = nx;
+            if (k + 1 < e) load_state<D, false>(pt, k + 1, nx);
+            float w[3][3], dw[3][3];
+            bool ok = axis_known<P, PER>(cur.x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
+            ok &= axis_known<P, PER>(cur.x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+            if (D == 3) ok &= axis_known<P, PER>(cur.x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
+            if (!ok) { err = 1; continue; }
+            float yz[NYZ];
+#pragma unroll
+            for (int c = 0; c < (D == 3 ? NS : 1); ++c)
+#pragma unroll
+                for (int bb = 0; bb < NS; ++bb) yz[c * NS + bb] = D == 3 ? w[1][bb] * w[2][c] : w[1][bb];
+            // A = G2P(f / m)
+            float A0 = 0.f, A1 = 0.f, A2 = 0.f;
+#pragma unroll
+            for (int j = 0; j < NYZ; ++j) {
+                const int row = base + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0;
+                float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    const float4 q = sA[row + a];
+                    x0 = fmaf(w[0][a], q.x, x0);
+                    x1 = fmaf(w[0][a], q.y, x1);
+                    x2 = fmaf(w[0][a], q.z, x2);
+                }
+                A0 = fmaf(yz[j], x0, A0);
+                A1 = fmaf(yz[j], x1, A1);
+                A2 = fmaf(yz[j], x2, A2);
+            }
+            const float vn0 = fmaf(dt, A0, cur.v[0]);
+            const float vn1 = fmaf(dt, A1, cur.v[1]);
+            const float vn2 = D == 3 ? fmaf(dt, A2, cur.v[2]) : 0.f;
+            vmax = fmaxf(vmax, fmaf(vn2, vn2, fmaf(vn1, vn1, vn0 * vn0)));
+            if (staged) {
+                wst[k - rb] = vn0;
+                wst[kStageCap + k - rb] = vn1;
+                if (D == 3) wst[2 * kStageCap + k - rb] = vn2;
+            } else {
+                pt.v[0][k] = vn0;
+                pt.v[1][k] = vn1;
+                if (D == 3) pt.v[D - 1][k] = vn2;
+            }
+            const float M = cur.M;
+            float2 cm[NS];
+            float cz[NS];
+#pragma unroll
+            for (int a = 0; a < NS; ++a) {
+                cm[a] = f2(M * vn0 * w[0][a], M * vn1 * w[0][a]);
+                cz[a] = M * vn2 * w[0][a];
+            }
+#pragma unroll
+            for (int j = 0; j < NYZ; ++j) {
+                const float2 yy = f2(yz[j], yz[j]);
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    r0[j * NS + a] = __ffma2_rn(cm[a], yy, r0[j * NS + a]);
+                    if (D == 3) r1[j * NS + a] = fmaf(cz[a], yz[j], r1[j * NS + a]);
+                }
+            }
+        }
+        if (b != e) {
+#pragma unroll
+            for (int j = 0; j < NYZ; ++j)
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    const int slot = base + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0 + a;
+                    atomicAdd(&s2[slot], r0[j * NS + a].x);
+                    atomicAdd(&s2[W + slot], r0[j * NS + a].y);
+                    if (D == 3) atomicAdd(&s2[2 * W + slot], r1[j * NS + a]);
+                }
+        }
+        __syncwarp();
+        if (staged) {
+            for (uint32_t i = lane; i < re - rb; i += 32)
+#pragma unroll
+                for (int d = 0; d < D; ++d) pt.v[d][rb + i] = wst[d * kStageCap + i];
+        }
+        __syncwarp();
+    }
+    vmax = warp_max(vmax);
+    if (lane == 0) atomic_max_nonneg(&clk->vmax_bits, (double)sqrtf(vmax));
+    if (err) atomicOr(&clk->err, ERR_TILE);
+    __syncthreads();
+    flush_window<D, P>(G, so, s2, D, out);
+}
+
+// ------------------------------- K3: G2PD + particle update + move + key
+
+template <int D, int P>
+__global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, Grid<float, float> gr,
+                                                   const uint32_t* __restrict__ cs, Clock* clk)
+{
+    if (!clk->active) return;
+    const int tile = blockIdx.x;
+    const uint32_t beg = cs[(int64_t)tile * G.Tvol];
+    const uint32_t end = cs[(int64_t)(tile + 1) * G.Tvol];
+    if (beg == end) return;
+    extern __shared__ __align__(16) float4 sn[];   // per node: {Vb, V2} records
+    constexpr int NS = P + 1;
+    const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
+    int so[3];
+    tile_origin(G, tile, so);
+    const float dt = (float)clk->dt_cur;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        int idx[3];
+        const int64_t node = slot_node<P>(G, so, i, idx);
+        float mv[3] = {0.f, 0.f, 0.f}, f[3] = {0.f, 0.f, 0.f}, m2[3] = {0.f, 0.f, 0.f}, m = 0.f;
+        if (node >= 0) {
+            m = gr.m[node];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                mv[a] = gr.mv[a][node];
+                f[a] = gr.f[a][node];
+                m2[a] = gr.mv2[a][node];
+            }
+            node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, mv, 0);
+            node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
+            node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, m2, 0);
+        }
+        const float im = m != 0.f ? __frcp_rn(m) : 0.f;
+        float vb[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vb[a] = fmaf(dt, f[a], mv[a]) * im;
+        if (D == 3) {
+            sn[2 * i] = make_float4(vb[0], vb[1], vb[2], m2[0] * im);
+            sn[2 * i + 1] = make_float4(m2[1] * im, m2[2] * im, 0.f, 0.f);
+        } else {
+            sn[i] = make_float4(vb[0], vb[1], m2[0] * im, m2[1] * im);
+        }
+    }
+    __syncthreads();
+    const float gm1 = (float)(G.gamma - 1.0), gam = (float)G.gamma, ih = (float)G.inv_h, hh = (float)G.h;
+    const float c0 = (float)G.c0, c1 = (float)G.c1;
+    float vmax = 0.f, cmax = 0.f;
+    int err = 0;
+    for (uint32_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
+        float x[3], w[3][3], dw[3][3];
+        int l[3] = {0, 0, 0}, csp[3] = {0, 0, 0};
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            x[a] = pt.x[a][k];
+            float xi;
+            const int c = span_of<float, P>(G, a, x[a], xi);
+            csp[a] = c;
+            weights1d<P>(__fsub_rn(xi, (float)(c - (P == 2 ? 1 : 0))), w[a], dw[a]);
+            l[a] = wrap_span(G, a, c) - so[a];
+            ok = ok && l[a] >= 0 && l[a] < G.T[a];
+        }
+        const float rho = pt.rho[k], E = pt.E[k], Q = pt.Q[k];
+        if (!ok) { err |= ERR_TILE; continue; }
+        const int base = (l[2] * W1 + l[1]) * W0 + l[0];
+        // Vbar = G2P(mv'/m); div V = trace of G2PD(mv2/m)
+        float vb[3] = {0.f, 0.f, 0.f}, dx = 0.f, dy = 0.f, dz = 0.f;
+#pragma unroll
+        for (int c = 0; c < (D == 3 ? NS : 1); ++c) {
+            float pv[3] = {0.f, 0.f, 0.f}, px = 0.f, py = 0.f, pz = 0.f;
+#pragma unroll
+            for (int bb = 0; bb < NS; ++bb) {
+                const int row = base + (c * W1 + bb) * W0;
+                float r0 = 0.f, r1 = 0.f, r2 = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    if (D == 3) {
+                        const float4 q0 = sn[2 * (row + a)], q1 = sn[2 * (row + a) + 1];
+                        r0 = fmaf(w[0][a], q0.x, r0);
+                        r1 = fmaf(w[0][a], q0.y, r1);
+                        r2 = fmaf(w[0][a], q0.z, r2);
+                        gx = fmaf(dw[0][a], q0.w, gx);
+                        gy = fmaf(w[0][a], q1.x, gy);
+                        gz = fmaf(w[0][a], q1.y, gz);
+                    } else {
+                        const float4 q = sn[row + a];
+                        r0 = fmaf(w[0][a], q.x, r0);
+                        r1 = fmaf(w[0][a], q.y, r1);
+                        gx = fmaf(dw[0][a], q.z, gx);
+                        gy = fmaf(w[0][a], q.w, gy);
+                    }
+                }
+                pv[0] = fmaf(w[1][bb], r0, pv[0]);
+                pv[1] = fmaf(w[1][bb], r1, pv[1]);
+                pv[2] = fmaf(w[1][bb], r2, pv[2]);
+                px = fmaf(w[1][bb], gx, px);
+                py = fmaf(dw[1][bb], gy, py);
+                pz = fmaf(w[1][bb], gz, pz);
+            }
+            const float wz = D == 3 ? w[2][c] : 1.f, dwz = D == 3 ? dw[2][c] : 0.f;
+            vb[0] = fmaf(wz, pv[0], vb[0]);
+            vb[1] = fmaf(wz, pv[1], vb[1]);
+            vb[2] = fmaf(wz, pv[2], vb[2]);
+            dx = fmaf(wz, px, dx);
+            dy = fmaf(wz, py, dy);
+            dz = fmaf(dwz, pz, dz);
+        }
+        const float dv = (dx + dy + (D == 3 ? dz : 0.f)) * ih;
+        // Sec. 3 step viii: energy, density, pressure, artificial viscosity
+        const float irho = __frcp_rn(rho);
+        const float Pk = gm1 * rho * E;
+        const float En = E - dt * (Pk + Q) * irho * dv;
+        const float den = 1.0f + dt * dv;
+        if (!(den > 0.f)) { err |= ERR_NONFINITE; continue; }
+        const float rn = __fdividef(rho, den);
+        const float Pn = gm1 * rn * En;
+        const float c2 = gam * gm1 * En;       // gamma P / rho with P = (gamma - 1) rho e
+        const float cs = sqrtf(c2 > 0.f ? c2 : 0.f);
+        float Qn = 0.f;
+        if (dv < 0.f) {
+            const float t1 = rn * hh * dv;
+            Qn = c0 * t1 * t1 - c1 * hh * cs * dv;
+        }
+        (void)Pn;
+        // step ix: move with Vbar; step x: wrap / hold / recycle; new key
+        float xn[3] = {0.f, 0.f, 0.f}, vb2 = 0.f;
+        int cn[3] = {0, 0, 0};
+        bool out = false, fin = isfinite(En) && isfinite(rn) && isfinite(Qn);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            xn[a] = __fadd_rn(x[a], __fmul_rn(dt, vb[a]));
+            vb2 = fmaf(vb[a], vb[a], vb2);
+            fin = fin && isfinite(xn[a]);
+            float xi;
+            cn[a] = span_of<float, P>(G, a, xn[a], xi);
+            const int d = cn[a] - csp[a];
+            if (d < -1 || d > 1) err |= ERR_CFL;
+            if (!G.per[a]) {
+                if (xn[a] < (float)G.lo[a] && G.bc[2 * a] == 3) out = true;
+                if (xn[a] >= (float)G.hi[a] && G.bc[2 * a + 1] == 3) out = true;
+            }
+        }
+        if (!fin) { err |= ERR_NONFINITE; continue; }
+        float En_s = En, rn_s = rn, Qn_s = Qn, cpart = cs;
+        int sp[3] = {0, 0, 0};
+        if (out && G.inflow_face >= 0) {
+            const uint32_t gk = pt.gen[k];
+            uint32_t c[4] = {gk, 0u, pt.id[k], 0u};
+            philox4x32_10(c, (uint32_t)G.seed, (uint32_t)(G.seed >> 32));
+            pt.gen[k] = gk + 1u;
+            const int af = G.inflow_face / 2, side = G.inflow_face % 2;
+            float vin2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float u = __fmul_rn((float)(c[a] >> 8), 1.0f / 16777216.0f);
+                if (a == af)
+                    xn[a] = side == 0 ? __fadd_rn((float)G.lo[a], __fmul_rn(u, hh))
+                                      : __fadd_rn(__fsub_rn((float)G.hi[a], hh), __fmul_rn(u, hh));
+                else
+                    xn[a] = __fadd_rn((float)G.lo[a], __fmul_rn(u, __fsub_rn((float)G.hi[a], (float)G.lo[a])));
+                const float vi = (float)G.inflow_v[a];
+                pt.v[a][k] = vi;
+                vin2 = fmaf(vi, vi, vin2);
+                float xi;
+                sp[a] = wrap_span(G, a, span_of<float, P>(G, a, xn[a], xi));
+            }
+            En_s = (float)G.inflow_e;
+            rn_s = (float)G.inflow_rho;
+            Qn_s = 0.f;
+            const float ci2 = gam * gm1 * En_s;
+            cpart = sqrtf(ci2 > 0.f ? ci2 : 0.f);
+            vmax = fmaxf(vmax, sqrtf(vin2));
+        } else {
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float lo = (float)G.lo[a], hi = (float)G.hi[a];
+                if (G.per[a]) {
+                    const float L = __fsub_rn(hi, lo);
+                    if (xn[a] < lo) xn[a] = __fadd_rn(xn[a], L);
+                    else if (xn[a] >= hi) xn[a] = __fsub_rn(xn[a], L);
+                    float xi;
+                    sp[a] = wrap_span(G, a, span_of<float, P>(G, a, xn[a], xi));
+                } else {
+                    // holding the particle at a face keeps its (clamped) span
+                    xn[a] = fminf(fmaxf(xn[a], lo), hi);
+                    sp[a] = cn[a];
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) pt.x[a][k] = xn[a];
+        pt.key[k] = key_of<float>(G, sp);
+        pt.E[k] = En_s;
+        pt.rho[k] = rn_s;
+        pt.Q[k] = Qn_s;
+        vmax = fmaxf(vmax, sqrtf(vb2));
+        cmax = fmaxf(cmax, cpart);
+    }
+    vmax = warp_max(vmax);
+    cmax = warp_max(cmax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) err |= __shfl_xor_sync(0xffffffffu, err, o);
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(&clk->vmax_bits, (double)vmax);
+        atomic_max_nonneg(&clk->cmax_bits, (double)cmax);
+        if (err) atomicOr(&clk->err, err);
+    }
+}
+
+}  // namespace mpm

@@ -22,8 +22,10 @@ enum : int { ERR_NONFINITE = 1, ERR_CFL = 2, ERR_TILE = 4 };
 struct Geom {
     int dim, p;
     int n[3], per[3], S[3], N[3], g[3], T[3], nt[3], W[3];
+    int tsh[3];                     // log2 of the tile edges (powers of two)
     int Tvol, Wvol, ntiles;
-    int64_t nnode, nkey;
+    int pitch;                      // stored x-extent of a node row (N[0] rounded up to 4)
+    int64_t nnode, nnode_p, nkey;   // nodes, stored nodes (padded rows), keys
     int bc[6];
     int inflow_face;                // -1: none
     double h, inv_h, lo[3], hi[3];
@@ -37,8 +39,7 @@ struct Clock {
     double t, t_end, dt_fixed, dt_next, dt_cur;
     long long step;
     int active, done, last, err;
-    unsigned vmax_bits, cmax_bits;
-    int pad[2];
+    unsigned long long vmax_bits, cmax_bits;   // bits of non-negative doubles
 };
 
 template <class R>
@@ -51,6 +52,7 @@ struct Particles {
     R* Q;
     uint32_t* id;
     uint32_t* key;
+    uint32_t* gen;   // times the particle has been recycled (keys its Philox draw)
 };
 
 template <class A, class R>
@@ -192,7 +194,7 @@ __device__ __forceinline__ int64_t slot_node(const Geom& G, const int so[3], int
         }
         idx[a] = i;
     }
-    return ((int64_t)idx[2] * G.N[1] + idx[1]) * G.N[0] + idx[0];
+    return ((int64_t)idx[2] * G.N[1] + idx[1]) * G.pitch + idx[0];
 }
 
 // Grid boundary conditions of one node (Sec. 3 steps iii and vii): obstacle
@@ -237,9 +239,8 @@ __device__ __forceinline__ void node_bc(const Geom& G, const uint8_t* mask, cons
 template <class R>
 __device__ __forceinline__ uint32_t key_of(const Geom& G, const int sp[3])
 {
-    int t = 0, l = 0;
-    t = ((sp[2] / G.T[2]) * G.nt[1] + sp[1] / G.T[1]) * G.nt[0] + sp[0] / G.T[0];
-    l = ((sp[2] % G.T[2]) * G.T[1] + sp[1] % G.T[1]) * G.T[0] + sp[0] % G.T[0];
+    const int t = ((sp[2] >> G.tsh[2]) * G.nt[1] + (sp[1] >> G.tsh[1])) * G.nt[0] + (sp[0] >> G.tsh[0]);
+    const int l = (((sp[2] & (G.T[2] - 1)) << G.tsh[1]) + (sp[1] & (G.T[1] - 1))) << G.tsh[0] | (sp[0] & (G.T[0] - 1));
     return (uint32_t)t * (uint32_t)G.Tvol + (uint32_t)l;
 }
 
@@ -257,9 +258,18 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
     }
 }
 
-__device__ __forceinline__ void atomic_max_nonneg(unsigned* p, float v)
+// Non-negative doubles order like their bit patterns as unsigned integers.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double v)
 {
-    if (v > 0.f) atomicMax(p, __float_as_uint(v));
+    if (v > 0.0) atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+template <class R>
+__device__ __forceinline__ R warp_max(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
 // ------------------------------------------------------------------ P2G
@@ -395,7 +405,7 @@ __global__ void __launch_bounds__(256) k_grid_g2p(Geom G, Particles<R> pt, Grid<
     }
     __syncthreads();
     constexpr int NS = P + 1;
-    float vmax = 0.f;
+    R vmax = (R)0;
     for (uint32_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
         AxisSup<R> sx[3];
         bool ok = true;
@@ -428,7 +438,7 @@ __global__ void __launch_bounds__(256) k_grid_g2p(Geom G, Particles<R> pt, Grid<
             MV[a] = O::mul(M, vn);
             v2 = O::add(v2, O::mul(vn, vn));
         }
-        vmax = fmaxf(vmax, (float)O::sqr(v2));
+        vmax = fmax(vmax, O::sqr(v2));
 #pragma unroll
         for (int kz = 0; kz < (D == 3 ? NS : 1); ++kz)
 #pragma unroll
@@ -444,9 +454,8 @@ __global__ void __launch_bounds__(256) k_grid_g2p(Geom G, Particles<R> pt, Grid<
                 }
     }
     // block max of |V'| for the CFL rule
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&clk->vmax_bits, vmax);
+    vmax = warp_max(vmax);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&clk->vmax_bits, (double)vmax);
     __syncthreads();
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         int idx[3];
@@ -507,7 +516,7 @@ __global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R
     constexpr int NS = P + 1;
     const R gm1 = (R)(G.gamma - 1.0), gam = (R)G.gamma, ih = (R)G.inv_h, hh = (R)G.h;
     const R c0 = (R)G.c0, c1 = (R)G.c1;
-    float vmax = 0.f, cmax = 0.f;
+    R vmax = (R)0, cmax = (R)0;
     int err = 0;
     for (uint32_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
         AxisSup<R> sx[3];
@@ -577,12 +586,12 @@ __global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R
         }
         if (!fin) { err |= ERR_NONFINITE; continue; }
         R En_s = En, rn_s = rn, Qn_s = Qn;
-        float cpart = (float)cs;
+        R cpart = cs;
         if (out && G.inflow_face >= 0) {
-            uint32_t id = pt.id[k];
-            unsigned long long st = (unsigned long long)clk->step;
-            uint32_t c[4] = {(uint32_t)st, (uint32_t)(st >> 32), id, 0u};
+            const uint32_t gk = pt.gen[k];
+            uint32_t c[4] = {gk, 0u, pt.id[k], 0u};
             philox4x32_10(c, (uint32_t)G.seed, (uint32_t)(G.seed >> 32));
+            pt.gen[k] = gk + 1u;
             const int af = G.inflow_face / 2, side = G.inflow_face % 2;
             R vin2 = (R)0;
 #pragma unroll
@@ -600,8 +609,8 @@ __global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R
             rn_s = (R)G.inflow_rho;
             Qn_s = (R)0;
             R ci2 = O::dvd(O::mul(gam, O::mul(O::mul(gm1, rn_s), En_s)), rn_s);
-            cpart = (float)O::sqr(ci2 > (R)0 ? ci2 : (R)0);
-            vmax = fmaxf(vmax, (float)O::sqr(vin2));
+            cpart = O::sqr(ci2 > (R)0 ? ci2 : (R)0);
+            vmax = fmax(vmax, O::sqr(vin2));
         } else {
 #pragma unroll
             for (int a = 0; a < D; ++a) {
@@ -627,18 +636,16 @@ __global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R
         pt.E[k] = En_s;
         pt.rho[k] = rn_s;
         pt.Q[k] = Qn_s;
-        vmax = fmaxf(vmax, (float)O::sqr(vb2));
-        cmax = fmaxf(cmax, cpart);
+        vmax = fmax(vmax, O::sqr(vb2));
+        cmax = fmax(cmax, cpart);
     }
+    vmax = warp_max(vmax);
+    cmax = warp_max(cmax);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-        err |= __shfl_xor_sync(0xffffffffu, err, o);
-    }
+    for (int o = 16; o > 0; o >>= 1) err |= __shfl_xor_sync(0xffffffffu, err, o);
     if ((threadIdx.x & 31) == 0) {
-        atomic_max_nonneg(&clk->vmax_bits, vmax);
-        atomic_max_nonneg(&clk->cmax_bits, cmax);
+        atomic_max_nonneg(&clk->vmax_bits, (double)vmax);
+        atomic_max_nonneg(&clk->cmax_bits, (double)cmax);
         if (err) atomicOr(&clk->err, err);
     }
 }
@@ -656,8 +663,8 @@ __global__ void k_prepare(Clock* clk)
     if (c.t_end > 0.0 && c.t + h >= c.t_end) { h = c.t_end - c.t; c.last = 1; }
     c.dt_cur = h;
     c.active = 1;
-    c.vmax_bits = 0u;
-    c.cmax_bits = 0u;
+    c.vmax_bits = 0ull;
+    c.cmax_bits = 0ull;
 }
 
 __global__ void k_finalize(Clock* clk, double cfl_h)
@@ -666,7 +673,8 @@ __global__ void k_finalize(Clock* clk, double cfl_h)
     if (!c.active) return;
     c.t = c.last ? c.t_end : c.t + c.dt_cur;
     c.step += 1;
-    const double v = (double)__uint_as_float(c.vmax_bits), cs = (double)__uint_as_float(c.cmax_bits);
+    const double v = __longlong_as_double((long long)c.vmax_bits);
+    const double cs = __longlong_as_double((long long)c.cmax_bits);
     c.dt_next = (v + cs) > 0.0 ? cfl_h / (v + cs) : 0.0;
     if (c.last || (c.t_end > 0.0 && c.t >= c.t_end)) c.done = 1;
 }
@@ -686,35 +694,33 @@ template <int D, class R>
 __global__ void k_cfl_init(Geom G, Particles<R> pt, int64_t n, Clock* clk)
 {
     typedef Op<R> O;
-    float vmax = 0.f, cmax = 0.f;
+    R vmax = (R)0, cmax = (R)0;
     const R gm1 = (R)(G.gamma - 1.0), gam = (R)G.gamma;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         R v2 = (R)0;
 #pragma unroll
         for (int a = 0; a < D; ++a) v2 = O::add(v2, O::mul(pt.v[a][k], pt.v[a][k]));
-        vmax = fmaxf(vmax, (float)O::sqr(v2));
+        vmax = fmax(vmax, O::sqr(v2));
         R P = O::mul(O::mul(gm1, pt.rho[k]), pt.E[k]);
         R c2 = O::dvd(O::mul(gam, P), pt.rho[k]);
-        cmax = fmaxf(cmax, (float)O::sqr(c2 > (R)0 ? c2 : (R)0));
+        cmax = fmax(cmax, O::sqr(c2 > (R)0 ? c2 : (R)0));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-    }
+    vmax = warp_max(vmax);
+    cmax = warp_max(cmax);
     if ((threadIdx.x & 31) == 0) {
-        atomic_max_nonneg(&clk->vmax_bits, vmax);
-        atomic_max_nonneg(&clk->cmax_bits, cmax);
+        atomic_max_nonneg(&clk->vmax_bits, (double)vmax);
+        atomic_max_nonneg(&clk->cmax_bits, (double)cmax);
     }
 }
 
 __global__ void k_cfl_init_finish(Clock* clk, double cfl_h)
 {
     Clock& c = *clk;
-    const double v = (double)__uint_as_float(c.vmax_bits), cs = (double)__uint_as_float(c.cmax_bits);
+    const double v = __longlong_as_double((long long)c.vmax_bits);
+    const double cs = __longlong_as_double((long long)c.cmax_bits);
     c.dt_next = (v + cs) > 0.0 ? cfl_h / (v + cs) : 0.0;
-    c.vmax_bits = 0u;
-    c.cmax_bits = 0u;
+    c.vmax_bits = 0ull;
+    c.cmax_bits = 0ull;
 }
 
 // ----------------------------------------------------- keys and gathering
@@ -752,6 +758,7 @@ __global__ void k_gather(Particles<R> in, Particles<R> out, const uint32_t* perm
     out.E[j] = in.E[s];
     out.Q[j] = in.Q[s];
     out.id[j] = in.id[s];
+    out.gen[j] = in.gen[s];
     out.key[j] = act ? sorted_keys[j] : in.key[s];
 }
 
