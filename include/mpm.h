@@ -170,6 +170,30 @@ mpm_status mpm_sizes(const mpm_sim* sim, int64_t out[4]);
 mpm_status mpm_profile(mpm_sim* sim, int enable);
 mpm_status mpm_profile_read(mpm_sim* sim, double out[8], int64_t counts[8], int reset);
 
+/* Stable sort of caller-supplied span keys that allocates no device memory.
+ * The paper has no counterpart: this is the library's re-order step (a1)
+ * offered to callers that must not call cudaMalloc -- code recording into a
+ * CUDA graph, components confined to another framework's memory pool, or
+ * loops where an allocation could synchronise the device.  Its scratch lives
+ * in fixed device arrays inside the library (3.1 MiB per GPU that loads the
+ * library, held until the process exits), so the input size is capped.
+ *   keys        device pointer, n keys, each < nkeys (not modified)
+ *   n           0 <= n <= MPM_SORT_STATIC_MAX_KEYS, else MPM_EINVAL
+ *   nkeys       1 <= nkeys <= MPM_SORT_STATIC_MAX_SPANS, else MPM_EINVAL
+ *   perm        device pointer, n entries: perm[j] = index of the key placed
+ *               at position j (equal keys keep their input order)
+ *   cell_start  device pointer, nkeys + 1 entries: first position of each key
+ *   stream      cudaStream_t the work is queued on (NULL: the default stream)
+ * The call only queues kernels and returns; the outputs are valid once the
+ * stream reaches them.  The first call on a device looks up the scratch
+ * addresses, so make it before any stream capture.  All calls on a device
+ * share the scratch: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and must be serialised by the caller. */
+#define MPM_SORT_STATIC_MAX_KEYS 262144
+#define MPM_SORT_STATIC_MAX_SPANS 16777216
+mpm_status mpm_sort_keys_static(const uint32_t* keys, int64_t n, int64_t nkeys, uint32_t* perm,
+                                uint32_t* cell_start, void* stream);
+
 /* The simulation's stream (cudaStream_t). */
 void* mpm_stream(const mpm_sim* sim);
 /* Message of the last error of this handle (static storage if sim is NULL). */

@@ -1099,3 +1099,6 @@ void mpm_destroy(mpm_sim* s)
 }
 
 }  // extern "C"
+
+// The allocation-free re-order entry point (same translation unit).
+#include "mpm_noalloc.cu"

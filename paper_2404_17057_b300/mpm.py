@@ -27,7 +27,9 @@ STATUS = {0: "MPM_OK", 1: "MPM_EINVAL", 2: "MPM_ENOMEM", 3: "MPM_ECUDA", 4: "MPM
 EXPORTS = ["mpm_create", "mpm_add_particles", "mpm_set_obstacle_mask", "mpm_cfl_dt", "mpm_step",
            "mpm_step_async", "mpm_sync", "mpm_read_state", "mpm_read_grid_fixed", "mpm_field_size",
            "mpm_conservation", "mpm_sizes", "mpm_profile", "mpm_profile_read", "mpm_stream",
-           "mpm_last_error", "mpm_destroy"]
+           "mpm_last_error", "mpm_destroy", "mpm_sort_keys_static"]
+SORT_STATIC_MAX_KEYS = 262144
+SORT_STATIC_MAX_SPANS = 16777216
 
 
 class MPMError(RuntimeError):
@@ -83,6 +85,7 @@ def load(path: str = LIB_PATH):
     L.mpm_last_error.restype = C.c_char_p
     L.mpm_destroy.argtypes = [vp]
     L.mpm_destroy.restype = None
+    L.mpm_sort_keys_static.argtypes = [vp, i64, i64, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("mpm_field_size", "mpm_stream", "mpm_last_error", "mpm_destroy"):
             getattr(L, name).restype = C.c_int
@@ -270,6 +273,15 @@ def mpm_last_error(h=None) -> str:
 
 def mpm_destroy(h):
     load().mpm_destroy(h)
+
+
+def mpm_sort_keys_static(keys_ptr: int, n: int, nkeys: int, perm_ptr: int, cell_start_ptr: int, stream: int = 0):
+    """Allocation-free stable key sort on caller device buffers (raw pointers).
+
+    For callers that must not allocate device memory (graph capture, a
+    foreign memory pool, latency-critical loops).  n is capped at
+    SORT_STATIC_MAX_KEYS; concurrent calls on one device must not overlap."""
+    _check(load().mpm_sort_keys_static(keys_ptr, int(n), int(nkeys), perm_ptr, cell_start_ptr, stream or None))
 
 
 # ------------------------------------------------------------ convenience
