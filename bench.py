@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override the grid size (cells per axis / x cells)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_fixed64", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="also run the serving stream with this many requests (batched vs one at a time)")
+    ap.add_argument("--serve-steps", type=int, default=500)
+    ap.add_argument("--saturated", action="store_true", help="serving: all requests arrive at t=0")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -193,6 +197,18 @@ def problem_meta_only(args):
                   "cells": [nx, nx // 2]}
 
 
+def serving(args):
+    """C5: continuous batching vs one-at-a-time plain solves on the same stream."""
+    from paper_2404_17057_b300 import inputs as I, serve as S
+    reqs = I.serving_stream(count=args.serve, seed=5, steps=args.serve_steps)
+    rt = not args.saturated
+    _, batched = S.Server().run(reqs, realtime=rt)
+    _, single = S.run_sequential(reqs, realtime=rt)
+    return {"requests": len(reqs), "steps_each": args.serve_steps, "arrivals": "all at t=0" if args.saturated
+            else "Poisson 50/s", "precision": "fp32_fixed64", "batched": batched, "one_at_a_time": single,
+            "speedup_solves_per_s": batched["solves_per_s"] / single["solves_per_s"]}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -256,6 +272,7 @@ def main():
     if not args.no_e2e and rank == 0:
         e2e = end_to_end(M, p, args)
     sim.close()
+    serve = serving(args) if (args.serve and rank == 0) else None
 
     if rank != 0:
         return
@@ -279,6 +296,8 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cb,
     }
+    if serve:
+        line["serving"] = serve
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -622,7 +622,7 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
     }
     int bits = 1;
     while (((int64_t)1 << bits) < s->G.nkey) ++bits;
-    s->radix_passes = (bits + 7) / 8;
+    s->radix_passes = (bits + kRadixBitsMax - 1) / kRadixBitsMax;
     s->radix_bits = (bits + s->radix_passes - 1) / s->radix_passes;
     *out = s;
     return MPM_OK;

@@ -555,13 +555,33 @@ __global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, 
     const float c0 = (float)G.c0, c1 = (float)G.c1;
     float vmax = 0.f, cmax = 0.f;
     int err = 0;
+    // the next particle's state is loaded while this one is processed
+    float px[3] = {0.f, 0.f, 0.f}, prho = 0.f, pE = 0.f, pQ = 0.f;
+    if (beg + threadIdx.x < end) {
+        const uint32_t k0 = beg + threadIdx.x;
+#pragma unroll
+        for (int a = 0; a < D; ++a) px[a] = pt.x[a][k0];
+        prho = pt.rho[k0];
+        pE = pt.E[k0];
+        pQ = pt.Q[k0];
+    }
     for (uint32_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
         float x[3], w[3][3], dw[3][3];
         int l[3] = {0, 0, 0}, csp[3] = {0, 0, 0};
         bool ok = true;
 #pragma unroll
+        for (int a = 0; a < D; ++a) x[a] = px[a];
+        const float rho = prho, E = pE, Q = pQ;
+        if (k + blockDim.x < end) {
+            const uint32_t kn = k + blockDim.x;
+#pragma unroll
+            for (int a = 0; a < D; ++a) px[a] = pt.x[a][kn];
+            prho = pt.rho[kn];
+            pE = pt.E[kn];
+            pQ = pt.Q[kn];
+        }
+#pragma unroll
         for (int a = 0; a < D; ++a) {
-            x[a] = pt.x[a][k];
             float xi;
             const int c = span_of<float, P>(G, a, x[a], xi);
             csp[a] = c;
@@ -569,7 +589,6 @@ __global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, 
             l[a] = wrap_span(G, a, c) - so[a];
             ok = ok && l[a] >= 0 && l[a] < G.T[a];
         }
-        const float rho = pt.rho[k], E = pt.E[k], Q = pt.Q[k];
         if (!ok) { err |= ERR_TILE; continue; }
         const int base = (l[2] * W1 + l[1]) * W0 + l[0];
         // Vbar = G2P(mv'/m); div V = trace of G2PD(mv2/m)

@@ -117,13 +117,15 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;                      // per thread
 constexpr int kSortTile = kSortThreads * kSortItems; // elements per block
 constexpr int kWarpSpan = kSortTile / kSortWarps;   // contiguous elements per warp
+constexpr int kRadixBitsMax = 9;                    // digits of up to 9 bits
+constexpr int kRadixMax = 1 << kRadixBitsMax;
 
 // Digit histogram of each block, stored digit-major: hist[d * nblocks + b].
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* keys, int64_t n, int shift, int bits,
                                                              uint32_t* hist, const int* active)
 {
     if (active && !*active) return;
-    __shared__ uint32_t h[256];
+    __shared__ uint32_t h[kRadixMax];
     const int radix = 1 << bits;
     for (int i = threadIdx.x; i < radix; i += blockDim.x) h[i] = 0;
     __syncthreads();
@@ -145,10 +147,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
                                                                 const int* active, int first_pass)
 {
     if (active && !*active) return;
-    __shared__ uint32_t cnt[kSortWarps][256];
+    __shared__ uint32_t cnt[kSortWarps][kRadixMax];
     const int radix = 1 << bits;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kSortWarps * 256; i += blockDim.x) (&cnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kSortWarps * kRadixMax; i += blockDim.x) (&cnt[0][0])[i] = 0;
     __syncthreads();
     const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * kWarpSpan;
     for (int c = 0; c < kWarpSpan; c += 32) {
