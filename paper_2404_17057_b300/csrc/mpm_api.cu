@@ -254,9 +254,9 @@ struct Impl {
                     o.p[1 + D + a] = (float*)gr.f[a];
                 }
                 if (G.per[0] | G.per[1] | G.per[2])
-                    k_p2g_span<D, P, true><<<G.ntiles, kSpanThreads, smem(G, 0), st>>>(G, pt, o, s->cellstart, s->clk);
+                    k_p2g_span<D, P, true><<<G.ntiles, kP2GThreads, smem(G, 0), st>>>(G, pt, o, s->cellstart, s->clk);
                 else
-                    k_p2g_span<D, P, false><<<G.ntiles, kSpanThreads, smem(G, 0), st>>>(G, pt, o, s->cellstart, s->clk);
+                    k_p2g_span<D, P, false><<<G.ntiles, kP2GThreads, smem(G, 0), st>>>(G, pt, o, s->cellstart, s->clk);
             } else {
                 k_p2g<D, P, R, A><<<G.ntiles, kThreads, smem(G, 0), st>>>(G, pt, gr, s->cellstart, s->clk);
             }

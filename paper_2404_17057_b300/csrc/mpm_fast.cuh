@@ -73,6 +73,59 @@ __device__ __forceinline__ bool axis_known(float x, float lo, float ih, float cb
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// Add one node row of a span's contributions into the shared window with the
+// neighbouring spans of the same x-row summed first.  Lane = span x in its
+// row segment of T0 lanes (lx); v[a] = contribution to window node lx + a.
+// Node lx gets v[0] of its own span, v[1] of span lx - 1 and v[2] of span
+// lx - 2 (warp shuffles); the last two lanes of a segment also carry the
+// halo nodes T0 and T0 + 1.  All lanes of the warp must call this together.
+// Same as xrow_add with plain read-add-write instead of atomics: valid when
+// no other warp writes this field of the window at the same time.  Within
+// the instruction every lane writes a different node (lanes of different
+// row segments use different node rows for the same (b, c)).
+template <int NS>
+__device__ __forceinline__ void xrow_rmw(float* row, const float* v, int lx, int T0)
+{
+    float s = v[0];
+#pragma unroll
+    for (int a = 1; a < NS; ++a) {
+        const float u = __shfl_up_sync(0xffffffffu, v[a], a);
+        if (lx >= a) s += u;
+    }
+    row[lx] += s;
+    if (NS == 3) {
+        const float u2 = __shfl_up_sync(0xffffffffu, v[2], 1);
+        const float d2 = __shfl_down_sync(0xffffffffu, v[2], 1);
+        if (lx >= T0 - 2) {
+            const int o = lx == T0 - 1 ? T0 : T0 + 1;
+            row[o] += lx == T0 - 1 ? v[1] + u2 : d2;
+        }
+    } else {
+        if (lx == T0 - 1) row[T0] += v[NS - 1];
+    }
+}
+
+template <int NS>
+__device__ __forceinline__ void xrow_add(float* row, const float* v, int lx, int T0)
+{
+    float s = v[0];
+#pragma unroll
+    for (int a = 1; a < NS; ++a) {
+        const float u = __shfl_up_sync(0xffffffffu, v[a], a);
+        if (lx >= a) s += u;
+    }
+    atomicAdd(row + lx, s);
+    if (NS == 3) {
+        // node T0 = v[1] of lane T0-1 + v[2] of lane T0-2 (added by lane T0-1);
+        // node T0+1 = v[2] of lane T0-1 (added by lane T0-2)
+        const float u2 = __shfl_up_sync(0xffffffffu, v[2], 1);
+        const float d2 = __shfl_down_sync(0xffffffffu, v[2], 1);
+        if (lx >= T0 - 2) atomicAdd(row + (lx == T0 - 1 ? T0 : T0 + 1), lx == T0 - 1 ? v[1] + u2 : d2);
+    } else {
+        if (lx == T0 - 1) atomicAdd(row + T0, v[NS - 1]);
+    }
+}
+
 struct FieldPtrs {
     float* p[7];
 };
@@ -164,11 +217,15 @@ __device__ __forceinline__ void load_state(const Particles<float>& pt, uint32_t 
 
 // ---------------------------------------------------------------- K1: P2G
 
-// A row is 32 consecutive spans (one x-row for the default tiles).  Each row
-// is handled by two warps: group 0 sums m and M V, group 1 the force
-// (P + Q) M/rho grad(phi); both read the same particles.
+// Two warps per CTA: warp 0 sums m and M V, warp 1 the force (P + Q) M/rho
+// grad(phi), each over all spans of the tile, 32 consecutive spans (one
+// x-row for the default tiles) at a time; both read the same particles.
+// Each warp is the only writer of its fields of the window, so the per-span
+// sums go in with plain shared-memory adds.
+constexpr int kP2GThreads = 64;
+
 template <int D, int P, bool PER>
-__global__ void __launch_bounds__(kSpanThreads, 3) k_p2g_span(Geom G, Particles<float> pt, FieldPtrs out,
+__global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, Particles<float> pt, FieldPtrs out,
                                                               const uint32_t* __restrict__ cs, Clock* clk)
 {
     if (!clk->active) return;
@@ -191,12 +248,12 @@ __global__ void __launch_bounds__(kSpanThreads, 3) k_p2g_span(Geom G, Particles<
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int group = warp & 1;
-    const int nrows = G.Tvol >> 5, rstep = blockDim.x >> 6;
+    const int nrows = G.Tvol >> 5;
     int err = 0;
-    for (int r = warp >> 1; r < nrows; r += rstep) {
+    for (int r = 0; r < nrows; ++r) {
         const int s = (r << 5) + lane;
+        // empty spans take part in the warp-wide row adds with zeros
         const uint32_t b = cs[kb + s], e = cs[kb + s + 1];
-        if (b == e) continue;
         const int lx = s & (G.T[0] - 1);
         const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
         const int lz = s >> (G.tsh[0] + G.tsh[1]);
@@ -204,6 +261,10 @@ __global__ void __launch_bounds__(kSpanThreads, 3) k_p2g_span(Geom G, Particles<
         const float cb0 = (float)(so[0] + lx - (P == 2 ? 1 : 0));
         const float cb1 = (float)(so[1] + ly - (P == 2 ? 1 : 0));
         const float cb2 = (float)(so[2] + lz - (P == 2 ? 1 : 0));
+        if (__all_sync(0xffffffffu, b == e)) continue;
+        // x-reduction segment: the spans of this warp chunk that share a row
+        const int tseg = G.T[0] < 32 ? G.T[0] : 32;
+        const int lxw = lane & (tseg - 1);
         if (group == 0) {
             // 3D: q0 = {m, mv_x}, q1 = {mv_y, mv_z}; 2D: q0 = {m, mv_x}, q3 = mv_y
             float2 q0[NN], q1[D == 3 ? NN : 1];
@@ -213,10 +274,12 @@ __global__ void __launch_bounds__(kSpanThreads, 3) k_p2g_span(Geom G, Particles<
                 q0[i] = f2(0.f, 0.f);
                 if (D == 3) q1[i] = f2(0.f, 0.f); else q3[i] = 0.f;
             }
-            float nx[3], nv[3], nM;
+            float nx[3] = {0.f, 0.f, 0.f}, nv[3] = {0.f, 0.f, 0.f}, nM = 0.f;
+            if (b < e) {
 #pragma unroll
-            for (int a = 0; a < D; ++a) { nx[a] = pt.x[a][b]; nv[a] = pt.v[a][b]; }
-            nM = pt.M[b];
+                for (int a = 0; a < D; ++a) { nx[a] = pt.x[a][b]; nv[a] = pt.v[a][b]; }
+                nM = pt.M[b];
+            }
             for (uint32_t k = b; k < e; ++k) {
                 float x[3], v[3];
 #pragma unroll
@@ -255,20 +318,24 @@ __global__ void __launch_bounds__(kSpanThreads, 3) k_p2g_span(Geom G, Particles<
                 }
             }
 #pragma unroll
-            for (int j = 0; j < NYZ; ++j)
+            for (int j = 0; j < NYZ; ++j) {
+                const int row = base - lxw + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0;
+                float v[NS];
 #pragma unroll
-                for (int a = 0; a < NS; ++a) {
-                    const int i = j * NS + a;
-                    const int slot = base + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0 + a;
-                    atomicAdd(&sm[slot], q0[i].x);
-                    atomicAdd(&sm[W + slot], q0[i].y);
-                    if (D == 3) {
-                        atomicAdd(&sm[2 * W + slot], q1[i].x);
-                        atomicAdd(&sm[3 * W + slot], q1[i].y);
-                    } else {
-                        atomicAdd(&sm[2 * W + slot], q3[i]);
-                    }
+                for (int a = 0; a < NS; ++a) v[a] = q0[j * NS + a].x;
+                xrow_rmw<NS>(sm + row, v, lxw, tseg);
+#pragma unroll
+                for (int a = 0; a < NS; ++a) v[a] = q0[j * NS + a].y;
+                xrow_rmw<NS>(sm + W + row, v, lxw, tseg);
+#pragma unroll
+                for (int a = 0; a < NS; ++a) v[a] = D == 3 ? q1[j * NS + a].x : q3[j * NS + a];
+                xrow_rmw<NS>(sm + 2 * W + row, v, lxw, tseg);
+                if (D == 3) {
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) v[a] = q1[j * NS + a].y;
+                    xrow_rmw<NS>(sm + 3 * W + row, v, lxw, tseg);
                 }
+            }
         } else {
             // 3D: q2 = {f_y, f_z}, q3 = f_x; 2D: q2 = {f_x, f_y}
             float2 q2[NN];
@@ -278,10 +345,12 @@ __global__ void __launch_bounds__(kSpanThreads, 3) k_p2g_span(Geom G, Particles<
                 q2[i] = f2(0.f, 0.f);
                 if (D == 3) q3[i] = 0.f;
             }
-            float nx[3], nM, nr, nE, nQ;
+            float nx[3] = {0.f, 0.f, 0.f}, nM = 0.f, nr = 1.f, nE = 0.f, nQ = 0.f;
+            if (b < e) {
 #pragma unroll
-            for (int a = 0; a < D; ++a) nx[a] = pt.x[a][b];
-            nM = pt.M[b]; nr = pt.rho[b]; nE = pt.E[b]; nQ = pt.Q[b];
+                for (int a = 0; a < D; ++a) nx[a] = pt.x[a][b];
+                nM = pt.M[b]; nr = pt.rho[b]; nE = pt.E[b]; nQ = pt.Q[b];
+            }
             for (uint32_t k = b; k < e; ++k) {
                 float x[3];
 #pragma unroll
@@ -327,20 +396,21 @@ __global__ void __launch_bounds__(kSpanThreads, 3) k_p2g_span(Geom G, Particles<
                 }
             }
 #pragma unroll
-            for (int j = 0; j < NYZ; ++j)
+            for (int j = 0; j < NYZ; ++j) {
+                const int row = base - lxw + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0;
+                float v[NS];
+                if (D == 3) {
 #pragma unroll
-                for (int a = 0; a < NS; ++a) {
-                    const int i = j * NS + a;
-                    const int slot = base + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0 + a;
-                    if (D == 3) {
-                        atomicAdd(&sm[4 * W + slot], q3[i]);      // f_x
-                        atomicAdd(&sm[5 * W + slot], q2[i].x);    // f_y
-                        atomicAdd(&sm[6 * W + slot], q2[i].y);    // f_z
-                    } else {
-                        atomicAdd(&sm[3 * W + slot], q2[i].x);    // f_x
-                        atomicAdd(&sm[4 * W + slot], q2[i].y);    // f_y
-                    }
+                    for (int a = 0; a < NS; ++a) v[a] = q3[j * NS + a];
+                    xrow_rmw<NS>(sm + 4 * W + row, v, lxw, tseg);     // f_x
                 }
+#pragma unroll
+                for (int a = 0; a < NS; ++a) v[a] = q2[j * NS + a].x;
+                xrow_rmw<NS>(sm + (D == 3 ? 5 : 3) * W + row, v, lxw, tseg);   // f_y (3D) / f_x (2D)
+#pragma unroll
+                for (int a = 0; a < NS; ++a) v[a] = q2[j * NS + a].y;
+                xrow_rmw<NS>(sm + (D == 3 ? 6 : 4) * W + row, v, lxw, tseg);   // f_z (3D) / f_y (2D)
+            }
         }
     }
     if (err) atomicOr(&clk->err, ERR_TILE);
@@ -480,16 +550,26 @@ __global__ void __launch_bounds__(kSpanThreads, 3) k_grid_g2p_span(Geom G, Parti
                 }
             }
         }
-        if (b != e) {
+        if (__any_sync(0xffffffffu, b != e)) {
+            // all lanes add their rows (zeros for empty spans), x-neighbours summed first
+            const int tseg = G.T[0] < 32 ? G.T[0] : 32;
+            const int lxw = lane & (tseg - 1);
 #pragma unroll
-            for (int j = 0; j < NYZ; ++j)
+            for (int j = 0; j < NYZ; ++j) {
+                const int row = base - lxw + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0;
+                float v[NS];
 #pragma unroll
-                for (int a = 0; a < NS; ++a) {
-                    const int slot = base + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0 + a;
-                    atomicAdd(&s2[slot], r0[j * NS + a].x);
-                    atomicAdd(&s2[W + slot], r0[j * NS + a].y);
-                    if (D == 3) atomicAdd(&s2[2 * W + slot], r1[j * NS + a]);
+                for (int a = 0; a < NS; ++a) v[a] = r0[j * NS + a].x;
+                xrow_add<NS>(s2 + row, v, lxw, tseg);
+#pragma unroll
+                for (int a = 0; a < NS; ++a) v[a] = r0[j * NS + a].y;
+                xrow_add<NS>(s2 + W + row, v, lxw, tseg);
+                if (D == 3) {
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) v[a] = r1[j * NS + a];
+                    xrow_add<NS>(s2 + 2 * W + row, v, lxw, tseg);
                 }
+            }
         }
         __syncwarp();
         if (staged) {
