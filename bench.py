@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--serve-steps", type=int, default=500)
     ap.add_argument("--saturated", action="store_true", help="serving: all requests arrive at t=0")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sweep", type=int, default=0,
+                    help="C4 precision sweep on the cylinder with this many steps (0: skip)")
+    ap.add_argument("--sweep-n", type=int, default=256, help="cylinder x cells for the sweep")
     return ap.parse_args()
 
 
@@ -209,10 +212,66 @@ def serving(args):
             "speedup_solves_per_s": batched["solves_per_s"] / single["solves_per_s"]}
 
 
+def sweep(args):
+    """C4: the cylinder in FP32 (float atomics), FP32 + int64 fixed point (unit 1
+    and normalised units), and FP64 on the GPU against the FP64 oracle after
+    `--sweep` steps: relative L1 / Linf of rho, |V|, P, e per mode, and whether
+    two runs of a mode agree bit for bit."""
+    from oracle import oracle as O
+    from paper_2404_17057_b300 import inputs as I, mpm as M
+    n = args.sweep_n
+    base = I.cylinder(nx=n, ny=n // 2, precision="fp64")
+    for k in ("x", "v", "mass", "rho", "e"):
+        setattr(base, k, getattr(base, k).astype(np.float32).astype(np.float64))
+    ref = O.OracleSim(base.cfg)
+    ref.add_particles(base.x, base.v, base.mass, base.rho, base.e)
+    ref.set_obstacle_mask(base.mask, base.normals)
+    t0 = time.perf_counter()
+    ref.step(args.sweep)
+    t_or = time.perf_counter() - t0
+    io = np.argsort(ref.read("ID"))
+    R = {f: ref.read(f)[..., io] for f in ("RHO", "P", "E", "V", "X")}
+    um = float(base.mass.mean())
+    umom = um * (3.0 + 1.0)
+    modes = [("fp32", "fp32", None), ("fp32_fixed64_unit1", "fp32_fixed64", [1.0, 1.0, 1.0]),
+             ("fp32_fixed64_normalised", "fp32_fixed64", [um, umom, umom / 1e-4]), ("fp64", "fp64", None)]
+    out = {"workload": f"cylinder {n}x{n // 2}, {base.n_particles} particles, {args.sweep} steps",
+           "oracle_seconds": t_or, "modes": {}}
+    for name, prec, unit in modes:
+        runs = []
+        for _ in range(2):
+            cfg = dict(base.cfg, precision=prec)
+            if unit:
+                cfg["fixed_unit"] = unit
+            p = I.Problem("c4", cfg, base.x, base.v, base.mass, base.rho, base.e, base.mask, base.normals)
+            g = M.Simulation.from_problem(p)
+            g.step(args.sweep)
+            ig = np.argsort(g.read("ID"))
+            runs.append({f: g.read(f)[..., ig] for f in ("RHO", "P", "E", "V", "X")})
+            g.close()
+        a = runs[0]
+        far = np.abs(a["X"] - R["X"]).max(axis=0) > base.cfg["h"]
+        ok = ~far
+        err = {}
+        for f in ("RHO", "P", "E"):
+            d = np.abs(a[f][ok] - R[f][ok])
+            err[f] = {"rel_l1": float(d.sum() / np.abs(R[f][ok]).sum()), "rel_linf": float(d.max() / np.abs(R[f][ok]).max())}
+        vm = np.sqrt((R["V"][:, ok] ** 2).sum(axis=0))
+        dv = np.sqrt(((a["V"][:, ok] - R["V"][:, ok]) ** 2).sum(axis=0))
+        err["V"] = {"rel_l1": float(dv.sum() / vm.sum()), "rel_linf": float(dv.max() / vm.max())}
+        same = all(np.array_equal(runs[0][f], runs[1][f]) for f in runs[0])
+        out["modes"][name] = {"errors": err, "bit_reproducible": bool(same), "excluded_far": int(far.sum())}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        import torch  # noqa: F401  (device memory through the binding)
+        print(json.dumps({"metric": "precision sweep", "sweep": sweep(args)}), flush=True)
+        return
     import torch
     from paper_2404_17057_b300 import build as B, mpm as M
 

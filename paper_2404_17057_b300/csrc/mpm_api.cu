@@ -485,7 +485,9 @@ void launch_sort(mpm_sim* s, cudaStream_t st, const int* active)
         o ^= 1;
     }
     s->vt->gather(s, s->cur, iin, kin, active, st);
-    k_cell_start<<<nblk(n + 1), kThreads, 0, st>>>(s->buf[1 - s->cur].key, n, s->G.nkey, s->cellstart, active);
+    // cell starts from the sorted keys of the last radix pass (the state
+    // gather does not copy keys; the next G2PD step rewrites them)
+    k_cell_start<<<nblk(n + 1), kThreads, 0, st>>>(kin, n, s->G.nkey, s->cellstart, active);
     s->launches += 1;
     s->cur ^= 1;
 }
@@ -945,7 +947,7 @@ mpm_status mpm_read_state(mpm_sim* s, int field, double* out, int64_t count)
         return MPM_OK;
     }
     case MPM_FIELD_ID: return read_u32(s, b.id, np, out);
-    case MPM_FIELD_KEY: return read_u32(s, b.key, np, out);
+    case MPM_FIELD_KEY: return read_u32(s, s->skeys[(s->radix_passes - 1) & 1], np, out);
     case MPM_FIELD_CELLSTART: return read_u32(s, s->cellstart, s->G.nkey + 1, out);
     case MPM_FIELD_CLOCK: {
         Clock c;

@@ -759,7 +759,7 @@ __global__ void k_gather(Particles<R> in, Particles<R> out, const uint32_t* perm
     out.Q[j] = in.Q[s];
     out.id[j] = in.id[s];
     out.gen[j] = in.gen[s];
-    out.key[j] = act ? sorted_keys[j] : in.key[s];
+    (void)sorted_keys;   // the sorted keys stay in the re-order's own buffer
 }
 
 // FP64 sums for the conservation diagnostics: one partial per block,

@@ -153,9 +153,22 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
     for (int i = threadIdx.x; i < kSortWarps * kRadixMax; i += blockDim.x) (&cnt[0][0])[i] = 0;
     __syncthreads();
     const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * kWarpSpan;
-    for (int c = 0; c < kWarpSpan; c += 32) {
-        int64_t j = wbase + c + lane;
-        if (j < n) atomicAdd(&cnt[warp][(keys_in[j] >> shift) & (radix - 1)], 1u);
+    constexpr int R = kWarpSpan / 32;
+    // the warp's keys and indices stay in registers between counting and placing
+    uint32_t kr[R], ir[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+        const int64_t j = wbase + c * 32 + lane;
+        const bool valid = j < n;
+        kr[c] = valid ? keys_in[j] : 0u;
+        ir[c] = valid ? (first_pass ? (uint32_t)j : idx_in[j]) : 0u;
+    }
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+        const bool valid = wbase + c * 32 + lane < n;
+        const uint32_t d = valid ? ((kr[c] >> shift) & (radix - 1)) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[warp][d], (uint32_t)__popc(peers));
     }
     __syncthreads();
     // exclusive prefix over warps, plus the global offset of (digit, block)
@@ -168,22 +181,20 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         }
     }
     __syncthreads();
-    for (int c = 0; c < kWarpSpan; c += 32) {
-        int64_t j = wbase + c + lane;
-        bool valid = j < n;
-        uint32_t k = valid ? keys_in[j] : 0u;
-        uint32_t id = valid ? (first_pass ? (uint32_t)j : idx_in[j]) : 0u;
-        uint32_t d = valid ? ((k >> shift) & (radix - 1)) : 0xffffffffu;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-        int leader = __ffs(peers) - 1;
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+        const bool valid = wbase + c * 32 + lane < n;
+        const uint32_t d = valid ? ((kr[c] >> shift) & (radix - 1)) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        const int leader = __ffs(peers) - 1;
         uint32_t basev = 0;
         if (valid && lane == leader) basev = cnt[warp][d];
         basev = __shfl_sync(0xffffffffu, basev, leader);
         if (valid) {
-            uint32_t pos = basev + rank;
-            keys_out[pos] = k;
-            idx_out[pos] = id;
+            const uint32_t pos = basev + rank;
+            keys_out[pos] = kr[c];
+            idx_out[pos] = ir[c];
         }
         __syncwarp();
         if (valid && lane == leader) cnt[warp][d] = basev + __popc(peers);
