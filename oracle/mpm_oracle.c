@@ -223,6 +223,7 @@ struct oracle_sim {
     double *x[3], *v[3], *vbar[3], *M, *rho, *E, *Q;
     int64_t* id;
     uint32_t* gen;       /* times each particle has been recycled */
+    uint8_t* recyc;      /* re-created at the inflow in the current step */
     uint32_t* key;
     int64_t* cellstart;
     double *gm, *gmv[3], *gf[3], *gmv2[3];     /* raw P2G sums of the last step */
@@ -241,7 +242,8 @@ static void free_particles(oracle_sim* s)
     for (int a = 0; a < 3; ++a) { free(s->x[a]); free(s->v[a]); free(s->vbar[a]); free(s->tmp_p[a]);
                                   s->x[a] = s->v[a] = s->vbar[a] = s->tmp_p[a] = NULL; }
     free(s->M); free(s->rho); free(s->E); free(s->Q); free(s->id); free(s->key); free(s->coef); free(s->gen);
-    s->M = s->rho = s->E = s->Q = s->coef = NULL; s->id = NULL; s->key = NULL; s->gen = NULL;
+    free(s->recyc);
+    s->M = s->rho = s->E = s->Q = s->coef = NULL; s->id = NULL; s->key = NULL; s->gen = NULL; s->recyc = NULL;
 }
 
 void oracle_destroy(oracle_sim* s)
@@ -306,7 +308,8 @@ int oracle_add_particles(oracle_sim* s, int64_t n, const double* x, const double
     int64_t* nid = realloc(s->id, np * sizeof(int64_t) + 8); if (nid) s->id = nid;
     uint32_t* nk = realloc(s->key, np * sizeof(uint32_t) + 8); if (nk) s->key = nk;
     uint32_t* ng = realloc(s->gen, np * sizeof(uint32_t) + 8); if (ng) s->gen = ng;
-    int ok = nM && nR && nE && nQ && nc && nid && nk && ng;
+    uint8_t* nrc = realloc(s->recyc, np + 8); if (nrc) s->recyc = nrc;
+    int ok = nM && nR && nE && nQ && nc && nid && nk && ng && nrc;
     for (int a = 0; a < 3; ++a) {
         nx[a] = realloc(s->x[a], np * sizeof(double) + 8); if (nx[a]) s->x[a] = nx[a];
         nv[a] = realloc(s->v[a], np * sizeof(double) + 8); if (nv[a]) s->v[a] = nv[a];
@@ -323,6 +326,7 @@ int oracle_add_particles(oracle_sim* s, int64_t n, const double* x, const double
             s->vbar[a][j] = s->v[a][j];
         }
         s->M[j] = mass[k]; s->rho[j] = rho[k]; s->E[j] = e[k]; s->Q[j] = 0.0; s->id[j] = j; s->gen[j] = 0;
+        s->recyc[j] = 0;
     }
     s->np = np;
     return sort_particles(s);
@@ -500,15 +504,42 @@ static void permute_d(double* a, const int64_t* perm, int64_t n, double* tmp)
     memcpy(a, tmp, (size_t)n * sizeof(double));
 }
 
+/* Recycled particles of one key, ordered by id (qsort comparator). */
+static const uint32_t* g_rk;
+static const int64_t* g_rid;
+static int cmp_recycled(const void* a, const void* b)
+{
+    int64_t i = *(const int64_t*)a, j = *(const int64_t*)b;
+    if (g_rk[i] != g_rk[j]) return g_rk[i] < g_rk[j] ? -1 : 1;
+    return g_rid[i] < g_rid[j] ? -1 : (g_rid[i] > g_rid[j] ? 1 : 0);
+}
+
+/* Sec. 3 step xii: rebuild each cell's list from the particles now in it, in
+ * their current order; particles re-created at the inflow during this step
+ * (Sec. 4.1) are new in their cell and are appended after the others, by id. */
 static int sort_particles(oracle_sim* s)
 {
     keys_of_particles(s);
     int64_t n = s->np;
     int64_t* perm = (int64_t*)malloc((size_t)n * sizeof(int64_t) + 8);
     double* tmp = (double*)malloc((size_t)n * sizeof(double) + 8);
-    if (!perm || !tmp) { free(perm); free(tmp); return OR_ENOMEM; }
-    int st = oracle_stable_sort(n, s->key, s->G.nkey, perm, s->cellstart);
-    if (st) { free(perm); free(tmp); return st; }
+    int64_t* cur = (int64_t*)malloc((size_t)s->G.nkey * sizeof(int64_t) + 8);
+    int64_t* rl = (int64_t*)malloc((size_t)n * sizeof(int64_t) + 8);
+    if (!perm || !tmp || !cur || !rl) { free(perm); free(tmp); free(cur); free(rl); return OR_ENOMEM; }
+    int64_t* start = s->cellstart;
+    for (int64_t i = 0; i <= s->G.nkey; ++i) start[i] = 0;
+    for (int64_t k = 0; k < n; ++k) start[s->key[k] + 1]++;
+    for (int64_t i = 0; i < s->G.nkey; ++i) start[i + 1] += start[i];
+    memcpy(cur, start, (size_t)s->G.nkey * sizeof(int64_t));
+    int64_t nr = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        if (s->recyc[k]) rl[nr++] = k;
+        else perm[cur[s->key[k]]++] = k;
+    }
+    g_rk = s->key; g_rid = s->id;
+    qsort(rl, (size_t)nr, sizeof(int64_t), cmp_recycled);
+    for (int64_t i = 0; i < nr; ++i) perm[cur[s->key[rl[i]]]++] = rl[i];
+    free(cur); free(rl);
     for (int a = 0; a < 3; ++a) { permute_d(s->x[a], perm, n, tmp); permute_d(s->v[a], perm, n, tmp);
                                   permute_d(s->vbar[a], perm, n, tmp); }
     permute_d(s->M, perm, n, tmp); permute_d(s->rho, perm, n, tmp);
@@ -521,6 +552,7 @@ static int sort_particles(oracle_sim* s)
     memcpy(s->key, tk, (size_t)n * sizeof(uint32_t));
     for (int64_t j = 0; j < n; ++j) tk[j] = s->gen[perm[j]];
     memcpy(s->gen, tk, (size_t)n * sizeof(uint32_t));
+    memset(s->recyc, 0, (size_t)n);
     free(perm); free(tmp);
     return OR_OK;
 }
@@ -633,6 +665,7 @@ static int one_step(oracle_sim* s, double dt)
         for (int a = 0; a < d; ++a) s->x[a][k] = xn[a];
         if (out && inflow >= 0) {
             recycle(s, k, inflow);
+            s->recyc[k] = 1;
             double vi = norm_d(s->v, d, k);
             if (vi > s->vmax_step) s->vmax_step = vi;
             continue;

@@ -8,6 +8,7 @@
 #include "mpm_kernels.cuh"
 #include "mpm_fast.cuh"
 #include "mpm_sort.cuh"
+#include "mpm_reorder.cuh"
 
 #include <cuda_runtime.h>
 
@@ -62,14 +63,14 @@ struct mpm_sim {
     uint8_t* mask = nullptr;
     void* nrm = nullptr;           // d x nodes of type R
     Clock* clk = nullptr;
-    uint32_t* cellstart = nullptr;
-    uint32_t* skeys[2] = {nullptr, nullptr};
-    uint32_t* sidx[2] = {nullptr, nullptr};
-    uint32_t* hist = nullptr;
-    uint32_t* scan_part = nullptr;
+    uint32_t* cs[2] = {nullptr, nullptr};   // cell starts of particle buffer b
+    uint32_t* count = nullptr;              // particles per new span (step re-order)
+    uint32_t* cscan_part = nullptr;         // scan partials over the spans
+    uint32_t* perm = nullptr;               // old index of each re-ordered particle
+    uint2* far = nullptr;                   // recycled particles of a step
+    uint32_t far_cap = 0;
     double* cons_part = nullptr;
     double* cons_out = nullptr;
-    int radix_passes = 0, radix_bits = 0;
     bool started = false, poisoned = false, stepped = false, cfl_done = false;
     std::vector<void*> allocs;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -155,6 +156,7 @@ struct Vtbl {
     void (*from_double)(const double* in, void* out, int64_t n, cudaStream_t st);
     cudaError_t (*set_smem)(const Geom& G);
     size_t (*smem)(const Geom& G, int kernel);
+    void (*reorder)(mpm_sim* s, cudaStream_t st);
 };
 
 namespace {
@@ -214,7 +216,9 @@ struct Impl {
     }
     static cudaError_t set_smem(const Geom& G)
     {
-        cudaError_t e;
+        cudaError_t e = cudaFuncSetAttribute(k_reorder<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)reorder_smem(G));
+        if (e != cudaSuccess) return e;
         if constexpr (kFast) {
             for (int per = 0; per < 2; ++per) {
                 e = cudaFuncSetAttribute(per ? (const void*)k_p2g_span<D, P, true> : (const void*)k_p2g_span<D, P, false>,
@@ -243,6 +247,8 @@ struct Impl {
         const Geom& G = s->G;
         Particles<R> pt = parts<R>(s->buf[s->cur]);
         Grid<A, R> gr = grid_view<A, R>(s);
+        const uint32_t* cs = s->cs[s->cur];
+        const Reorder ro = {s->count, s->far, s->far_cap};
         if (which & 1) {
             k_zero<<<std::min<int64_t>(nblk(s->grid_bytes / 16), 148 * 8), kThreads, 0, st>>>(
                 (uint4*)s->grid, (int64_t)(s->grid_bytes / 16), &s->clk->active);
@@ -254,11 +260,11 @@ struct Impl {
                     o.p[1 + D + a] = (float*)gr.f[a];
                 }
                 if (G.per[0] | G.per[1] | G.per[2])
-                    k_p2g_span<D, P, true><<<G.ntiles, kP2GThreads, smem(G, 0), st>>>(G, pt, o, s->cellstart, s->clk);
+                    k_p2g_span<D, P, true><<<G.ntiles, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk);
                 else
-                    k_p2g_span<D, P, false><<<G.ntiles, kP2GThreads, smem(G, 0), st>>>(G, pt, o, s->cellstart, s->clk);
+                    k_p2g_span<D, P, false><<<G.ntiles, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk);
             } else {
-                k_p2g<D, P, R, A><<<G.ntiles, kThreads, smem(G, 0), st>>>(G, pt, gr, s->cellstart, s->clk);
+                k_p2g<D, P, R, A><<<G.ntiles, kThreads, smem(G, 0), st>>>(G, pt, gr, cs, s->clk);
             }
             s->launches += 2;
         }
@@ -267,23 +273,29 @@ struct Impl {
                 FieldPtrs o = {};
                 for (int a = 0; a < D; ++a) o.p[a] = (float*)gr.mv2[a];
                 if (G.per[0] | G.per[1] | G.per[2])
-                    k_grid_g2p_span<D, P, true><<<G.ntiles, kSpanThreads, smem(G, 1), st>>>(G, pt, gr, o, s->cellstart,
-                                                                                             s->clk);
+                    k_grid_g2p_span<D, P, true><<<G.ntiles, kSpanThreads, smem(G, 1), st>>>(G, pt, gr, o, cs, s->clk);
                 else
-                    k_grid_g2p_span<D, P, false><<<G.ntiles, kSpanThreads, smem(G, 1), st>>>(G, pt, gr, o, s->cellstart,
-                                                                                              s->clk);
+                    k_grid_g2p_span<D, P, false><<<G.ntiles, kSpanThreads, smem(G, 1), st>>>(G, pt, gr, o, cs, s->clk);
             } else {
-                k_grid_g2p<D, P, R, A><<<G.ntiles, kThreads, smem(G, 1), st>>>(G, pt, gr, s->cellstart, s->clk);
+                k_grid_g2p<D, P, R, A><<<G.ntiles, kThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
             }
             s->launches += 1;
         }
         if (which & 4) {
             if constexpr (kFast)
-                k_g2pd_fast<D, P><<<G.ntiles, 256, smem(G, 2), st>>>(G, pt, gr, s->cellstart, s->clk);
+                k_g2pd_fast<D, P><<<G.ntiles, 256, smem(G, 2), st>>>(G, pt, gr, cs, s->clk, ro);
             else
-                k_g2pd<D, P, R, A><<<G.ntiles, kThreads, smem(G, 2), st>>>(G, pt, gr, s->cellstart, s->clk);
+                k_g2pd<D, P, R, A><<<G.ntiles, kThreads, smem(G, 2), st>>>(G, pt, gr, cs, s->clk, ro);
             s->launches += 1;
         }
+    }
+    static void reorder(mpm_sim* s, cudaStream_t st)
+    {
+        const int b = s->cur;
+        k_reorder<D, R><<<s->G.ntiles, kReorderThreads, reorder_smem(s->G), st>>>(
+            s->G, parts<R>(s->buf[b]), parts<R>(s->buf[1 - b]), s->cs[b], s->cs[1 - b], s->count, s->perm, s->np,
+            s->clk);
+        s->launches += 1;
     }
     static void keys(mpm_sim* s, int b, cudaStream_t st)
     {
@@ -324,7 +336,7 @@ const Vtbl* vtbl_of()
 {
     typedef Impl<D, P, R, A> I;
     static const Vtbl v = {I::step_kernels, I::keys, I::gather, I::cfl_init, I::cons, I::from_double, I::set_smem,
-                           I::smem};
+                           I::smem, I::reorder};
     return &v;
 }
 
@@ -391,7 +403,7 @@ mpm_status make_geom(const mpm_config* c, Geom* G, std::string* why)
         nnode *= G->N[a];
     }
     nkey = (int64_t)ntiles * tvol;
-    if (nkey >= (int64_t)0xFFFFFFF0LL) { *why = "too many spans for 32-bit keys"; return MPM_EINVAL; }
+    if (nkey >= (int64_t)0x7FFFFFFFLL) { *why = "too many spans for 31-bit keys"; return MPM_EINVAL; }
     if (tvol < 32) { *why = "a tile must hold at least 32 spans"; return MPM_EINVAL; }
     G->Tvol = tvol;
     G->Wvol = wvol;
@@ -462,9 +474,19 @@ void drop_graphs(mpm_sim* s)
         if (s->graph[b]) { cudaGraphExecDestroy(s->graph[b]); s->graph[b] = nullptr; }
 }
 
-// Re-order: LSD radix passes over (key, index), then gather into the other
-// buffer and rebuild the cell-start table.  Swaps s->cur.
-void launch_sort(mpm_sim* s, cudaStream_t st, const int* active)
+// Scratch of the LSD radix sort used for the arbitrary initial order.
+struct RadixScratch {
+    uint32_t* skeys[2] = {nullptr, nullptr};
+    uint32_t* sidx[2] = {nullptr, nullptr};
+    uint32_t* hist = nullptr;
+    uint32_t* part = nullptr;
+    int passes = 0, bits = 0;
+};
+
+// Initial re-order of particles in any order: LSD radix passes over
+// (key, index), gather into the other buffer, cell starts of that buffer.
+// Swaps s->cur.
+void launch_sort(mpm_sim* s, const RadixScratch& rs, cudaStream_t st)
 {
     const int64_t n = s->np;
     if (n == 0) return;
@@ -472,23 +494,38 @@ void launch_sort(mpm_sim* s, cudaStream_t st, const int* active)
     const uint32_t* kin = s->buf[s->cur].key;
     const uint32_t* iin = nullptr;
     int o = 0;
-    for (int pass = 0; pass < s->radix_passes; ++pass) {
-        const int shift = pass * s->radix_bits;
-        const int bits = s->radix_bits;
-        k_radix_hist<<<nb, kSortThreads, 0, st>>>(kin, n, shift, bits, s->hist, active);
-        scan_exclusive(s->hist, s->hist, (int64_t)(1 << bits) * nb, s->scan_part, 0, st, &s->launches);
-        k_radix_scatter<<<nb, kSortThreads, 0, st>>>(kin, iin, s->skeys[o], s->sidx[o], n, shift, bits, s->hist,
-                                                      active, pass == 0);
+    for (int pass = 0; pass < rs.passes; ++pass) {
+        const int shift = pass * rs.bits;
+        k_radix_hist<<<nb, kSortThreads, 0, st>>>(kin, n, shift, rs.bits, rs.hist, nullptr);
+        scan_exclusive(rs.hist, rs.hist, (int64_t)(1 << rs.bits) * nb, rs.part, 0, st, &s->launches);
+        k_radix_scatter<<<nb, kSortThreads, 0, st>>>(kin, iin, rs.skeys[o], rs.sidx[o], n, shift, rs.bits, rs.hist,
+                                                      nullptr, pass == 0);
         s->launches += 2;
-        kin = s->skeys[o];
-        iin = s->sidx[o];
+        kin = rs.skeys[o];
+        iin = rs.sidx[o];
         o ^= 1;
     }
-    s->vt->gather(s, s->cur, iin, kin, active, st);
-    // cell starts from the sorted keys of the last radix pass (the state
-    // gather does not copy keys; the next G2PD step rewrites them)
-    k_cell_start<<<nblk(n + 1), kThreads, 0, st>>>(kin, n, s->G.nkey, s->cellstart, active);
+    s->vt->gather(s, s->cur, iin, nullptr, nullptr, st);
+    k_cell_start<<<nblk(n + 1), kThreads, 0, st>>>(kin, n, s->G.nkey, s->cs[1 - s->cur], nullptr);
     s->launches += 1;
+    s->cur ^= 1;
+}
+
+// Per-step re-order (Sec. 3 step xii): the G2PD step has written each
+// particle's new key and counted the particles of every new span; scan the
+// counts into the other buffer's cell starts, give recycled particles their
+// slots, then move every tile's particles into the other buffer.  Swaps
+// s->cur.
+void launch_reorder(mpm_sim* s, cudaStream_t st)
+{
+    if (s->np == 0) return;
+    uint32_t* cs_new = s->cs[1 - s->cur];
+    scan_exclusive(s->count, cs_new, s->G.nkey, s->cscan_part, 1, st, &s->launches);
+    if (s->far_cap) {
+        k_far_place<<<148 * 2, 256, 0, st>>>(s->far, s->far_cap, s->count, cs_new, s->perm, s->clk);
+        s->launches += 1;
+    }
+    s->vt->reorder(s, st);
     s->cur ^= 1;
 }
 
@@ -507,7 +544,7 @@ void launch_step(mpm_sim* s, cudaStream_t st, ProfStep* ps)
     k_finalize<<<1, 1, 0, st>>>(s->clk, s->G.cfl * s->G.h);
     s->launches += 1;
     if (ps) cudaEventRecord(ps->ev[4], st);
-    launch_sort(s, st, &s->clk->active);
+    launch_reorder(s, st);
     if (ps) cudaEventRecord(ps->ev[5], st);
 }
 
@@ -518,9 +555,9 @@ mpm_status check_device_errors(mpm_sim* s)
     CK(cudaStreamSynchronize(s->stream), "synchronize");
     if (c.err) {
         s->poisoned = true;
-        if (c.err & ERR_TILE) return fail(s, MPM_ESTATE, "internal: particle outside its tile (order lost)");
         if (c.err & ERR_CFL) return fail(s, MPM_ECFL, "a particle crossed more than one span in one step");
-        return fail(s, MPM_ENONFINITE, "non-finite state or 1 + dt div(v) <= 0");
+        if (c.err & ERR_NONFINITE) return fail(s, MPM_ENONFINITE, "non-finite state or 1 + dt div(v) <= 0");
+        return fail(s, MPM_ESTATE, "internal: particle outside its tile (order lost)");
     }
     return MPM_OK;
 }
@@ -598,6 +635,10 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
             mpm_destroy(s);
             return fail(nullptr, MPM_EINVAL, "tile too large for shared memory");
         }
+    if ((int)reorder_smem(s->G) > smem_optin || reorder_ranges(s->G) > kReorderMaxRanges) {
+        mpm_destroy(s);
+        return fail(nullptr, MPM_EINVAL, "tile too large for the re-order");
+    }
     cudaError_t e = s->vt->set_smem(s->G);
     if (e != cudaSuccess) {
         mpm_destroy(s);
@@ -607,25 +648,28 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
     s->grid_bytes = align16((size_t)(1 + 3 * d) * (size_t)s->G.nnode_p * s->asize);
     s->grid = dalloc(s, s->grid_bytes);
     s->clk = (Clock*)dalloc(s, sizeof(Clock));
-    s->cellstart = (uint32_t*)dalloc(s, (size_t)(s->G.nkey + 1) * 4);
+    const size_t csb = (size_t)(s->G.nkey + 1) * 4;
+    s->cs[0] = (uint32_t*)dalloc(s, csb);
+    s->cs[1] = (uint32_t*)dalloc(s, csb);
+    s->count = (uint32_t*)dalloc(s, csb);
+    s->cscan_part = (uint32_t*)dalloc(s, (size_t)scan_blocks(s->G.nkey) * 4);
     s->cons_part = (double*)dalloc(s, 1024 * 5 * sizeof(double));
     s->cons_out = (double*)dalloc(s, 8 * sizeof(double));
-    if (!s->grid || !s->clk || !s->cellstart || !s->cons_part || !s->cons_out) {
+    if (!s->grid || !s->clk || !s->cs[0] || !s->cs[1] || !s->count || !s->cscan_part || !s->cons_part ||
+        !s->cons_out) {
         mpm_destroy(s);
         return fail(nullptr, MPM_ENOMEM, "device allocation failed");
     }
     if (cudaMemsetAsync(s->grid, 0, s->grid_bytes, s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->clk, 0, sizeof(Clock), s->stream) != cudaSuccess ||
-        cudaMemsetAsync(s->cellstart, 0, (size_t)(s->G.nkey + 1) * 4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->cs[0], 0, csb, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->cs[1], 0, csb, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->count, 0, csb, s->stream) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess) {
         cudaGetLastError();
         mpm_destroy(s);
         return fail(nullptr, MPM_ECUDA, "device initialisation failed");
     }
-    int bits = 1;
-    while (((int64_t)1 << bits) < s->G.nkey) ++bits;
-    s->radix_passes = (bits + kRadixBitsMax - 1) / kRadixBitsMax;
-    s->radix_bits = (bits + s->radix_passes - 1) / s->radix_passes;
     *out = s;
     return MPM_OK;
 }
@@ -699,27 +743,49 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
     s->buf[1] = nb[1];
     s->cur = 0;
     s->np = np;
-    for (int b = 0; b < 2; ++b) {
-        dfree(s, s->skeys[b]);
-        dfree(s, s->sidx[b]);
-        s->skeys[b] = (uint32_t*)dalloc(s, (size_t)np * 4);
-        s->sidx[b] = (uint32_t*)dalloc(s, (size_t)np * 4);
+    dfree(s, s->perm);
+    dfree(s, s->far);
+    s->perm = nullptr;
+    s->far = nullptr;
+    s->far_cap = G.inflow_face >= 0 ? (uint32_t)np : 0u;
+    if (s->far_cap) {
+        s->perm = (uint32_t*)dalloc(s, (size_t)np * 4);
+        s->far = (uint2*)dalloc(s, (size_t)np * sizeof(uint2));
+        if (!s->perm || !s->far) return fail(s, MPM_ENOMEM, "device allocation failed");
     }
-    dfree(s, s->hist);
-    dfree(s, s->scan_part);
+    // radix scratch for the initial order only
+    RadixScratch sc;
+    int bits = 1;
+    while (((int64_t)1 << bits) < G.nkey) ++bits;
+    sc.passes = (bits + kRadixBitsMax - 1) / kRadixBitsMax;
+    sc.bits = (bits + sc.passes - 1) / sc.passes;
     const int64_t nblocks = (np + kSortTile - 1) / kSortTile;
-    const int64_t nhist = nblocks * ((int64_t)1 << s->radix_bits);
-    s->hist = (uint32_t*)dalloc(s, (size_t)nhist * 4);
-    s->scan_part = (uint32_t*)dalloc(s, (size_t)std::max<int64_t>(scan_blocks(nhist), 1) * 4);
-    if (!s->skeys[0] || !s->skeys[1] || !s->sidx[0] || !s->sidx[1] || !s->hist || !s->scan_part)
+    const int64_t nhist = nblocks * ((int64_t)1 << sc.bits);
+    for (int b = 0; b < 2; ++b) {
+        sc.skeys[b] = (uint32_t*)dalloc(s, (size_t)np * 4);
+        sc.sidx[b] = (uint32_t*)dalloc(s, (size_t)np * 4);
+    }
+    sc.hist = (uint32_t*)dalloc(s, (size_t)nhist * 4);
+    sc.part = (uint32_t*)dalloc(s, (size_t)std::max<int64_t>(scan_blocks(nhist), 1) * 4);
+    auto free_sc = [&]() {
+        for (int b = 0; b < 2; ++b) { dfree(s, sc.skeys[b]); dfree(s, sc.sidx[b]); }
+        dfree(s, sc.hist);
+        dfree(s, sc.part);
+    };
+    if (!sc.skeys[0] || !sc.skeys[1] || !sc.sidx[0] || !sc.sidx[1] || !sc.hist || !sc.part) {
+        free_sc();
         return fail(s, MPM_ENOMEM, "device allocation failed");
+    }
     drop_graphs(s);
     s->cfl_done = false;
     // initial order: keys from the positions, then the stable re-order
     s->vt->keys(s, s->cur, S);
-    launch_sort(s, S, nullptr);
-    CK(cudaGetLastError(), "launch");
-    CK(cudaStreamSynchronize(S), "synchronize");
+    launch_sort(s, sc, S);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t se = cudaStreamSynchronize(S);
+    free_sc();
+    CK(le, "launch");
+    CK(se, "synchronize");
     return MPM_OK;
 }
 
@@ -819,9 +885,9 @@ static mpm_status capture_graph(mpm_sim* s, int b)
 
 static int64_t step_launch_count(const mpm_sim* s)
 {
-    // prepare, zero, 3 step kernels, finalize, per radix pass (hist, 3 scan,
-    // scatter), gather, cell start
-    return 6 + 5 * (int64_t)s->radix_passes + 2;
+    // prepare, zero, 3 step kernels, finalize; re-order: 3 scan kernels,
+    // recycled placement (inflow only), tile moves
+    return 6 + 4 + (s->far_cap ? 1 : 0);
 }
 
 mpm_status mpm_step_async(mpm_sim* s, int64_t nsteps, double dt, double t_end)
@@ -947,8 +1013,18 @@ mpm_status mpm_read_state(mpm_sim* s, int field, double* out, int64_t count)
         return MPM_OK;
     }
     case MPM_FIELD_ID: return read_u32(s, b.id, np, out);
-    case MPM_FIELD_KEY: return read_u32(s, s->skeys[(s->radix_passes - 1) & 1], np, out);
-    case MPM_FIELD_CELLSTART: return read_u32(s, s->cellstart, s->G.nkey + 1, out);
+    case MPM_FIELD_KEY: {
+        // keys of the current order, expanded from its cell starts
+        if (np == 0) return MPM_OK;
+        uint32_t* tk = (uint32_t*)dalloc(s, (size_t)np * 4);
+        if (!tk) return fail(s, MPM_ENOMEM, "device allocation failed");
+        k_keys_from_start<<<std::min<int64_t>(nblk(s->G.nkey), 148 * 16), kThreads, 0, s->stream>>>(
+            s->cs[s->cur], s->G.nkey, tk);
+        st = read_u32(s, tk, np, out);
+        dfree(s, tk);
+        return st;
+    }
+    case MPM_FIELD_CELLSTART: return read_u32(s, s->cs[s->cur], s->G.nkey + 1, out);
     case MPM_FIELD_CLOCK: {
         Clock c;
         CK(cudaMemcpyAsync(&c, s->clk, sizeof(Clock), cudaMemcpyDeviceToHost, s->stream), "read clock");
@@ -1069,7 +1145,7 @@ mpm_status mpm_profile_read(mpm_sim* s, double out[8], int64_t counts[8], int re
         counts[1] = 1;
         counts[2] = 1;
         counts[3] = 1;   // finalize (prepare counted with the step)
-        counts[4] = 5 * (int64_t)s->radix_passes + 2;
+        counts[4] = 4 + (s->far_cap ? 1 : 0);
         counts[6] = s->launches;
     }
     if (reset) {

@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(kSpanThreads, 3) k_grid_g2p_span(Geom G, Parti
 
 template <int D, int P>
 __global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, Grid<float, float> gr,
-                                                   const uint32_t* __restrict__ cs, Clock* clk)
+                                                   const uint32_t* __restrict__ cs, Clock* clk, Reorder ro)
 {
     if (!clk->active) return;
     const int tile = blockIdx.x;
@@ -797,7 +797,7 @@ __global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, 
         }
 #pragma unroll
         for (int a = 0; a < D; ++a) pt.x[a][k] = xn[a];
-        pt.key[k] = key_of<float>(G, sp);
+        pt.key[k] = record_key(ro, clk, key_of<float>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, err);
         pt.E[k] = En_s;
         pt.rho[k] = rn_s;
         pt.Q[k] = Qn_s;

@@ -19,6 +19,15 @@ namespace mpm {
 
 enum : int { ERR_NONFINITE = 1, ERR_CFL = 2, ERR_TILE = 4 };
 
+constexpr uint32_t kFarFlag = 0x80000000u;   // key bit of a particle recycled this step
+
+// Per-step re-order bookkeeping written by the G2PD step.
+struct Reorder {
+    uint32_t* count;   // particles per new span; zeroed again by the pull
+    uint2* far;        // particles recycled this step: {new key, old index}
+    uint32_t far_cap;  // entries of far (0: the problem has no inflow face)
+};
+
 struct Geom {
     int dim, p;
     int n[3], per[3], S[3], N[3], g[3], T[3], nt[3], W[3];
@@ -40,7 +49,26 @@ struct Clock {
     long long step;
     int active, done, last, err;
     unsigned long long vmax_bits, cmax_bits;   // bits of non-negative doubles
+    unsigned nfar;                             // recycled particles this step
+    unsigned pad;
 };
+
+// New key of particle k: count it for its span; recycled particles go to the
+// far list (they may jump anywhere) and carry the flag bit.
+__device__ __forceinline__ uint32_t record_key(const Reorder& ro, Clock* clk, uint32_t key, bool recycled,
+                                               uint32_t k, int& err)
+{
+    const unsigned m = __activemask();
+    const unsigned peers = __match_any_sync(m, key);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&ro.count[key], (uint32_t)__popc(peers));
+    if (recycled) {
+        const unsigned slot = atomicAdd(&clk->nfar, 1u);
+        if (slot < ro.far_cap) ro.far[slot] = make_uint2(key, k);
+        else err |= ERR_TILE;
+        return key | kFarFlag;
+    }
+    return key;
+}
 
 template <class R>
 struct Particles {
@@ -473,7 +501,7 @@ __global__ void __launch_bounds__(256) k_grid_g2p(Geom G, Particles<R> pt, Grid<
 
 template <int D, int P, class R, class A>
 __global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R> gr, const uint32_t* cellstart,
-                                              Clock* clk)
+                                              Clock* clk, Reorder ro)
 {
     typedef Op<R> O;
     if (!clk->active) return;
@@ -632,7 +660,7 @@ __global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R
             sp[a] = wrap_span(G, a, span_of<R, P>(G, a, xn[a], xi));
             pt.x[a][k] = xn[a];
         }
-        pt.key[k] = key_of<R>(G, sp);
+        pt.key[k] = record_key(ro, clk, key_of<R>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, err);
         pt.E[k] = En_s;
         pt.rho[k] = rn_s;
         pt.Q[k] = Qn_s;
@@ -656,6 +684,7 @@ __global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R
 __global__ void k_prepare(Clock* clk)
 {
     Clock& c = *clk;
+    c.nfar = 0u;
     if (c.done || c.err) { c.active = 0; return; }
     double h = c.dt_fixed > 0.0 ? c.dt_fixed : c.dt_next;
     if (!(h > 0.0)) { c.err |= ERR_NONFINITE; c.active = 0; return; }
@@ -747,7 +776,10 @@ __global__ void k_gather(Particles<R> in, Particles<R> out, const uint32_t* perm
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const bool act = active == nullptr || *active;
-    const uint32_t s = act ? perm[j] : (uint32_t)j;
+    uint32_t s = act ? perm[j] : (uint32_t)j;
+    // a step that failed (reported through the clock's error bits) may leave
+    // parts of perm unwritten: never follow an index out of the buffer
+    if ((int64_t)s >= n) s = (uint32_t)j;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         out.x[a][j] = in.x[a][s];
@@ -815,3 +847,4 @@ __global__ void k_iota(uint32_t* out, int64_t n, uint32_t base)
 }
 
 }  // namespace mpm
+
