@@ -69,6 +69,8 @@ struct mpm_sim {
     uint32_t* perm = nullptr;               // old index of each re-ordered particle
     uint2* far = nullptr;                   // recycled particles of a step
     uint32_t far_cap = 0;
+    unsigned long long* ring = nullptr;     // per tile: ring parts entered in a step
+    int mwords = 0;
     double* cons_part = nullptr;
     double* cons_out = nullptr;
     bool started = false, poisoned = false, stepped = false, cfl_done = false;
@@ -248,7 +250,7 @@ struct Impl {
         Particles<R> pt = parts<R>(s->buf[s->cur]);
         Grid<A, R> gr = grid_view<A, R>(s);
         const uint32_t* cs = s->cs[s->cur];
-        const Reorder ro = {s->count, s->far, s->far_cap};
+        const Reorder ro = {s->count, s->far, s->far_cap, s->mwords, s->ring};
         if (which & 1) {
             k_zero<<<std::min<int64_t>(nblk(s->grid_bytes / 16), 148 * 8), kThreads, 0, st>>>(
                 (uint4*)s->grid, (int64_t)(s->grid_bytes / 16), &s->clk->active);
@@ -294,7 +296,7 @@ struct Impl {
         const int b = s->cur;
         k_reorder<D, R><<<s->G.ntiles, kReorderThreads, reorder_smem(s->G), st>>>(
             s->G, parts<R>(s->buf[b]), parts<R>(s->buf[1 - b]), s->cs[b], s->cs[1 - b], s->count, s->perm, s->np,
-            s->clk);
+            s->ring, s->mwords, s->clk);
         s->launches += 1;
     }
     static void keys(mpm_sim* s, int b, cudaStream_t st)
@@ -557,6 +559,7 @@ mpm_status check_device_errors(mpm_sim* s)
         s->poisoned = true;
         if (c.err & ERR_CFL) return fail(s, MPM_ECFL, "a particle crossed more than one span in one step");
         if (c.err & ERR_NONFINITE) return fail(s, MPM_ENONFINITE, "non-finite state or 1 + dt div(v) <= 0");
+        if (c.err & ERR_TIMEOUT) return fail(s, MPM_ETIMEOUT, "a bounded device wait expired");
         return fail(s, MPM_ESTATE, "internal: particle outside its tile (order lost)");
     }
     return MPM_OK;
@@ -635,7 +638,7 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
             mpm_destroy(s);
             return fail(nullptr, MPM_EINVAL, "tile too large for shared memory");
         }
-    if ((int)reorder_smem(s->G) > smem_optin || reorder_ranges(s->G) > kReorderMaxRanges) {
+    if ((int)reorder_smem(s->G) + 128 > smem_optin || reorder_ranges(s->G) > kReorderMaxRanges) {
         mpm_destroy(s);
         return fail(nullptr, MPM_EINVAL, "tile too large for the re-order");
     }
@@ -653,10 +656,13 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
     s->cs[1] = (uint32_t*)dalloc(s, csb);
     s->count = (uint32_t*)dalloc(s, csb);
     s->cscan_part = (uint32_t*)dalloc(s, (size_t)scan_blocks(s->G.nkey) * 4);
+    s->mwords = (reorder_ranges(s->G) + 63) / 64;
+    const size_t ringb = (size_t)s->G.ntiles * s->mwords * 8;
+    s->ring = (unsigned long long*)dalloc(s, ringb);
     s->cons_part = (double*)dalloc(s, 1024 * 5 * sizeof(double));
     s->cons_out = (double*)dalloc(s, 8 * sizeof(double));
-    if (!s->grid || !s->clk || !s->cs[0] || !s->cs[1] || !s->count || !s->cscan_part || !s->cons_part ||
-        !s->cons_out) {
+    if (!s->grid || !s->clk || !s->cs[0] || !s->cs[1] || !s->count || !s->cscan_part || !s->ring ||
+        !s->cons_part || !s->cons_out) {
         mpm_destroy(s);
         return fail(nullptr, MPM_ENOMEM, "device allocation failed");
     }
@@ -665,6 +671,7 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
         cudaMemsetAsync(s->cs[0], 0, csb, s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->cs[1], 0, csb, s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->count, 0, csb, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->ring, 0, ringb, s->stream) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess) {
         cudaGetLastError();
         mpm_destroy(s);

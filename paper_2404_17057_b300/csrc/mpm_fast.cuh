@@ -797,7 +797,11 @@ __global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, 
         }
 #pragma unroll
         for (int a = 0; a < D; ++a) pt.x[a][k] = xn[a];
-        pt.key[k] = record_key(ro, clk, key_of<float>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, err);
+        int old[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) old[a] = so[a] + l[a];
+        pt.key[k] = record_key(G, ro, clk, key_of<float>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, tile, old,
+                               err);
         pt.E[k] = En_s;
         pt.rho[k] = rn_s;
         pt.Q[k] = Qn_s;

@@ -17,15 +17,17 @@
 
 namespace mpm {
 
-enum : int { ERR_NONFINITE = 1, ERR_CFL = 2, ERR_TILE = 4 };
+enum : int { ERR_NONFINITE = 1, ERR_CFL = 2, ERR_TILE = 4, ERR_TIMEOUT = 8 };
 
 constexpr uint32_t kFarFlag = 0x80000000u;   // key bit of a particle recycled this step
 
 // Per-step re-order bookkeeping written by the G2PD step.
 struct Reorder {
-    uint32_t* count;   // particles per new span; zeroed again by the pull
-    uint2* far;        // particles recycled this step: {new key, old index}
-    uint32_t far_cap;  // entries of far (0: the problem has no inflow face)
+    uint32_t* count;               // particles per new span; cleared by the re-order
+    uint2* far;                    // particles recycled this step: {new key, old index}
+    uint32_t far_cap;              // entries of far (0: the problem has no inflow face)
+    int mwords;                    // words of ring bits per tile
+    unsigned long long* ring;      // per tile: parts of its one-span ring that particles entered from
 };
 
 struct Geom {
@@ -53,10 +55,60 @@ struct Clock {
     unsigned pad;
 };
 
+// Rows of spans (y, z) of a tile and its one-span ring, times three x-parts
+// (the tile's own x-range and the span before and after it).
+__host__ __device__ inline int reorder_ranges(const Geom& G)
+{
+    return 3 * (G.T[1] + 2) * (G.dim == 3 ? G.T[2] + 2 : 1);
+}
+
+// The real spans [lo, hi] of a tile along axis a, plus the up to two span
+// coordinates next to them (wrapped on a periodic axis), without repeats.
+__device__ __forceinline__ int axis_ring(const Geom& G, int a, int lo, int hi, int ex[2])
+{
+    int m = 0;
+    if (a >= G.dim) return 0;
+    int l = lo - 1, r = hi + 1;
+    if (G.per[a]) {
+        l = l < 0 ? l + G.n[a] : l;
+        r = r >= G.n[a] ? r - G.n[a] : r;
+    }
+    if (l >= 0 && l < G.S[a] && (l < lo || l > hi)) ex[m++] = l;
+    if (r >= 0 && r < G.S[a] && (r < lo || r > hi) && (m == 0 || ex[0] != r)) ex[m++] = r;
+    return m;
+}
+
+// Ring part of tile t that contains span `old` (numbered as the re-order
+// lists them: 3 * (iz * ny + iy) + x part), or -1 if it is not next to t.
+__device__ __forceinline__ int ring_bit(const Geom& G, uint32_t t, const int old[3])
+{
+    const int tc[3] = {(int)(t % (uint32_t)G.nt[0]), (int)((t / (uint32_t)G.nt[0]) % (uint32_t)G.nt[1]),
+                       (int)(t / (uint32_t)(G.nt[0] * G.nt[1]))};
+    int idx[3] = {0, 0, 0}, ny = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a >= G.dim) continue;
+        const int lo = tc[a] * G.T[a], hi = min(lo + G.T[a], G.S[a]) - 1;
+        int ex[2];
+        const int m = axis_ring(G, a, lo, hi, ex);
+        if (a == 1) ny = hi - lo + 1 + m;
+        if (old[a] >= lo && old[a] <= hi) {
+            idx[a] = a == 0 ? 0 : old[a] - lo;
+        } else {
+            int f = -1;
+            for (int j = 0; j < m; ++j)
+                if (ex[j] == old[a]) f = j;
+            if (f < 0) return -1;
+            idx[a] = a == 0 ? 1 + f : hi - lo + 1 + f;
+        }
+    }
+    return 3 * (idx[2] * ny + idx[1]) + idx[0];
+}
+
 // New key of particle k: count it for its span; recycled particles go to the
 // far list (they may jump anywhere) and carry the flag bit.
-__device__ __forceinline__ uint32_t record_key(const Reorder& ro, Clock* clk, uint32_t key, bool recycled,
-                                               uint32_t k, int& err)
+__device__ __forceinline__ uint32_t record_key(const Geom& G, const Reorder& ro, Clock* clk, uint32_t key,
+                                               bool recycled, uint32_t k, int tile, const int old[3], int& err)
 {
     const unsigned m = __activemask();
     const unsigned peers = __match_any_sync(m, key);
@@ -66,6 +118,12 @@ __device__ __forceinline__ uint32_t record_key(const Reorder& ro, Clock* clk, ui
         if (slot < ro.far_cap) ro.far[slot] = make_uint2(key, k);
         else err |= ERR_TILE;
         return key | kFarFlag;
+    }
+    // a particle that enters another tile: mark the ring part it comes from
+    const uint32_t nt = key >> (G.tsh[0] + G.tsh[1] + G.tsh[2]);
+    if (nt != (uint32_t)tile) {
+        const int bit = ring_bit(G, nt, old);
+        if (bit >= 0) atomicOr(&ro.ring[(int64_t)nt * ro.mwords + (bit >> 6)], 1ull << (bit & 63));
     }
     return key;
 }
@@ -660,7 +718,10 @@ __global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R
             sp[a] = wrap_span(G, a, span_of<R, P>(G, a, xn[a], xi));
             pt.x[a][k] = xn[a];
         }
-        pt.key[k] = record_key(ro, clk, key_of<R>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, err);
+        int old[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) old[a] = wrap_span(G, a, sx[a].c);
+        pt.key[k] = record_key(G, ro, clk, key_of<R>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, tile, old, err);
         pt.E[k] = En_s;
         pt.rho[k] = rn_s;
         pt.Q[k] = Qn_s;

@@ -29,32 +29,10 @@ constexpr int kReorderChunk = kReorderThreads * kReorderItems;
 constexpr int kReorderCap = 6144;                                 // compacted particles per flush
 constexpr int kReorderMaxRanges = 1024;
 
-// Rows of spans (y, z) around a tile, times three x-ranges per row.
-__host__ __device__ inline int reorder_ranges(const Geom& G)
-{
-    return 3 * (G.T[1] + 2) * (G.dim == 3 ? G.T[2] + 2 : 1);
-}
-
 __host__ inline size_t reorder_smem(const Geom& G)
 {
     const size_t T = (size_t)G.Tvol, nr = (size_t)reorder_ranges(G);
     return ((kReorderWarps + 2) * T + kReorderCap + 4 * nr + 2 + kReorderWarps) * 4 + kReorderCap * 2;
-}
-
-// The real spans [lo, hi] of a tile along axis a, plus the up to two span
-// coordinates next to them (wrapped on a periodic axis), without repeats.
-__device__ __forceinline__ int axis_ring(const Geom& G, int a, int lo, int hi, int ex[2])
-{
-    int m = 0;
-    if (a >= G.dim) return 0;
-    int l = lo - 1, r = hi + 1;
-    if (G.per[a]) {
-        l = l < 0 ? l + G.n[a] : l;
-        r = r >= G.n[a] ? r - G.n[a] : r;
-    }
-    if (l >= 0 && l < G.S[a] && (l < lo || l > hi)) ex[m++] = l;
-    if (r >= 0 && r < G.S[a] && (r < lo || r > hi) && (m == 0 || ex[0] != r)) ex[m++] = r;
-    return m;
 }
 
 template <class R>
@@ -78,6 +56,42 @@ __device__ __forceinline__ void copy_particle(const Particles<R>& in, const Part
     out.gen[j] = gen;
 }
 
+// Copy kB particles per lane, q[u] -> j[u] where ok[u]: all loads first, so
+// that 12 kB independent loads per lane are in flight.
+template <int kB, class R>
+__device__ __forceinline__ void copy_batch(const Particles<R>& in, const Particles<R>& out, int D, const uint32_t* q,
+                                           const uint32_t* j, const bool* ok)
+{
+    R xv[kB][6], M[kB], rho[kB], E[kB], Q[kB];
+    uint32_t id[kB], gen[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+        if (!ok[u]) continue;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (a < D) { xv[u][a] = in.x[a][q[u]]; xv[u][3 + a] = in.v[a][q[u]]; }
+        M[u] = in.M[q[u]];
+        rho[u] = in.rho[q[u]];
+        E[u] = in.E[q[u]];
+        Q[u] = in.Q[q[u]];
+        id[u] = in.id[q[u]];
+        gen[u] = in.gen[q[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+        if (!ok[u]) continue;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (a < D) { out.x[a][j[u]] = xv[u][a]; out.v[a][j[u]] = xv[u][3 + a]; }
+        out.M[j[u]] = M[u];
+        out.rho[j[u]] = rho[u];
+        out.E[j[u]] = E[u];
+        out.Q[j[u]] = Q[u];
+        out.id[j[u]] = id[u];
+        out.gen[j[u]] = gen[u];
+    }
+}
+
 // Recycled particles may land anywhere: each takes a slot at the end of its
 // new span's segment (count[K] counts down to the span's stayers); their
 // order inside the span is fixed by k_reorder (by id).
@@ -95,9 +109,10 @@ __global__ void k_far_place(const uint2* __restrict__ far, uint32_t far_cap, uin
 }
 
 template <int D, class R>
-__global__ void __launch_bounds__(kReorderThreads) k_reorder(Geom G, Particles<R> in, Particles<R> out,
+__global__ void __launch_bounds__(kReorderThreads, 3) k_reorder(Geom G, Particles<R> in, Particles<R> out,
                                                              const uint32_t* __restrict__ cs_old, uint32_t* cs_new,
                                                              uint32_t* __restrict__ count, uint32_t* perm, int64_t n,
+                                                             unsigned long long* __restrict__ ring, int mwords,
                                                              Clock* clk)
 {
     extern __shared__ __align__(16) uint32_t reorder_sm[];
@@ -141,6 +156,10 @@ __global__ void __launch_bounds__(kReorderThreads) k_reorder(Geom G, Particles<R
     }
     const int ny = hi[1] - lo[1] + 1 + nex[1], nz = hi[2] - lo[2] + 1 + nex[2];
     const int nrows = ny * nz, nr = 3 * nrows;
+    // ring parts that particles entered this tile from (set by the G2PD step)
+    __shared__ unsigned long long rbits[kReorderMaxRanges / 64];
+    for (int w = tid; w < kReorderMaxRanges / 64; w += kReorderThreads)
+        rbits[w] = w < mwords ? ring[(int64_t)t * mwords + w] : 0ull;
 
     for (int k = tid; k < kReorderWarps * Tvol; k += kReorderThreads) cnt[k] = 0u;
     int err = 0;
@@ -151,20 +170,27 @@ __global__ void __launch_bounds__(kReorderThreads) k_reorder(Geom G, Particles<R
         base[k] = s0;
         endv[k] = s0 + stay;
     }
-    // 1. old index ranges of the neighbourhood
+    __syncthreads();
+    // 1. old index ranges of the tile's rows and of the ring parts entered
     for (int row = tid; row < nrows; row += kReorderThreads) {
         const int iy = row % ny, iz = row / ny;
+        const bool inner = iy <= hi[1] - lo[1] && iz <= hi[2] - lo[2];
         const int y = iy <= hi[1] - lo[1] ? lo[1] + iy : ex[1][iy - (hi[1] - lo[1] + 1)];
         const int z = iz <= hi[2] - lo[2] ? lo[2] + iz : ex[2][iz - (hi[2] - lo[2] + 1)];
+        auto marked = [&](int bit) { return ((rbits[bit >> 6] >> (bit & 63)) & 1ull) != 0ull; };
         {
-            const int a0[3] = {lo[0], y, z}, a1[3] = {hi[0], y, z};
-            const uint32_t b = cs_old[key_of<float>(G, a0)], e = cs_old[key_of<float>(G, a1) + 1];
+            uint32_t b = 0, l = 0;
+            if (inner || marked(3 * row)) {
+                const int a0[3] = {lo[0], y, z}, a1[3] = {hi[0], y, z};
+                b = cs_old[key_of<float>(G, a0)];
+                l = cs_old[key_of<float>(G, a1) + 1] - b;
+            }
             ustart[3 * row] = b;
-            ulen[3 * row] = e - b;
+            ulen[3 * row] = l;
         }
         for (int j = 0; j < 2; ++j) {
             uint32_t b = 0, l = 0;
-            if (j < nex[0]) {
+            if (j < nex[0] && marked(3 * row + 1 + j)) {
                 const int sp[3] = {ex[0][j], y, z};
                 const uint32_t k = key_of<float>(G, sp);
                 b = cs_old[k];
@@ -286,23 +312,30 @@ __global__ void __launch_bounds__(kReorderThreads) k_reorder(Geom G, Particles<R
             base[k] = run;
         }
         __syncthreads();
-        for (uint32_t j0 = wb; j0 < we; j0 += 32) {
-            const uint32_t j = j0 + lane;
-            const bool valid = j < we;
-            const uint32_t kl = valid ? list_k[j] : 0xffffffffu;
-            const uint32_t peers = __match_any_sync(0xffffffffu, kl);
-            const int leader = __ffs(peers) - 1;
-            uint32_t bv = 0;
-            if (valid && lane == leader) bv = wc[kl];
-            bv = __shfl_sync(0xffffffffu, bv, leader);
-            if (valid) {
+        constexpr int kB = sizeof(R) == 4 ? 4 : 2;     // particles per lane per batch
+        for (uint32_t j0 = wb; j0 < we; j0 += 32 * kB) {
+            uint32_t qv[kB], pv[kB];
+            bool okv[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const uint32_t j = j0 + u * 32 + lane;
+                const bool valid = j < we;
+                const uint32_t kl = valid ? list_k[j] : 0xffffffffu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, kl);
+                const int leader = __ffs(peers) - 1;
+                uint32_t bv = 0;
+                if (valid && lane == leader) bv = wc[kl];
+                bv = __shfl_sync(0xffffffffu, bv, leader);
                 const uint32_t pos = bv + __popc(peers & lt);
-                if (pos < endv[kl]) copy_particle(in, out, D, list_q[j], pos);
-                else err |= ERR_TILE;
+                okv[u] = valid && pos < endv[kl];
+                if (valid && !okv[u]) err |= ERR_TILE;
+                qv[u] = valid ? list_q[j] : 0u;
+                pv[u] = pos;
+                __syncwarp();
+                if (valid && lane == leader) wc[kl] = bv + __popc(peers);
+                __syncwarp();
             }
-            __syncwarp();
-            if (valid && lane == leader) wc[kl] = bv + __popc(peers);
-            __syncwarp();
+            copy_batch<kB>(in, out, D, qv, pv, okv);
         }
         __syncthreads();
         for (int k = tid; k < kReorderWarps * Tvol; k += kReorderThreads) cnt[k] = 0u;
@@ -310,6 +343,7 @@ __global__ void __launch_bounds__(kReorderThreads) k_reorder(Geom G, Particles<R
         __syncthreads();
     }
 
+    for (int w = tid; w < mwords; w += kReorderThreads) ring[(int64_t)t * mwords + w] = 0ull;
     // 4. every span got exactly its stayers; then its recycled particles by id
     for (int k = tid; k < Tvol; k += kReorderThreads) {
         const int64_t K = K0 + k;
