@@ -20,6 +20,7 @@ Under torchrun each rank runs its own independent replica (weak scaling).
 from __future__ import annotations
 
 import argparse
+import glob
 import json
 import os
 import subprocess
@@ -135,6 +136,36 @@ class ClockSampler:
         except Exception:
             pass
         return out
+
+
+# DRAM bytes per particle of the step kernels, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch each) of the
+# 128^3 blast, FP32, degree 2, divided by its 16,777,216 particles.  Traffic
+# grows with the particle count (same tiles, same ppc), so a full 256^3 launch
+# moves 8x those bytes.  Valid only for the kernel sources with this digest.
+MEASURED_TRAFFIC = {
+    "sources": "8ce99f8b6054e5a6",
+    "config": ("blast", 3, 2, "fp32"),
+    "bytes_per_particle": {"p2g": 49.66, "grid_g2p": 44.13, "g2pd": 55.13, "reorder": 101.58},
+}
+
+
+def sources_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2404_17057_b300", "csrc", "*.cu*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, config: str, dim: int, degree: int, precision: str, n_p: int):
+    """DRAM bytes of one launch of `kernel`, or None when the counters were
+    taken on other kernel sources or another kind of workload."""
+    t = MEASURED_TRAFFIC
+    if t["config"] != (config, dim, degree, precision) or sources_digest() != t["sources"]:
+        return None
+    return t["bytes_per_particle"][kernel] * n_p
 
 
 def peaks():
@@ -343,7 +374,8 @@ def main():
                                                            "fp64": "f64"}[args.precision],
         "data": "synthetic", "config": meta,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                     "frac": ach / hbm, "peak_source": which, "traffic": None,
+                     "frac": ach / hbm, "peak_source": which,
+                     "traffic": measured_traffic(dom, args.config, dim, int(p.cfg["degree"]), args.precision, n_p),
                      "k1_k2_k3_gbs": k123_gbs, "k1_k2_k3_frac": k123_gbs / hbm,
                      "k1_k2_k3_frac_nominal_7.7TB": k123_gbs / NOMINAL_HBM},
         "phase_ms_per_step": {"p2g": per_launch_ms["p2g"], "grid_g2p": per_launch_ms["grid_g2p"],

@@ -210,7 +210,7 @@ struct Impl {
         if (kFast) {
             if (kernel == 0) return (1 + 2 * D) * W * sizeof(float);
             if (kernel == 1) return 16 * W + D * W * sizeof(float) + (kSpanThreads / 32) * D * kStageCap * sizeof(float);
-            return (D == 3 ? 2 : 1) * 16 * W;
+            return (D == 3 ? 24 : 16) * W;
         }
         if (kernel == 0) return (1 + 2 * D) * W * sizeof(A);
         if (kernel == 1) return align16(D * W * sizeof(R)) + D * W * sizeof(A);

@@ -597,7 +597,8 @@ __global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, 
     const uint32_t beg = cs[(int64_t)tile * G.Tvol];
     const uint32_t end = cs[(int64_t)(tile + 1) * G.Tvol];
     if (beg == end) return;
-    extern __shared__ __align__(16) float4 sn[];   // per node: {Vb, V2} records
+    // per node: 3D {Vb_x, Vb_y, Vb_z, V2_y} + {V2_x, V2_z}; 2D {Vb_x, Vb_y, V2_x, V2_y}
+    extern __shared__ __align__(16) float4 sn[];
     constexpr int NS = P + 1;
     const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
     int so[3];
@@ -624,8 +625,8 @@ __global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, 
 #pragma unroll
         for (int a = 0; a < 3; ++a) vb[a] = fmaf(dt, f[a], mv[a]) * im;
         if (D == 3) {
-            sn[2 * i] = make_float4(vb[0], vb[1], vb[2], m2[0] * im);
-            sn[2 * i + 1] = make_float4(m2[1] * im, m2[2] * im, 0.f, 0.f);
+            sn[i] = make_float4(vb[0], vb[1], vb[2], m2[1] * im);
+            reinterpret_cast<float2*>(sn + W)[i] = make_float2(m2[0] * im, m2[2] * im);
         } else {
             sn[i] = make_float4(vb[0], vb[1], m2[0] * im, m2[1] * im);
         }
@@ -671,48 +672,58 @@ __global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, 
         }
         if (!ok) { err |= ERR_TILE; continue; }
         const int base = (l[2] * W1 + l[1]) * W0 + l[0];
-        // Vbar = G2P(mv'/m); div V = trace of G2PD(mv2/m)
-        float vb[3] = {0.f, 0.f, 0.f}, dx = 0.f, dy = 0.f, dz = 0.f;
+        // Vbar = G2P(mv'/m); div V = trace of G2PD(mv2/m), summed x first,
+        // then y, then z, two sums per packed FMA
+        const float2* sn2 = reinterpret_cast<const float2*>(sn + W);
+        float2 wx[NS], wxd[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            wx[a] = f2(w[0][a], w[0][a]);
+            wxd[a] = f2(dw[0][a], w[0][a]);
+        }
+        // 3D: V01 = {Vb_x, Vb_y}, V2g = {Vb_z, grad_y}, Gxz = {grad_x, grad_z}
+        // 2D: V01 = {Vb_x, Vb_y}, Gxz = {grad_x, grad_y}
+        float2 V01 = f2(0.f, 0.f), V2g = f2(0.f, 0.f), Gxz = f2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < (D == 3 ? NS : 1); ++c) {
-            float pv[3] = {0.f, 0.f, 0.f}, px = 0.f, py = 0.f, pz = 0.f;
+            float2 p01 = f2(0.f, 0.f), p2g = f2(0.f, 0.f), pxz = f2(0.f, 0.f);
 #pragma unroll
             for (int bb = 0; bb < NS; ++bb) {
                 const int row = base + (c * W1 + bb) * W0;
-                float r0 = 0.f, r1 = 0.f, r2 = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+                float2 r01 = f2(0.f, 0.f), r2g = f2(0.f, 0.f), gxz = f2(0.f, 0.f);
 #pragma unroll
                 for (int a = 0; a < NS; ++a) {
+                    const float4 q = sn[row + a];
+                    r01 = __ffma2_rn(wx[a], f2(q.x, q.y), r01);
                     if (D == 3) {
-                        const float4 q0 = sn[2 * (row + a)], q1 = sn[2 * (row + a) + 1];
-                        r0 = fmaf(w[0][a], q0.x, r0);
-                        r1 = fmaf(w[0][a], q0.y, r1);
-                        r2 = fmaf(w[0][a], q0.z, r2);
-                        gx = fmaf(dw[0][a], q0.w, gx);
-                        gy = fmaf(w[0][a], q1.x, gy);
-                        gz = fmaf(w[0][a], q1.y, gz);
+                        const float2 q2 = sn2[row + a];
+                        r2g = __ffma2_rn(wx[a], f2(q.z, q.w), r2g);
+                        gxz = __ffma2_rn(wxd[a], q2, gxz);
                     } else {
-                        const float4 q = sn[row + a];
-                        r0 = fmaf(w[0][a], q.x, r0);
-                        r1 = fmaf(w[0][a], q.y, r1);
-                        gx = fmaf(dw[0][a], q.z, gx);
-                        gy = fmaf(w[0][a], q.w, gy);
+                        gxz = __ffma2_rn(wxd[a], f2(q.z, q.w), gxz);
                     }
                 }
-                pv[0] = fmaf(w[1][bb], r0, pv[0]);
-                pv[1] = fmaf(w[1][bb], r1, pv[1]);
-                pv[2] = fmaf(w[1][bb], r2, pv[2]);
-                px = fmaf(w[1][bb], gx, px);
-                py = fmaf(dw[1][bb], gy, py);
-                pz = fmaf(w[1][bb], gz, pz);
+                const float wy = w[1][bb], dwy = dw[1][bb];
+                p01 = __ffma2_rn(f2(wy, wy), r01, p01);
+                if (D == 3) {
+                    p2g = __ffma2_rn(f2(wy, dwy), r2g, p2g);
+                    pxz = __ffma2_rn(f2(wy, wy), gxz, pxz);
+                } else {
+                    pxz = __ffma2_rn(f2(wy, dwy), gxz, pxz);
+                }
             }
-            const float wz = D == 3 ? w[2][c] : 1.f, dwz = D == 3 ? dw[2][c] : 0.f;
-            vb[0] = fmaf(wz, pv[0], vb[0]);
-            vb[1] = fmaf(wz, pv[1], vb[1]);
-            vb[2] = fmaf(wz, pv[2], vb[2]);
-            dx = fmaf(wz, px, dx);
-            dy = fmaf(wz, py, dy);
-            dz = fmaf(dwz, pz, dz);
+            if (D == 3) {
+                const float wz = w[2][c], dwz = dw[2][c];
+                V01 = __ffma2_rn(f2(wz, wz), p01, V01);
+                V2g = __ffma2_rn(f2(wz, wz), p2g, V2g);
+                Gxz = __ffma2_rn(f2(wz, dwz), pxz, Gxz);
+            } else {
+                V01 = p01;
+                Gxz = pxz;
+            }
         }
+        const float vb[3] = {V01.x, V01.y, D == 3 ? V2g.x : 0.f};
+        const float dx = Gxz.x, dy = D == 3 ? V2g.y : Gxz.y, dz = D == 3 ? Gxz.y : 0.f;
         const float dv = (dx + dy + (D == 3 ? dz : 0.f)) * ih;
         // Sec. 3 step viii: energy, density, pressure, artificial viscosity
         const float irho = __frcp_rn(rho);
