@@ -232,15 +232,26 @@ def problem_meta_only(args):
 
 
 def serving(args):
-    """C5: continuous batching vs one-at-a-time plain solves on the same stream."""
-    from paper_2404_17057_b300 import inputs as I, serve as S
+    """C5: continuous batching vs one-at-a-time plain solves on the same stream.
+    Tile shapes are tuned once per problem class before either arm is timed
+    and both arms use them."""
+    from paper_2404_17057_b300 import inputs as I, serve as S, tune as T
     reqs = I.serving_stream(count=args.serve, seed=5, steps=args.serve_steps)
     rt = not args.saturated
-    _, batched = S.Server().run(reqs, realtime=rt)
-    _, single = S.run_sequential(reqs, realtime=rt)
+    tuner = T.TileTuner()
+    t0 = time.perf_counter()
+    seen = set()
+    for r in reqs:
+        if (r["kind"], r["side"]) not in seen:
+            seen.add((r["kind"], r["side"]))
+            tuner.tile_for(I.request_problem(r))
+    tune_s = time.perf_counter() - t0
+    _, batched = S.Server(tuner=tuner).run(reqs, realtime=rt)
+    _, single = S.run_sequential(reqs, realtime=rt, tuner=tuner)
     return {"requests": len(reqs), "steps_each": args.serve_steps, "arrivals": "all at t=0" if args.saturated
             else "Poisson 50/s", "precision": "fp32_fixed64", "batched": batched, "one_at_a_time": single,
-            "speedup_solves_per_s": batched["solves_per_s"] / single["solves_per_s"]}
+            "speedup_solves_per_s": batched["solves_per_s"] / single["solves_per_s"],
+            "tiles": {"classes": len(tuner.table), "tuning_seconds": tune_s, "chosen": tuner.table}}
 
 
 def sweep(args):

@@ -194,6 +194,46 @@ mpm_status mpm_profile_read(mpm_sim* sim, double out[8], int64_t counts[8], int 
 mpm_status mpm_sort_keys_static(const uint32_t* keys, int64_t n, int64_t nkeys, uint32_t* perm,
                                 uint32_t* cell_start, void* stream);
 
+/* ---- Batched execution of independent simulations (serving) ----
+ * The paper solves one problem at a time; a batch advances many resident
+ * simulations together: each stage of the step (Algorithm 1) is one launch
+ * over a flattened list of (simulation, tile) pairs, and one step of the whole
+ * batch is recorded once as a CUDA graph and replayed.  Every member runs the
+ * same tile code with its own geometry, clock and CFL time step, so its
+ * results equal those of mpm_step on that simulation alone (bit for bit in
+ * the fixed-point mode).
+ *   mpm_batch_create  stream: cudaStream_t the batch runs on (NULL: its own).
+ *   mpm_batch_add     sim joins (it must have particles and not be in a
+ *                     batch); it takes at most nsteps further steps in batched
+ *                     runs (nsteps > 0), with dt and t_end as in mpm_step.
+ *                     While a member, the sim accepts only mpm_batch_remove,
+ *                     mpm_stream, mpm_last_error and mpm_destroy; other calls
+ *                     return MPM_ESTATE.  The batch's stream waits for the
+ *                     sim's queued work.
+ *   mpm_batch_remove  sim leaves; its stream waits for the batch's queued
+ *                     work, after which all calls on the sim are valid again.
+ *   mpm_batch_step_async  queue nsteps steps of every member (a member whose
+ *                     step budget or t_end is reached idles).  Changing the
+ *                     members re-records the graph at the next call.
+ *   mpm_batch_sync    wait for the batch's work; a member whose kernels
+ *                     raised an error is poisoned and the first such status
+ *                     is returned.
+ *   mpm_batch_destroy removes all members and releases the batch.
+ * Members are grouped by kernel variant (dimension, degree, precision,
+ * periodicity); each group's stages are single launches. */
+typedef struct mpm_batch mpm_batch;
+mpm_status mpm_batch_create(void* stream, mpm_batch** out);
+mpm_status mpm_batch_add(mpm_batch* batch, mpm_sim* sim, int64_t nsteps, double dt, double t_end);
+mpm_status mpm_batch_remove(mpm_batch* batch, mpm_sim* sim);
+mpm_status mpm_batch_step_async(mpm_batch* batch, int64_t nsteps);
+mpm_status mpm_batch_sync(mpm_batch* batch);
+/* {members, groups, launches per batched step, graph recordings so far}. */
+mpm_status mpm_batch_info(const mpm_batch* batch, int64_t out[4]);
+/* The batch's stream (cudaStream_t). */
+void* mpm_batch_stream(const mpm_batch* batch);
+const char* mpm_batch_last_error(const mpm_batch* batch);
+void mpm_batch_destroy(mpm_batch* batch);
+
 /* The simulation's stream (cudaStream_t). */
 void* mpm_stream(const mpm_sim* sim);
 /* Message of the last error of this handle (static storage if sim is NULL). */

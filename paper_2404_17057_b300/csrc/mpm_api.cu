@@ -9,6 +9,7 @@
 #include "mpm_fast.cuh"
 #include "mpm_sort.cuh"
 #include "mpm_reorder.cuh"
+#include "mpm_batch_kernels.cuh"
 
 #include <cuda_runtime.h>
 
@@ -84,6 +85,7 @@ struct mpm_sim {
     int64_t prof_launch[8] = {0};
     int64_t launches = 0;
     std::string err;
+    mpm_batch* batch = nullptr;     // set while the simulation is a member of a batch
 };
 
 namespace {
@@ -159,6 +161,11 @@ struct Vtbl {
     cudaError_t (*set_smem)(const Geom& G);
     size_t (*smem)(const Geom& G, int kernel);
     void (*reorder)(mpm_sim* s, cudaStream_t st);
+    // batched execution: descriptor of a member, stage launches of a group
+    size_t bdesc_size;
+    void (*bdesc_fill)(const mpm_sim* s, void* out);
+    void (*blaunch)(int stage, const void* desc, const TileRef* tl, int ntl, size_t smem, int per, cudaStream_t st);
+    cudaError_t (*bset_smem)(const size_t smem[4]);
 };
 
 namespace {
@@ -216,31 +223,36 @@ struct Impl {
         if (kernel == 1) return align16(D * W * sizeof(R)) + D * W * sizeof(A);
         return 2 * D * W * sizeof(R);
     }
+    // Shared-memory limits of the single-problem kernels: the device's whole
+    // shared memory (a limit, not an allocation), so that simulations with
+    // different tiles never lower each other's limit; G's needs must fit.
     static cudaError_t set_smem(const Geom& G)
     {
-        cudaError_t e = cudaFuncSetAttribute(k_reorder<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)reorder_smem(G));
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        auto allow = [&](const void* f, size_t need) -> cudaError_t {
+            cudaFuncAttributes fa;
+            cudaError_t e = cudaFuncGetAttributes(&fa, f);
+            if (e != cudaSuccess) return e;
+            const int room = optin - (int)fa.sharedSizeBytes;
+            if ((int)need > room) return cudaErrorInvalidValue;
+            return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
+        };
+        cudaError_t e = allow((const void*)k_reorder<D, R>, reorder_smem(G));
         if (e != cudaSuccess) return e;
         if constexpr (kFast) {
-            for (int per = 0; per < 2; ++per) {
-                e = cudaFuncSetAttribute(per ? (const void*)k_p2g_span<D, P, true> : (const void*)k_p2g_span<D, P, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(G, 0));
-                if (e != cudaSuccess) return e;
-                e = cudaFuncSetAttribute(per ? (const void*)k_grid_g2p_span<D, P, true>
-                                             : (const void*)k_grid_g2p_span<D, P, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(G, 1));
-                if (e != cudaSuccess) return e;
-            }
-            return cudaFuncSetAttribute(k_g2pd_fast<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem(G, 2));
+            const void* f[5] = {(const void*)k_p2g_span<D, P, true>, (const void*)k_p2g_span<D, P, false>,
+                                (const void*)k_grid_g2p_span<D, P, true>, (const void*)k_grid_g2p_span<D, P, false>,
+                                (const void*)k_g2pd_fast<D, P>};
+            const size_t z[5] = {smem(G, 0), smem(G, 0), smem(G, 1), smem(G, 1), smem(G, 2)};
+            for (int i = 0; i < 5; ++i)
+                if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
+            return cudaSuccess;
         } else {
-            e = cudaFuncSetAttribute(k_p2g<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem(G, 0));
-            if (e != cudaSuccess) return e;
-            e = cudaFuncSetAttribute(k_grid_g2p<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem(G, 1));
-            if (e != cudaSuccess) return e;
-            return cudaFuncSetAttribute(k_g2pd<D, P, R, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem(G, 2));
+            if ((e = allow((const void*)k_p2g<D, P, R, A>, smem(G, 0))) != cudaSuccess) return e;
+            if ((e = allow((const void*)k_grid_g2p<D, P, R, A>, smem(G, 1))) != cudaSuccess) return e;
+            return allow((const void*)k_g2pd<D, P, R, A>, smem(G, 2));
         }
     }
     // which bit 0: zero + P2G, bit 1: grid + G2P + P2G, bit 2: G2PD + update
@@ -255,12 +267,7 @@ struct Impl {
             k_zero<<<std::min<int64_t>(nblk(s->grid_bytes / 16), 148 * 8), kThreads, 0, st>>>(
                 (uint4*)s->grid, (int64_t)(s->grid_bytes / 16), &s->clk->active);
             if constexpr (kFast) {
-                FieldPtrs o = {};
-                o.p[0] = (float*)gr.m;
-                for (int a = 0; a < D; ++a) {
-                    o.p[1 + a] = (float*)gr.mv[a];
-                    o.p[1 + D + a] = (float*)gr.f[a];
-                }
+                const FieldPtrs o = p2g_fields(gr);
                 if (G.per[0] | G.per[1] | G.per[2])
                     k_p2g_span<D, P, true><<<G.ntiles, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk);
                 else
@@ -272,8 +279,7 @@ struct Impl {
         }
         if (which & 2) {
             if constexpr (kFast) {
-                FieldPtrs o = {};
-                for (int a = 0; a < D; ++a) o.p[a] = (float*)gr.mv2[a];
+                const FieldPtrs o = g2p_fields(gr);
                 if (G.per[0] | G.per[1] | G.per[2])
                     k_grid_g2p_span<D, P, true><<<G.ntiles, kSpanThreads, smem(G, 1), st>>>(G, pt, gr, o, cs, s->clk);
                 else
@@ -298,6 +304,100 @@ struct Impl {
             s->G, parts<R>(s->buf[b]), parts<R>(s->buf[1 - b]), s->cs[b], s->cs[1 - b], s->count, s->perm, s->np,
             s->ring, s->mwords, s->clk);
         s->launches += 1;
+    }
+    static FieldPtrs p2g_fields(const Grid<A, R>& gr)
+    {
+        FieldPtrs o = {};
+        o.p[0] = (float*)gr.m;
+        for (int a = 0; a < D; ++a) {
+            o.p[1 + a] = (float*)gr.mv[a];
+            o.p[1 + D + a] = (float*)gr.f[a];
+        }
+        return o;
+    }
+    static FieldPtrs g2p_fields(const Grid<A, R>& gr)
+    {
+        FieldPtrs o = {};
+        for (int a = 0; a < D; ++a) o.p[a] = (float*)gr.mv2[a];
+        return o;
+    }
+    static void bdesc_fill(const mpm_sim* s, void* out)
+    {
+        BatchProb<R, A> d;
+        memset(&d, 0, sizeof d);
+        d.G = s->G;
+        d.pt[0] = parts<R>(s->buf[0]);
+        d.pt[1] = parts<R>(s->buf[1]);
+        d.gr = grid_view<A, R>(s);
+        if constexpr (kFast) {
+            d.p2g_out = p2g_fields(d.gr);
+            d.g2p_out = g2p_fields(d.gr);
+        }
+        d.cs[0] = s->cs[0];
+        d.cs[1] = s->cs[1];
+        d.ro = {s->count, s->far, s->far_cap, s->mwords, s->ring};
+        d.perm = s->perm;
+        d.np = s->np;
+        d.clk = s->clk;
+        memcpy(out, &d, sizeof d);
+    }
+    // stage 0: P2G, 1: grid + G2P + P2G, 2: G2PD + update, 3: re-order
+    static void blaunch(int stage, const void* dv, const TileRef* tl, int ntl, size_t sm, int per, cudaStream_t st)
+    {
+        const BatchProb<R, A>* d = static_cast<const BatchProb<R, A>*>(dv);
+        if (ntl <= 0) return;
+        if (stage == 3) {
+            kb_reorder<D, R, A><<<ntl, kReorderThreads, sm, st>>>(d, tl);
+            return;
+        }
+        if constexpr (kFast) {
+            if (stage == 0) {
+                if (per) kb_p2g_span<D, P, true><<<ntl, kP2GThreads, sm, st>>>(d, tl);
+                else kb_p2g_span<D, P, false><<<ntl, kP2GThreads, sm, st>>>(d, tl);
+            } else if (stage == 1) {
+                if (per) kb_grid_g2p_span<D, P, true><<<ntl, kSpanThreads, sm, st>>>(d, tl);
+                else kb_grid_g2p_span<D, P, false><<<ntl, kSpanThreads, sm, st>>>(d, tl);
+            } else {
+                kb_g2pd_fast<D, P><<<ntl, 256, sm, st>>>(d, tl);
+            }
+        } else {
+            if (stage == 0) kb_p2g<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
+            else if (stage == 1) kb_grid_g2p<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
+            else kb_g2pd<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
+        }
+    }
+    // Allow every batched kernel the device's whole shared memory (a limit,
+    // not an allocation: each launch asks for what its group needs), so that
+    // groups and batches with different tiles never undercut each other;
+    // fails if a group needs more than a kernel can have.
+    static cudaError_t bset_smem(const size_t sm[4])
+    {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        auto allow = [&](const void* f, size_t need) -> cudaError_t {
+            cudaFuncAttributes fa;
+            cudaError_t e = cudaFuncGetAttributes(&fa, f);
+            if (e != cudaSuccess) return e;
+            const int room = optin - (int)fa.sharedSizeBytes;
+            if ((int)need > room) return cudaErrorInvalidValue;
+            return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
+        };
+        cudaError_t e = allow((const void*)kb_reorder<D, R, A>, sm[3]);
+        if (e != cudaSuccess) return e;
+        if constexpr (kFast) {
+            const void* f[5] = {(const void*)kb_p2g_span<D, P, true>, (const void*)kb_p2g_span<D, P, false>,
+                                (const void*)kb_grid_g2p_span<D, P, true>, (const void*)kb_grid_g2p_span<D, P, false>,
+                                (const void*)kb_g2pd_fast<D, P>};
+            const size_t z[5] = {sm[0], sm[0], sm[1], sm[1], sm[2]};
+            for (int i = 0; i < 5; ++i)
+                if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
+            return cudaSuccess;
+        } else {
+            if ((e = allow((const void*)kb_p2g<D, P, R, A>, sm[0])) != cudaSuccess) return e;
+            if ((e = allow((const void*)kb_grid_g2p<D, P, R, A>, sm[1])) != cudaSuccess) return e;
+            return allow((const void*)kb_g2pd<D, P, R, A>, sm[2]);
+        }
     }
     static void keys(mpm_sim* s, int b, cudaStream_t st)
     {
@@ -338,7 +438,7 @@ const Vtbl* vtbl_of()
 {
     typedef Impl<D, P, R, A> I;
     static const Vtbl v = {I::step_kernels, I::keys, I::gather, I::cfl_init, I::cons, I::from_double, I::set_smem,
-                           I::smem, I::reorder};
+                           I::smem, I::reorder, sizeof(BatchProb<R, A>), I::bdesc_fill, I::blaunch, I::bset_smem};
     return &v;
 }
 
@@ -685,6 +785,7 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
                              const double* rho, const double* e)
 {
     if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
     if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
     if (s->started) return fail(s, MPM_ESTATE, "particles can only be added before the first step");
     if (n < 0) return fail(s, MPM_EINVAL, "n < 0");
@@ -799,6 +900,7 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
 mpm_status mpm_set_obstacle_mask(mpm_sim* s, const uint8_t* mask, const double* normals)
 {
     if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
     if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
     if (!mask || !normals) return fail(s, MPM_EINVAL, "NULL input array");
     const Geom& G = s->G;
@@ -856,6 +958,7 @@ static mpm_status ensure_cfl(mpm_sim* s)
 mpm_status mpm_cfl_dt(mpm_sim* s, double* dt_out)
 {
     if (!s || !dt_out) return fail(s, MPM_EINVAL, "NULL argument");
+    if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
     if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
     mpm_status st = ensure_cfl(s);
     if (st != MPM_OK) return st;
@@ -900,6 +1003,7 @@ static int64_t step_launch_count(const mpm_sim* s)
 mpm_status mpm_step_async(mpm_sim* s, int64_t nsteps, double dt, double t_end)
 {
     if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
     if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
     if (nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t_end)) return fail(s, MPM_EINVAL, "bad step arguments");
     mpm_status st = ensure_cfl(s);
@@ -935,6 +1039,7 @@ mpm_status mpm_step_async(mpm_sim* s, int64_t nsteps, double dt, double t_end)
 mpm_status mpm_sync(mpm_sim* s)
 {
     if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
     if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
     return check_device_errors(s);
 }
@@ -991,6 +1096,7 @@ static mpm_status read_u32(mpm_sim* s, const uint32_t* src, int64_t n, double* o
 mpm_status mpm_read_state(mpm_sim* s, int field, double* out, int64_t count)
 {
     if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
     if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
     if (!out) return fail(s, MPM_EINVAL, "out is NULL");
     const int64_t need = mpm_field_size(s, field);
@@ -1076,6 +1182,7 @@ mpm_status mpm_read_state(mpm_sim* s, int field, double* out, int64_t count)
 mpm_status mpm_read_grid_fixed(mpm_sim* s, int field, int64_t* out, int64_t count)
 {
     if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
     if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
     if (s->cfg.precision != MPM_FP32_FIXED64) return fail(s, MPM_EINVAL, "not a fixed-point simulation");
     if (!out || field < MPM_FIELD_GRID_M || field > MPM_FIELD_GRID_MV2) return fail(s, MPM_EINVAL, "bad field");
@@ -1100,6 +1207,7 @@ mpm_status mpm_read_grid_fixed(mpm_sim* s, int field, int64_t* out, int64_t coun
 mpm_status mpm_conservation(mpm_sim* s, double out[5])
 {
     if (!s || !out) return fail(s, MPM_EINVAL, "NULL argument");
+    if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
     if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
     mpm_status st = check_device_errors(s);
     if (st != MPM_OK) return st;
@@ -1117,6 +1225,7 @@ mpm_status mpm_conservation(mpm_sim* s, double out[5])
 mpm_status mpm_sizes(const mpm_sim* s, int64_t out[4])
 {
     if (!s || !out) return MPM_EINVAL;
+    if (s->batch) return MPM_ESTATE;
     Clock c;
     memset(&c, 0, sizeof(c));
     if (cudaMemcpyAsync(&c, s->clk, sizeof(Clock), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
@@ -1132,6 +1241,7 @@ mpm_status mpm_sizes(const mpm_sim* s, int64_t out[4])
 mpm_status mpm_profile(mpm_sim* s, int enable)
 {
     if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
     s->profiling = enable != 0;
     return MPM_OK;
 }
@@ -1139,6 +1249,7 @@ mpm_status mpm_profile(mpm_sim* s, int enable)
 mpm_status mpm_profile_read(mpm_sim* s, double out[8], int64_t counts[8], int reset)
 {
     if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
+    if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
     mpm_status st = collect_profile(s);
     if (st != MPM_OK) return st;
     // launches per phase of one step, times the profiled steps
@@ -1171,6 +1282,7 @@ const char* mpm_last_error(const mpm_sim* s)
 void mpm_destroy(mpm_sim* s)
 {
     if (!s) return;
+    if (s->batch) mpm_batch_remove(s->batch, s);
     if (s->stream) cudaStreamSynchronize(s->stream);
     drop_graphs(s);
     for (auto& ps : s->prof)
@@ -1187,3 +1299,4 @@ void mpm_destroy(mpm_sim* s)
 
 // The allocation-free re-order entry point (same translation unit).
 #include "mpm_noalloc.cu"
+#include "mpm_batch.cu"

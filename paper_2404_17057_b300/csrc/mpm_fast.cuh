@@ -225,11 +225,10 @@ __device__ __forceinline__ void load_state(const Particles<float>& pt, uint32_t 
 constexpr int kP2GThreads = 64;
 
 template <int D, int P, bool PER>
-__global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, Particles<float> pt, FieldPtrs out,
-                                                              const uint32_t* __restrict__ cs, Clock* clk)
+__device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<float>& pt, const FieldPtrs& out,
+                                              const uint32_t* __restrict__ cs, Clock* clk, const int tile)
 {
     if (!clk->active) return;
-    const int tile = blockIdx.x;
     const int64_t kb = (int64_t)tile * G.Tvol;
     if (cs[kb] == cs[kb + G.Tvol]) return;
     extern __shared__ __align__(16) float sm[];
@@ -418,15 +417,21 @@ __global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, Particles<f
     flush_window<D, P>(G, so, sm, NF, out);
 }
 
+template <int D, int P, bool PER>
+__global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, Particles<float> pt, FieldPtrs out,
+                                                              const uint32_t* __restrict__ cs, Clock* clk)
+{
+    p2g_span_tile<D, P, PER>(G, pt, out, cs, clk, blockIdx.x);
+}
+
 // ----------------------------------------- K2: grid update + G2P + P2G
 
 template <int D, int P, bool PER>
-__global__ void __launch_bounds__(kSpanThreads, 3) k_grid_g2p_span(Geom G, Particles<float> pt,
-                                                                   Grid<float, float> gr, FieldPtrs out,
-                                                                   const uint32_t* __restrict__ cs, Clock* clk)
+__device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particles<float>& pt,
+                                                   const Grid<float, float>& gr, const FieldPtrs& out,
+                                                   const uint32_t* __restrict__ cs, Clock* clk, const int tile)
 {
     if (!clk->active) return;
-    const int tile = blockIdx.x;
     const int64_t kb = (int64_t)tile * G.Tvol;
     if (cs[kb] == cs[kb + G.Tvol]) return;
     extern __shared__ __align__(16) float sm[];
@@ -586,14 +591,22 @@ __global__ void __launch_bounds__(kSpanThreads, 3) k_grid_g2p_span(Geom G, Parti
     flush_window<D, P>(G, so, s2, D, out);
 }
 
+template <int D, int P, bool PER>
+__global__ void __launch_bounds__(kSpanThreads, 3) k_grid_g2p_span(Geom G, Particles<float> pt,
+                                                                   Grid<float, float> gr, FieldPtrs out,
+                                                                   const uint32_t* __restrict__ cs, Clock* clk)
+{
+    grid_g2p_span_tile<D, P, PER>(G, pt, gr, out, cs, clk, blockIdx.x);
+}
+
 // ------------------------------- K3: G2PD + particle update + move + key
 
 template <int D, int P>
-__global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, Grid<float, float> gr,
-                                                   const uint32_t* __restrict__ cs, Clock* clk, Reorder ro)
+__device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<float>& pt, const Grid<float, float>& gr,
+                                               const uint32_t* __restrict__ cs, Clock* clk, const Reorder& ro,
+                                               const int tile)
 {
     if (!clk->active) return;
-    const int tile = blockIdx.x;
     const uint32_t beg = cs[(int64_t)tile * G.Tvol];
     const uint32_t end = cs[(int64_t)(tile + 1) * G.Tvol];
     if (beg == end) return;
@@ -828,6 +841,13 @@ __global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, 
         atomic_max_nonneg(&clk->cmax_bits, (double)cmax);
         if (err) atomicOr(&clk->err, err);
     }
+}
+
+template <int D, int P>
+__global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, Grid<float, float> gr,
+                                                   const uint32_t* __restrict__ cs, Clock* clk, Reorder ro)
+{
+    g2pd_fast_tile<D, P>(G, pt, gr, cs, clk, ro, blockIdx.x);
 }
 
 }  // namespace mpm

@@ -52,7 +52,8 @@ struct Clock {
     int active, done, last, err;
     unsigned long long vmax_bits, cmax_bits;   // bits of non-negative doubles
     unsigned nfar;                             // recycled particles this step
-    unsigned pad;
+    int par;                                   // batched runs: buffer holding the state
+    long long step_end;                        // > 0: no step starts at or after this count
 };
 
 // Rows of spans (y, z) of a tile and its one-span ring, times three x-parts
@@ -382,12 +383,11 @@ __device__ __forceinline__ void node_weights(const AxisSup<R>* s, int kx, int ky
 }
 
 template <int D, int P, class R, class A>
-__global__ void __launch_bounds__(256) k_p2g(Geom G, Particles<R> pt, Grid<A, R> gr, const uint32_t* cellstart,
-                                             Clock* clk)
+__device__ __forceinline__ void p2g_tile(const Geom& G, const Particles<R>& pt, const Grid<A, R>& gr,
+                                         const uint32_t* cellstart, Clock* clk, const int tile)
 {
     typedef Op<R> O;
     if (!clk->active) return;
-    const int tile = blockIdx.x;
     const uint32_t beg = cellstart[(int64_t)tile * G.Tvol];
     const uint32_t end = cellstart[(int64_t)(tile + 1) * G.Tvol];
     if (beg == end) return;
@@ -452,15 +452,21 @@ __global__ void __launch_bounds__(256) k_p2g(Geom G, Particles<R> pt, Grid<A, R>
     }
 }
 
+template <int D, int P, class R, class A>
+__global__ void __launch_bounds__(256) k_p2g(Geom G, Particles<R> pt, Grid<A, R> gr, const uint32_t* cellstart,
+                                             Clock* clk)
+{
+    p2g_tile<D, P, R, A>(G, pt, gr, cellstart, clk, blockIdx.x);
+}
+
 // ----------------------------------------------- grid update + G2P + P2G
 
 template <int D, int P, class R, class A>
-__global__ void __launch_bounds__(256) k_grid_g2p(Geom G, Particles<R> pt, Grid<A, R> gr,
-                                                  const uint32_t* cellstart, Clock* clk)
+__device__ __forceinline__ void grid_g2p_tile(const Geom& G, const Particles<R>& pt, const Grid<A, R>& gr,
+                                              const uint32_t* cellstart, Clock* clk, const int tile)
 {
     typedef Op<R> O;
     if (!clk->active) return;
-    const int tile = blockIdx.x;
     const uint32_t beg = cellstart[(int64_t)tile * G.Tvol];
     const uint32_t end = cellstart[(int64_t)(tile + 1) * G.Tvol];
     if (beg == end) return;
@@ -555,15 +561,21 @@ __global__ void __launch_bounds__(256) k_grid_g2p(Geom G, Particles<R> pt, Grid<
     }
 }
 
+template <int D, int P, class R, class A>
+__global__ void __launch_bounds__(256) k_grid_g2p(Geom G, Particles<R> pt, Grid<A, R> gr,
+                                                  const uint32_t* cellstart, Clock* clk)
+{
+    grid_g2p_tile<D, P, R, A>(G, pt, gr, cellstart, clk, blockIdx.x);
+}
+
 // ------------------------------------ G2PD + particle update + move + key
 
 template <int D, int P, class R, class A>
-__global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R> gr, const uint32_t* cellstart,
-                                              Clock* clk, Reorder ro)
+__device__ __forceinline__ void g2pd_tile(const Geom& G, const Particles<R>& pt, const Grid<A, R>& gr,
+                                          const uint32_t* cellstart, Clock* clk, const Reorder& ro, const int tile)
 {
     typedef Op<R> O;
     if (!clk->active) return;
-    const int tile = blockIdx.x;
     const uint32_t beg = cellstart[(int64_t)tile * G.Tvol];
     const uint32_t end = cellstart[(int64_t)(tile + 1) * G.Tvol];
     if (beg == end) return;
@@ -739,14 +751,20 @@ __global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R
     }
 }
 
+template <int D, int P, class R, class A>
+__global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R> gr, const uint32_t* cellstart,
+                                              Clock* clk, Reorder ro)
+{
+    g2pd_tile<D, P, R, A>(G, pt, gr, cellstart, clk, ro, blockIdx.x);
+}
+
 // ---------------------------------------------------------- time control
 
 // Decide this step's dt (fixed or CFL) and clip it to t_end (step xiii).
-__global__ void k_prepare(Clock* clk)
+__device__ __forceinline__ void prepare_clock(Clock& c)
 {
-    Clock& c = *clk;
     c.nfar = 0u;
-    if (c.done || c.err) { c.active = 0; return; }
+    if (c.done || c.err || (c.step_end > 0 && c.step >= c.step_end)) { c.active = 0; return; }
     double h = c.dt_fixed > 0.0 ? c.dt_fixed : c.dt_next;
     if (!(h > 0.0)) { c.err |= ERR_NONFINITE; c.active = 0; return; }
     c.last = 0;
@@ -757,9 +775,10 @@ __global__ void k_prepare(Clock* clk)
     c.cmax_bits = 0ull;
 }
 
-__global__ void k_finalize(Clock* clk, double cfl_h)
+__global__ void k_prepare(Clock* clk) { prepare_clock(*clk); }
+
+__device__ __forceinline__ void finalize_clock(Clock& c, double cfl_h)
 {
-    Clock& c = *clk;
     if (!c.active) return;
     c.t = c.last ? c.t_end : c.t + c.dt_cur;
     c.step += 1;
@@ -767,6 +786,15 @@ __global__ void k_finalize(Clock* clk, double cfl_h)
     const double cs = __longlong_as_double((long long)c.cmax_bits);
     c.dt_next = (v + cs) > 0.0 ? cfl_h / (v + cs) : 0.0;
     if (c.last || (c.t_end > 0.0 && c.t >= c.t_end)) c.done = 1;
+}
+
+__global__ void k_finalize(Clock* clk, double cfl_h) { finalize_clock(*clk, cfl_h); }
+
+// Step budget (from the current step) and buffer parity of a batch member.
+__global__ void k_set_batch(Clock* clk, long long nsteps, int par)
+{
+    clk->step_end = nsteps > 0 ? clk->step + nsteps : 0;
+    clk->par = par;
 }
 
 __global__ void k_set_params(Clock* clk, double dt_fixed, double t_end)

@@ -95,12 +95,14 @@ __device__ __forceinline__ void copy_batch(const Particles<R>& in, const Particl
 // Recycled particles may land anywhere: each takes a slot at the end of its
 // new span's segment (count[K] counts down to the span's stayers); their
 // order inside the span is fixed by k_reorder (by id).
-__global__ void k_far_place(const uint2* __restrict__ far, uint32_t far_cap, uint32_t* __restrict__ count,
-                            const uint32_t* __restrict__ cs_new, uint32_t* __restrict__ perm, const Clock* clk)
+__device__ __forceinline__ void far_place_block(const uint2* __restrict__ far, uint32_t far_cap,
+                                                uint32_t* __restrict__ count, const uint32_t* __restrict__ cs_new,
+                                                uint32_t* __restrict__ perm, const Clock* clk, unsigned blk,
+                                                unsigned nblk)
 {
     if (!clk->active) return;
     const unsigned F = min(clk->nfar, far_cap);
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < F; i += gridDim.x * blockDim.x) {
+    for (unsigned i = blk * blockDim.x + threadIdx.x; i < F; i += nblk * blockDim.x) {
         const uint2 e = far[i];
         const uint32_t r = atomicSub(&count[e.x], 1u) - 1u;
         const uint32_t pos = cs_new[e.x] + r;
@@ -108,12 +110,17 @@ __global__ void k_far_place(const uint2* __restrict__ far, uint32_t far_cap, uin
     }
 }
 
+__global__ void k_far_place(const uint2* __restrict__ far, uint32_t far_cap, uint32_t* __restrict__ count,
+                            const uint32_t* __restrict__ cs_new, uint32_t* __restrict__ perm, const Clock* clk)
+{
+    far_place_block(far, far_cap, count, cs_new, perm, clk, blockIdx.x, gridDim.x);
+}
+
 template <int D, class R>
-__global__ void __launch_bounds__(kReorderThreads, 3) k_reorder(Geom G, Particles<R> in, Particles<R> out,
-                                                             const uint32_t* __restrict__ cs_old, uint32_t* cs_new,
-                                                             uint32_t* __restrict__ count, uint32_t* perm, int64_t n,
-                                                             unsigned long long* __restrict__ ring, int mwords,
-                                                             Clock* clk)
+__device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& in, const Particles<R>& out,
+                                             const uint32_t* __restrict__ cs_old, uint32_t* cs_new,
+                                             uint32_t* __restrict__ count, uint32_t* perm, int64_t n,
+                                             unsigned long long* __restrict__ ring, int mwords, Clock* clk, const int t)
 {
     extern __shared__ __align__(16) uint32_t reorder_sm[];
     const int Tvol = G.Tvol;
@@ -129,7 +136,6 @@ __global__ void __launch_bounds__(kReorderThreads, 3) k_reorder(Geom G, Particle
     uint32_t* wsum = soff + nrmax + 1;                    // per-warp totals (+1 spare)
     uint16_t* list_k = reinterpret_cast<uint16_t*>(wsum + kReorderWarps + 1);
 
-    const int t = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t K0 = (int64_t)t * Tvol;
 
@@ -364,6 +370,16 @@ __global__ void __launch_bounds__(kReorderThreads, 3) k_reorder(Geom G, Particle
         for (uint32_t i = fb; i < fe; ++i) copy_particle(in, out, D, perm[i], i);
     }
     if (err) atomicOr(&clk->err, err);
+}
+
+template <int D, class R>
+__global__ void __launch_bounds__(kReorderThreads, 3) k_reorder(Geom G, Particles<R> in, Particles<R> out,
+                                                             const uint32_t* __restrict__ cs_old, uint32_t* cs_new,
+                                                             uint32_t* __restrict__ count, uint32_t* perm, int64_t n,
+                                                             unsigned long long* __restrict__ ring, int mwords,
+                                                             Clock* clk)
+{
+    reorder_tile<D, R>(G, in, out, cs_old, cs_new, count, perm, n, ring, mwords, clk, blockIdx.x);
 }
 
 // Sorted keys from the cell-start table (for reading the state back).

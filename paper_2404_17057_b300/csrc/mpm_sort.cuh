@@ -41,21 +41,26 @@ __device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t* w
     return v;
 }
 
-// Phase 1: per-tile sums.
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* in, int64_t n, uint32_t* partial)
+// Phase 1: per-tile sums (block blk of the scan).
+__device__ __forceinline__ void scan_reduce_block(const uint32_t* in, int64_t n, uint32_t* partial, int64_t blk)
 {
     __shared__ uint32_t ws[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    const int64_t base = blk * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i)
         if (base + i < n) s += in[base + i];
     s = block_inclusive_scan(s, ws);
-    if (threadIdx.x == blockDim.x - 1) partial[blockIdx.x] = s;
+    if (threadIdx.x == blockDim.x - 1) partial[blk] = s;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* in, int64_t n, uint32_t* partial)
+{
+    scan_reduce_block(in, n, partial, blockIdx.x);
 }
 
 // Phase 2: exclusive scan of the per-tile sums by one block.
-__global__ void __launch_bounds__(kScanThreads) k_scan_partials(uint32_t* partial, int64_t m)
+__device__ __forceinline__ void scan_partials_block(uint32_t* partial, int64_t m)
 {
     __shared__ uint32_t ws[32];
     __shared__ uint32_t carry;
@@ -73,13 +78,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partials(uint32_t* partia
     }
 }
 
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(uint32_t* partial, int64_t m)
+{
+    scan_partials_block(partial, m);
+}
+
 // Phase 3: exclusive scan inside each tile plus its offset; out[n] = total
 // when write_total is set (out must then hold n + 1 values).
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, int64_t n, const uint32_t* partial,
-                                                           uint32_t* out, int write_total)
+__device__ __forceinline__ void scan_down_block(const uint32_t* in, int64_t n, const uint32_t* partial, uint32_t* out,
+                                                int write_total, int64_t blk)
 {
     __shared__ uint32_t ws[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    const int64_t base = blk * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems], s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
@@ -87,7 +97,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, 
         s += v[i];
     }
     uint32_t inc = block_inclusive_scan(s, ws);
-    uint32_t run = partial[blockIdx.x] + inc - s;
+    uint32_t run = partial[blk] + inc - s;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         if (base + i < n) out[base + i] = run;
@@ -96,7 +106,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, 
     }
 }
 
-inline int64_t scan_blocks(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, int64_t n, const uint32_t* partial,
+                                                           uint32_t* out, int write_total)
+{
+    scan_down_block(in, n, partial, out, write_total, blockIdx.x);
+}
+
+__host__ __device__ inline int64_t scan_blocks(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 
 // Exclusive scan of n u32 values; partial needs scan_blocks(n) entries.
 inline void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* partial, int write_total,

@@ -27,7 +27,9 @@ STATUS = {0: "MPM_OK", 1: "MPM_EINVAL", 2: "MPM_ENOMEM", 3: "MPM_ECUDA", 4: "MPM
 EXPORTS = ["mpm_create", "mpm_add_particles", "mpm_set_obstacle_mask", "mpm_cfl_dt", "mpm_step",
            "mpm_step_async", "mpm_sync", "mpm_read_state", "mpm_read_grid_fixed", "mpm_field_size",
            "mpm_conservation", "mpm_sizes", "mpm_profile", "mpm_profile_read", "mpm_stream",
-           "mpm_last_error", "mpm_destroy", "mpm_sort_keys_static"]
+           "mpm_last_error", "mpm_destroy", "mpm_sort_keys_static", "mpm_batch_create", "mpm_batch_add",
+           "mpm_batch_remove", "mpm_batch_step_async", "mpm_batch_sync", "mpm_batch_info", "mpm_batch_stream",
+           "mpm_batch_last_error", "mpm_batch_destroy"]
 SORT_STATIC_MAX_KEYS = 262144
 SORT_STATIC_MAX_SPANS = 16777216
 
@@ -86,8 +88,21 @@ def load(path: str = LIB_PATH):
     L.mpm_destroy.argtypes = [vp]
     L.mpm_destroy.restype = None
     L.mpm_sort_keys_static.argtypes = [vp, i64, i64, vp, vp, vp]
+    L.mpm_batch_create.argtypes = [vp, P(vp)]
+    L.mpm_batch_add.argtypes = [vp, vp, i64, d, d]
+    L.mpm_batch_remove.argtypes = [vp, vp]
+    L.mpm_batch_step_async.argtypes = [vp, i64]
+    L.mpm_batch_sync.argtypes = [vp]
+    L.mpm_batch_info.argtypes = [vp, vp]
+    L.mpm_batch_stream.argtypes = [vp]
+    L.mpm_batch_stream.restype = vp
+    L.mpm_batch_last_error.argtypes = [vp]
+    L.mpm_batch_last_error.restype = C.c_char_p
+    L.mpm_batch_destroy.argtypes = [vp]
+    L.mpm_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("mpm_field_size", "mpm_stream", "mpm_last_error", "mpm_destroy"):
+        if name not in ("mpm_field_size", "mpm_stream", "mpm_last_error", "mpm_destroy", "mpm_batch_stream",
+                        "mpm_batch_last_error", "mpm_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -284,6 +299,49 @@ def mpm_sort_keys_static(keys_ptr: int, n: int, nkeys: int, perm_ptr: int, cell_
     _check(load().mpm_sort_keys_static(keys_ptr, int(n), int(nkeys), perm_ptr, cell_start_ptr, stream or None))
 
 
+def _bcheck(code: int, bh=None):
+    if code != 0:
+        msg = load().mpm_batch_last_error(bh)
+        raise MPMError(code, msg.decode() if msg else "")
+
+
+def mpm_batch_create(stream=None):
+    h = C.c_void_p()
+    _bcheck(load().mpm_batch_create(stream, C.byref(h)))
+    return h
+
+
+def mpm_batch_add(bh, h, nsteps: int, dt: float = 0.0, t_end: float = 0.0):
+    _bcheck(load().mpm_batch_add(bh, h, int(nsteps), float(dt), float(t_end)), bh)
+
+
+def mpm_batch_remove(bh, h):
+    _bcheck(load().mpm_batch_remove(bh, h), bh)
+
+
+def mpm_batch_step_async(bh, nsteps: int):
+    _bcheck(load().mpm_batch_step_async(bh, int(nsteps)), bh)
+
+
+def mpm_batch_sync(bh):
+    _bcheck(load().mpm_batch_sync(bh), bh)
+
+
+def mpm_batch_info(bh) -> dict:
+    out = np.zeros(4, dtype=np.int64)
+    _bcheck(load().mpm_batch_info(bh, _ptr(out)), bh)
+    return {"members": int(out[0]), "groups": int(out[1]), "launches_per_step": int(out[2]),
+            "recordings": int(out[3])}
+
+
+def mpm_batch_stream(bh) -> int:
+    return int(load().mpm_batch_stream(bh) or 0)
+
+
+def mpm_batch_destroy(bh):
+    load().mpm_batch_destroy(bh)
+
+
 # ------------------------------------------------------------ convenience
 
 class Simulation:
@@ -362,3 +420,49 @@ class Simulation:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Owning wrapper of one mpm_batch handle (members are Simulation objects)."""
+
+    def __init__(self, stream=None):
+        import torch
+        self._own = None
+        if stream is None:
+            self._own = torch.cuda.Stream()
+            stream = self._own.cuda_stream
+        self._h = mpm_batch_create(stream)
+        self.members: list[Simulation] = []
+
+    def add(self, sim: Simulation, nsteps: int, dt: float = 0.0, t_end: float = 0.0):
+        mpm_batch_add(self._h, sim.handle, nsteps, dt, t_end)
+        self.members.append(sim)
+
+    def remove(self, sim: Simulation):
+        mpm_batch_remove(self._h, sim.handle)
+        self.members.remove(sim)
+
+    def step_async(self, nsteps: int):
+        mpm_batch_step_async(self._h, nsteps)
+
+    def sync(self):
+        mpm_batch_sync(self._h)
+
+    def info(self) -> dict:
+        return mpm_batch_info(self._h)
+
+    @property
+    def stream(self) -> int:
+        return mpm_batch_stream(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            mpm_batch_destroy(self._h)
+            self._h = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

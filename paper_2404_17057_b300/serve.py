@@ -3,15 +3,17 @@
 Requests (independent problems of different sizes) arrive over time.  A
 request is admitted as soon as it has arrived and its device memory fits in
 the remaining HBM budget; its state then stays resident on the GPU until it
-finishes.  Every admitted problem advances in chunks of steps that are
-queued asynchronously (each step a CUDA-graph launch) on the problem's own
-stream, so the work of all admitted problems overlaps on the device.  A
-problem whose last chunk has completed is read back and retired at once,
-freeing its slot and memory for waiting requests.
+finishes.  All admitted problems are members of one batch (mpm_batch_*): each
+stage of a step is one launch over the flattened list of (problem, tile)
+pairs, one step of the whole batch is a recorded CUDA graph, and the batch
+advances in chunks of steps.  When a chunk completes, problems that have done
+their steps are read back and retired at once, freeing memory for waiting
+requests, which join before the next chunk.  Tile shapes come from the tile
+tuner (tune.py) when one is given.
 
 The baseline `run_sequential` solves the same requests one at a time in
-arrival order with the same kernels.  Both report solves/s and the p50/p99
-latency from arrival to the result on the host.
+arrival order with the same kernels and tile shapes.  Both report solves/s
+and the p50/p99 latency from arrival to the result on the host.
 """
 from __future__ import annotations
 
@@ -77,12 +79,14 @@ def _finish(sim, req, arrival, admitted, n, steps) -> Result:
 
 
 class Server:
-    """Admission by HBM budget, resident state, chunked asynchronous steps."""
+    """Continuous batching over one mpm_batch: admission by HBM budget, state
+    resident on the device, all members advanced together chunk by chunk."""
 
-    def __init__(self, hbm_budget: float = 120e9, chunk: int = 25, max_active: int = 256):
+    def __init__(self, hbm_budget: float = 120e9, chunk: int = 25, max_active: int = 256, tuner=None):
         self.budget = float(hbm_budget)
         self.chunk = int(chunk)
         self.max_active = int(max_active)
+        self.tuner = tuner
 
     def run(self, requests: list[dict], realtime: bool = True) -> tuple[list[Result], dict]:
         import torch
@@ -92,57 +96,68 @@ class Server:
         results: list[Result] = []
         used = 0.0
         nxt = 0
+        batch = M.Batch()
+        ev = None
         t0 = time.perf_counter()
-        while nxt < len(reqs) or waiting or active:
-            now = time.perf_counter() - t0
-            # arrivals (all at once when not in real time)
-            while nxt < len(reqs) and (not realtime or reqs[nxt]["arrival"] <= now):
-                r = reqs[nxt]
-                prob = I.request_problem(r)
-                waiting.append((r, prob, footprint_bytes(prob)))
-                nxt += 1
-            # admission in arrival order while memory and slots allow
-            while waiting and len(active) < self.max_active and used + waiting[0][2] <= self.budget:
-                r, prob, fb = waiting.pop(0)
-                sim = M.Simulation.from_problem(prob)
-                arrival = t0 + (r["arrival"] if realtime else 0.0)
-                active.append({"req": r, "sim": sim, "left": prob.steps, "bytes": fb, "arrival": arrival,
-                               "admitted": time.perf_counter(), "n": prob.n_particles, "steps": prob.steps,
-                               "ev": None})
-                used += fb
-            # keep every active problem's stream busy: one chunk in flight each
-            progressed = False
-            for a in active:
-                if a["ev"] is None and a["left"] > 0:
-                    k = min(self.chunk, a["left"])
-                    a["sim"].step_async(k)
-                    a["left"] -= k
+        try:
+            while nxt < len(reqs) or waiting or active:
+                now = time.perf_counter() - t0
+                # arrivals (all at once when not in real time)
+                while nxt < len(reqs) and (not realtime or reqs[nxt]["arrival"] <= now):
+                    r = reqs[nxt]
+                    prob = I.request_problem(r)
+                    if self.tuner is not None:
+                        prob.cfg["tile"] = self.tuner.tile_for(prob)
+                    waiting.append((r, prob, footprint_bytes(prob)))
+                    nxt += 1
+                if ev is not None and not ev.query():
+                    time.sleep(0.0002)
+                    continue
+                if ev is not None:
+                    # a chunk has completed: account it, retire finished members
+                    batch.sync()
+                    ev = None
+                    still = []
+                    for a in active:
+                        a["left"] -= a["running"]
+                        a["running"] = 0
+                        if a["left"] <= 0:
+                            batch.remove(a["sim"])
+                            results.append(_finish(a["sim"], a["req"], a["arrival"], a["admitted"], a["n"],
+                                                   a["steps"]))
+                            a["sim"].close()
+                            used -= a["bytes"]
+                        else:
+                            still.append(a)
+                    active = still
+                # admission in arrival order while memory and slots allow
+                while waiting and len(active) < self.max_active and used + waiting[0][2] <= self.budget:
+                    r, prob, fb = waiting.pop(0)
+                    sim = M.Simulation.from_problem(prob)
+                    batch.add(sim, prob.steps)
+                    arrival = t0 + (r["arrival"] if realtime else 0.0)
+                    active.append({"req": r, "sim": sim, "left": prob.steps, "running": 0, "bytes": fb,
+                                   "arrival": arrival, "admitted": time.perf_counter(), "n": prob.n_particles,
+                                   "steps": prob.steps})
+                    used += fb
+                if active:
+                    k = min(self.chunk, max(a["left"] for a in active))
+                    batch.step_async(k)
+                    for a in active:
+                        a["running"] = k
                     ev = torch.cuda.Event()
-                    ev.record(torch.cuda.ExternalStream(a["sim"].stream))
-                    a["ev"] = ev
-                    progressed = True
-            # collect finished chunks and retire finished problems
-            still = []
-            for a in active:
-                if a["ev"] is not None and a["ev"].query():
-                    a["ev"] = None
-                    if a["left"] == 0:
-                        a["sim"].sync()
-                        results.append(_finish(a["sim"], a["req"], a["arrival"], a["admitted"], a["n"], a["steps"]))
-                        a["sim"].close()
-                        used -= a["bytes"]
-                        continue
-                still.append(a)
-            active = still
-            if not progressed:
-                if not active and waiting and used == 0 and waiting[0][2] > self.budget:
+                    ev.record(torch.cuda.ExternalStream(batch.stream))
+                elif waiting and used == 0 and waiting[0][2] > self.budget:
                     raise RuntimeError("request larger than the HBM budget")
-                time.sleep(0.0002)
+                else:
+                    time.sleep(0.0002)
+        finally:
+            batch.close()
         t1 = time.perf_counter()
         return results, _summary(results, t0, t1)
 
 
-def run_sequential(requests: list[dict], realtime: bool = True) -> tuple[list[Result], dict]:
+def run_sequential(requests: list[dict], realtime: bool = True, tuner=None) -> tuple[list[Result], dict]:
     """One request at a time in arrival order with the same kernels."""
     reqs = sorted(requests, key=lambda r: r["arrival"])
     results = []
@@ -153,6 +168,8 @@ def run_sequential(requests: list[dict], realtime: bool = True) -> tuple[list[Re
             if wait > 0:
                 time.sleep(wait)
         prob = I.request_problem(r)
+        if tuner is not None:
+            prob.cfg["tile"] = tuner.tile_for(prob)
         admitted = time.perf_counter()
         sim = M.Simulation.from_problem(prob)
         sim.step(prob.steps)

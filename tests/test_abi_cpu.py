@@ -45,3 +45,9 @@ def test_null_handles_are_rejected_without_a_device():
     assert L.mpm_step(None, 1, 0.0, 0.0) == 1
     assert L.mpm_create(None, None) == 1
     L.mpm_destroy(None)
+    assert L.mpm_batch_create(None, None) == 1
+    assert L.mpm_batch_add(None, None, 1, 0.0, 0.0) == 1
+    assert L.mpm_batch_remove(None, None) == 1
+    assert L.mpm_batch_step_async(None, 1) == 1
+    assert L.mpm_batch_sync(None) == 1
+    L.mpm_batch_destroy(None)
