@@ -64,7 +64,7 @@ static int geom_init(const oracle_config* c, geom* G)
         G->S[a] = G->per[a] ? c->n[a] : (G->p == 2 ? c->n[a] + 1 : c->n[a]);
         G->N[a] = G->per[a] ? c->n[a] : c->n[a] + 2 * G->p - 1;
         G->g[a] = G->per[a] ? 0 : G->p - 1;
-        static const int def3[3] = {32, 4, 4}, def2[3] = {32, 8, 1};
+        static const int def3[3] = {16, 8, 4}, def2[3] = {32, 8, 1};
         G->T[a] = c->tile[a] > 0 ? c->tile[a] : (c->dim == 3 ? def3[a] : def2[a]);
         G->nt[a] = (G->S[a] + G->T[a] - 1) / G->T[a];
         G->lo[a] = c->origin[a];

@@ -489,7 +489,7 @@ mpm_status make_geom(const mpm_config* c, Geom* G, std::string* why)
         G->S[a] = G->per[a] ? c->n[a] : (G->p == 2 ? c->n[a] + 1 : c->n[a]);
         G->N[a] = G->per[a] ? c->n[a] : c->n[a] + 2 * G->p - 1;
         G->g[a] = G->per[a] ? 0 : G->p - 1;
-        static const int def3[3] = {32, 4, 4}, def2[3] = {32, 8, 1};
+        static const int def3[3] = {16, 8, 4}, def2[3] = {32, 8, 1};
         G->T[a] = c->tile[a] > 0 ? c->tile[a] : (c->dim == 3 ? def3[a] : def2[a]);
         if (G->T[a] > 64 || (G->T[a] & (G->T[a] - 1))) { *why = "tile edges must be powers of two <= 64"; return MPM_EINVAL; }
         while ((1 << G->tsh[a]) < G->T[a]) ++G->tsh[a];

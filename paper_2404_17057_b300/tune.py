@@ -20,7 +20,7 @@ from . import mpm as M
 
 CANDIDATES = {
     2: [(32, 8, 1), (32, 4, 1), (16, 8, 1), (16, 16, 1), (64, 4, 1), (32, 16, 1), (64, 8, 1)],
-    3: [(32, 4, 4), (32, 2, 4), (32, 4, 2), (16, 4, 4), (32, 8, 4), (8, 8, 8), (16, 8, 4)],
+    3: [(16, 8, 4), (16, 4, 8), (8, 8, 8), (32, 4, 4), (16, 4, 4), (8, 16, 4), (32, 8, 2)],
 }
 
 

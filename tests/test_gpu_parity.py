@@ -94,7 +94,7 @@ def decode_spans(cfg, keys):
     """Spans of each key from the tile-major numbering (the ABI's definition)."""
     dim, p = cfg["dim"], cfg["degree"]
     per = [cfg["bc"][2 * a] == "periodic" for a in range(dim)]
-    default = [32, 4, 4] if dim == 3 else [32, 8]
+    default = [16, 8, 4] if dim == 3 else [32, 8]
     T = [cfg["tile"][a] or default[a] for a in range(dim)] + [1] * (3 - dim)
     S = [cfg["n"][a] if per[a] else cfg["n"][a] + (1 if p == 2 else 0) for a in range(dim)]
     nt = [(S[a] + T[a] - 1) // T[a] for a in range(dim)] + [1] * (3 - dim)
