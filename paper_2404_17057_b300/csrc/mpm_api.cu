@@ -216,7 +216,8 @@ struct Impl {
         const size_t W = (size_t)G.Wvol;
         if (kFast) {
             if (kernel == 0) return (1 + 2 * D) * W * sizeof(float);
-            if (kernel == 1) return 16 * W + D * W * sizeof(float) + (kSpanThreads / 32) * D * kStageCap * sizeof(float);
+            if (kernel == 1)
+                return (K2Cfg<D>::kHeadFloats + tile_cs_words(G)) * sizeof(float) + 16 * W + D * W * sizeof(float);
             return (D == 3 ? 24 : 16) * W;
         }
         if (kernel == 0) return (1 + 2 * D) * W * sizeof(A);
@@ -281,9 +282,11 @@ struct Impl {
             if constexpr (kFast) {
                 const FieldPtrs o = g2p_fields(gr);
                 if (G.per[0] | G.per[1] | G.per[2])
-                    k_grid_g2p_span<D, P, true><<<G.ntiles, kSpanThreads, smem(G, 1), st>>>(G, pt, gr, o, cs, s->clk);
+                    k_grid_g2p_span<D, P, true><<<G.ntiles, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, pt, gr, o, cs,
+                                                                                              s->clk);
                 else
-                    k_grid_g2p_span<D, P, false><<<G.ntiles, kSpanThreads, smem(G, 1), st>>>(G, pt, gr, o, cs, s->clk);
+                    k_grid_g2p_span<D, P, false><<<G.ntiles, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, pt, gr, o, cs,
+                                                                                              s->clk);
             } else {
                 k_grid_g2p<D, P, R, A><<<G.ntiles, kThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
             }
@@ -355,8 +358,8 @@ struct Impl {
                 if (per) kb_p2g_span<D, P, true><<<ntl, kP2GThreads, sm, st>>>(d, tl);
                 else kb_p2g_span<D, P, false><<<ntl, kP2GThreads, sm, st>>>(d, tl);
             } else if (stage == 1) {
-                if (per) kb_grid_g2p_span<D, P, true><<<ntl, kSpanThreads, sm, st>>>(d, tl);
-                else kb_grid_g2p_span<D, P, false><<<ntl, kSpanThreads, sm, st>>>(d, tl);
+                if (per) kb_grid_g2p_span<D, P, true><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
+                else kb_grid_g2p_span<D, P, false><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
             } else {
                 kb_g2pd_fast<D, P><<<ntl, 256, sm, st>>>(d, tl);
             }

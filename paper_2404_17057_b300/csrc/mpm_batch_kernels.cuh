@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(kP2GThreads, 6) kb_p2g_span(const BatchProb<fl
 }
 
 template <int D, int P, bool PER>
-__global__ void __launch_bounds__(kSpanThreads, 3) kb_grid_g2p_span(const BatchProb<float, float>* __restrict__ bp,
-                                                                    const TileRef* __restrict__ tl)
+__global__ void __launch_bounds__(K2Cfg<D>::kThreads, 3)
+    kb_grid_g2p_span(const BatchProb<float, float>* __restrict__ bp, const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(float, float)
     grid_g2p_span_tile<D, P, PER>(p.G, p.pt[par], p.gr, p.g2p_out, p.cs[par], p.clk, r.tile);

@@ -15,11 +15,10 @@
 // are factored along the axes (x first, then y, then z).
 #pragma once
 #include "mpm_kernels.cuh"
+#include "mpm_tma.cuh"
 
 namespace mpm {
 
-constexpr int kSpanThreads = 128;   // threads of the span-per-thread kernels
-constexpr int kStageCap = 512;      // particles per warp staged for coalesced stores
 
 template <int P>
 __device__ __forceinline__ void weights1d(float fx, float* w, float* dw)
@@ -425,21 +424,85 @@ __global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, Particles<f
 }
 
 // ----------------------------------------- K2: grid update + G2P + P2G
+//
+// The tile's particles are staged row chunk by row chunk (32 spans, at most
+// kCap particles) into shared memory by bulk copies, double-buffered.  Per
+// chunk, phase (i): one thread per particle gathers A = G2P(f/m) from the
+// window (lanes of a warp mostly share a span, so node records are
+// broadcast), forms V' = V + dt A, stores it (coalesced) and into the stage;
+// phase (ii): warp d (d < dim) owns the momentum field mv2_d: its lanes own
+// the row's spans, sum M V'_d phi over their particles in registers and add
+// the row's sums into the window with plain shared-memory adds.
+template <int D>
+struct K2Cfg {
+    static constexpr int kThreads = 128;
+    static constexpr int kFields = 2 * D + 1;      // x[D], v[D], M
+    static constexpr int kCap = 256;               // particles per chunk
+    static constexpr int kPitch = kCap + 8;        // staged floats per field (16-byte multiple)
+    static constexpr int kStageFloats = 2 * kFields * kPitch;
+    static constexpr int kWeightFloats = 3 * D * kPitch;    // 1D weights of the chunk's particles
+    static constexpr int kHeadFloats = kStageFloats + kWeightFloats + 4;   // + two mbarriers
+};
+
+// Tile cell starts kept in shared memory (Tvol + 1 words, rounded to 4).
+__host__ __device__ inline int tile_cs_words(const Geom& G) { return (G.Tvol + 1 + 3) & ~3; }
+
+// Chunk [lo, hi) of row r of a tile (which ends at re).
+struct RowChunk {
+    int r;
+    uint32_t lo, hi, re;
+    bool valid;
+};
+
+__device__ __forceinline__ RowChunk next_chunk(const uint32_t* tcs, int nrows, RowChunk c, int cap)
+{
+    if (c.valid && c.hi < c.re) {
+        c.lo = c.hi;
+        c.hi = min(c.re, c.lo + (uint32_t)cap);
+        return c;
+    }
+    for (int r = c.r + 1; r < nrows; ++r) {
+        const uint32_t rb = tcs[r << 5], re = tcs[(r << 5) + 32];
+        if (rb < re) return RowChunk{r, rb, min(re, rb + (uint32_t)cap), re, true};
+    }
+    return RowChunk{nrows, 0u, 0u, 0u, false};
+}
+
+// Copies of one chunk of fields x[D], v[D], M, widened to 16-byte boundaries
+// (particle arrays are allocated in multiples of 256 bytes, so the widened
+// end stays inside them).
+template <int D>
+__device__ __forceinline__ void k2_stage(const RowChunk& c, const Particles<float>& pt, float* stage, uint64_t* bar)
+{
+    typedef K2Cfg<D> C;
+    const uint32_t a = c.lo & ~3u, b = (c.hi + 3u) & ~3u;
+    const uint32_t bytes = (b - a) * 4u;
+    mbar_arrive_expect_tx(bar, bytes * C::kFields);
+#pragma unroll
+    for (int f = 0; f < C::kFields; ++f) {
+        const float* src = f < D ? pt.x[f] : (f < 2 * D ? pt.v[f - D] : pt.M);
+        bulk_g2s(stage + f * C::kPitch, src + a, bytes, bar);
+    }
+}
 
 template <int D, int P, bool PER>
 __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particles<float>& pt,
                                                    const Grid<float, float>& gr, const FieldPtrs& out,
                                                    const uint32_t* __restrict__ cs, Clock* clk, const int tile)
 {
+    typedef K2Cfg<D> C;
     if (!clk->active) return;
     const int64_t kb = (int64_t)tile * G.Tvol;
     if (cs[kb] == cs[kb + G.Tvol]) return;
     extern __shared__ __align__(16) float sm[];
     constexpr int NS = P + 1, NYZ = (D == 3) ? NS * NS : NS, NN = NYZ * NS;
     const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
-    float4* sA = reinterpret_cast<float4*>(sm);              // W records: f/m after BC
-    float* s2 = sm + 4 * W;                                   // D x W: momentum P2G
-    float* stage = s2 + D * W;                                // per warp: D x kStageCap
+    float* stage = sm;
+    float* sw = sm + C::kStageFloats;          // [axis][node][particle] weights of the current chunk
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + C::kStageFloats + C::kWeightFloats);
+    uint32_t* tcs = reinterpret_cast<uint32_t*>(sm + C::kHeadFloats);
+    float4* sA = reinterpret_cast<float4*>(sm + C::kHeadFloats + tile_cs_words(G));   // W records: f/m after BC
+    float* s2 = reinterpret_cast<float*>(sA + W);                                       // D x W: momentum P2G
     int so[3];
     tile_origin(G, tile, so);
     const float dt = (float)clk->dt_cur;
@@ -458,60 +521,67 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
 #pragma unroll
         for (int a = 0; a < D; ++a) s2[a * W + i] = 0.f;
     }
+    for (int i = threadIdx.x; i <= G.Tvol; i += blockDim.x) tcs[i] = cs[kb + i];
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_init_fence();
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* wst = stage + warp * D * kStageCap;
-    float vmax = 0.f;
-    int err = 0;
-    const float ih = (float)G.inv_h;
-    float lo[3], nper[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        lo[a] = (float)G.lo[a];
-        nper[a] = G.per[a] ? (float)G.n[a] : 3.0e38f;
-    }
-    // a warp covers 32 consecutive spans per round; their particles are one range
-    for (int s0 = warp * 32; s0 < G.Tvol; s0 += blockDim.x) {
-        const int s = s0 + lane;
-        const bool has = s < G.Tvol;
-        const uint32_t rb = cs[kb + s0], re = cs[kb + min(s0 + 32, G.Tvol)];
-        const bool staged = (re - rb) <= (uint32_t)kStageCap;
-        const uint32_t b = has ? cs[kb + s] : 0u, e = has ? cs[kb + s + 1] : 0u;
-        // 3D: r0 = {mv2_x, mv2_y}, r1 = mv2_z; 2D: r0 = {mv2_x, mv2_y}
-        float2 r0[NN];
-        float r1[D == 3 ? NN : 1];
-#pragma unroll
-        for (int i = 0; i < NN; ++i) {
-            r0[i] = f2(0.f, 0.f);
-            if (D == 3) r1[i] = 0.f;
+    const int nrows = G.Tvol >> 5;
+    const int tseg = G.T[0] < 32 ? G.T[0] : 32;
+    const int lxw = lane & (tseg - 1);
+    const bool producer = threadIdx.x == 0;
+    RowChunk c = next_chunk(tcs, nrows, RowChunk{-1, 0u, 0u, 0u, false}, C::kCap);
+    RowChunk pc = c;
+    int issued = 0;
+    if (producer) {
+        for (int s = 0; s < 2 && pc.valid; ++s) {
+            k2_stage<D>(pc, pt, stage + s * C::kFields * C::kPitch, bar + s);
+            pc = next_chunk(tcs, nrows, pc, C::kCap);
+            ++issued;
         }
-        const int lx = s & (G.T[0] - 1);
-        const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
-        const int lz = s >> (G.tsh[0] + G.tsh[1]);
-        const int base = (lz * W1 + ly) * W0 + lx;
-        const float cb0 = (float)(so[0] + lx - (P == 2 ? 1 : 0));
-        const float cb1 = (float)(so[1] + ly - (P == 2 ? 1 : 0));
-        const float cb2 = (float)(so[2] + lz - (P == 2 ? 1 : 0));
-        PState<D> nx;
-        if (b != e) load_state<D, false>(pt, b, nx);
-        for (uint32_t k = b; k < e; ++k) {
-            const PState<D> cur = nx;
-            if (k + 1 < e) load_state<D, false>(pt, k + 1, nx);
-            float w[3][3], dw[3][3];
-            bool ok = axis_known<P, PER>(cur.x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
-            ok &= axis_known<P, PER>(cur.x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
-            if (D == 3) ok &= axis_known<P, PER>(cur.x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
+    }
+    // phase (ii) state of this lane (warps d < D)
+    float acc[NN];
+    uint32_t sb = 0, se = 0;
+    int base = 0;
+    float vmax = 0.f;
+    int err = 0, fail = 0, i = 0;
+    for (; c.valid; ++i) {
+        const int st = i & 1;
+        if (!mbar_wait(bar + st, (uint32_t)(i >> 1) & 1u)) fail = 1;
+        float* sg = stage + st * C::kFields * C::kPitch;
+        const uint32_t a0 = c.lo & ~3u;
+        // (i) one thread per particle: V' = V + dt G2P(f/m)
+        for (uint32_t k = c.lo + threadIdx.x; k < c.hi; k += blockDim.x) {
+            const uint32_t j = k - a0;
+            float x[3], w[3][3], dw[3][3];
+            int l[3] = {0, 0, 0};
+            bool ok = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                x[a] = sg[a * C::kPitch + j];
+                float xi;
+                const int cc = span_of<float, P>(G, a, x[a], xi);
+                weights1d<P>(__fsub_rn(xi, (float)(cc - (P == 2 ? 1 : 0))), w[a], dw[a]);
+                l[a] = wrap_span(G, a, cc) - so[a];
+                ok = ok && l[a] >= 0 && l[a] < G.T[a];
+            }
+            // weights for the momentum P2G of phase (ii) (zero: no contribution)
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int q = 0; q < NS; ++q) sw[(a * 3 + q) * C::kPitch + j] = ok ? w[a][q] : 0.f;
             if (!ok) { err = 1; continue; }
-            float yz[NYZ];
-#pragma unroll
-            for (int c = 0; c < (D == 3 ? NS : 1); ++c)
-#pragma unroll
-                for (int bb = 0; bb < NS; ++bb) yz[c * NS + bb] = D == 3 ? w[1][bb] * w[2][c] : w[1][bb];
-            // A = G2P(f / m)
+            const int nb = (l[2] * W1 + l[1]) * W0 + l[0];
             float A0 = 0.f, A1 = 0.f, A2 = 0.f;
 #pragma unroll
-            for (int j = 0; j < NYZ; ++j) {
-                const int row = base + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0;
+            for (int jj = 0; jj < NYZ; ++jj) {
+                const int bb = D == 3 ? jj % NS : jj, cz = D == 3 ? jj / NS : 0;
+                const float yz = D == 3 ? w[1][bb] * w[2][cz] : w[1][bb];
+                const int row = nb + (cz * W1 + bb) * W0;
                 float x0 = 0.f, x1 = 0.f, x2 = 0.f;
 #pragma unroll
                 for (int a = 0; a < NS; ++a) {
@@ -520,81 +590,97 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
                     x1 = fmaf(w[0][a], q.y, x1);
                     x2 = fmaf(w[0][a], q.z, x2);
                 }
-                A0 = fmaf(yz[j], x0, A0);
-                A1 = fmaf(yz[j], x1, A1);
-                A2 = fmaf(yz[j], x2, A2);
+                A0 = fmaf(yz, x0, A0);
+                A1 = fmaf(yz, x1, A1);
+                A2 = fmaf(yz, x2, A2);
             }
-            const float vn0 = fmaf(dt, A0, cur.v[0]);
-            const float vn1 = fmaf(dt, A1, cur.v[1]);
-            const float vn2 = D == 3 ? fmaf(dt, A2, cur.v[2]) : 0.f;
-            vmax = fmaxf(vmax, fmaf(vn2, vn2, fmaf(vn1, vn1, vn0 * vn0)));
-            if (staged) {
-                wst[k - rb] = vn0;
-                wst[kStageCap + k - rb] = vn1;
-                if (D == 3) wst[2 * kStageCap + k - rb] = vn2;
-            } else {
-                pt.v[0][k] = vn0;
-                pt.v[1][k] = vn1;
-                if (D == 3) pt.v[D - 1][k] = vn2;
+            const float A[3] = {A0, A1, A2};
+            float v2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float vn = fmaf(dt, A[a], sg[(D + a) * C::kPitch + j]);
+                sg[(D + a) * C::kPitch + j] = vn;
+                pt.v[a][k] = vn;
+                v2 = fmaf(vn, vn, v2);
             }
-            const float M = cur.M;
-            float2 cm[NS];
-            float cz[NS];
+            vmax = fmaxf(vmax, v2);
+        }
+        // V' was written into the stage by generic stores; order them before
+        // the bulk copy that will later refill this stage
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        // (ii) warp d: P2G of M V'_d over the row's spans, one span per lane
+        if (warp < D) {
+            if (c.lo == tcs[c.r << 5]) {
+                const int s = (c.r << 5) + lane;
+                sb = tcs[s];
+                se = tcs[s + 1];
+                const int lx = s & (G.T[0] - 1);
+                const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
+                const int lz = s >> (G.tsh[0] + G.tsh[1]);
+                base = (lz * W1 + ly) * W0 + lx;
 #pragma unroll
-            for (int a = 0; a < NS; ++a) {
-                cm[a] = f2(M * vn0 * w[0][a], M * vn1 * w[0][a]);
-                cz[a] = M * vn2 * w[0][a];
+                for (int q = 0; q < NN; ++q) acc[q] = 0.f;
             }
+            const uint32_t kb0 = max(sb, c.lo), kb1 = min(se, c.hi);
+            const uint32_t cnt = kb1 > kb0 ? kb1 - kb0 : 0u;
+            const uint32_t rot = cnt ? ((uint32_t)lane >> 2) % cnt : 0u;
+            for (uint32_t ii = 0; ii < cnt; ++ii) {
+                const uint32_t kk = ii + rot;
+                const uint32_t j = kb0 - a0 + (kk >= cnt ? kk - cnt : kk);
+                float w[3][3];
 #pragma unroll
-            for (int j = 0; j < NYZ; ++j) {
-                const float2 yy = f2(yz[j], yz[j]);
+                for (int a = 0; a < D; ++a)
 #pragma unroll
-                for (int a = 0; a < NS; ++a) {
-                    r0[j * NS + a] = __ffma2_rn(cm[a], yy, r0[j * NS + a]);
-                    if (D == 3) r1[j * NS + a] = fmaf(cz[a], yz[j], r1[j * NS + a]);
+                    for (int q = 0; q < NS; ++q) w[a][q] = sw[(a * 3 + q) * C::kPitch + j];
+                const float mv = sg[2 * D * C::kPitch + j] * sg[(D + warp) * C::kPitch + j];
+                float cm[NS];
+#pragma unroll
+                for (int a = 0; a < NS; ++a) cm[a] = mv * w[0][a];
+#pragma unroll
+                for (int jj = 0; jj < NYZ; ++jj) {
+                    const float yz = D == 3 ? w[1][jj % NS] * w[2][jj / NS] : w[1][jj];
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) acc[jj * NS + a] = fmaf(cm[a], yz, acc[jj * NS + a]);
+                }
+            }
+            if (c.hi == c.re) {
+                // the row is complete: add its sums (x-neighbours summed first)
+#pragma unroll
+                for (int jj = 0; jj < NYZ; ++jj) {
+                    const int row = base - lxw + ((D == 3 ? jj / NS : 0) * W1 + (D == 3 ? jj % NS : jj)) * W0;
+                    float v[NS];
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) v[a] = acc[jj * NS + a];
+                    xrow_rmw<NS>(s2 + warp * W + row, v, lxw, tseg);
                 }
             }
         }
-        if (__any_sync(0xffffffffu, b != e)) {
-            // all lanes add their rows (zeros for empty spans), x-neighbours summed first
-            const int tseg = G.T[0] < 32 ? G.T[0] : 32;
-            const int lxw = lane & (tseg - 1);
-#pragma unroll
-            for (int j = 0; j < NYZ; ++j) {
-                const int row = base - lxw + ((D == 3 ? j / NS : 0) * W1 + (D == 3 ? j % NS : j)) * W0;
-                float v[NS];
-#pragma unroll
-                for (int a = 0; a < NS; ++a) v[a] = r0[j * NS + a].x;
-                xrow_add<NS>(s2 + row, v, lxw, tseg);
-#pragma unroll
-                for (int a = 0; a < NS; ++a) v[a] = r0[j * NS + a].y;
-                xrow_add<NS>(s2 + W + row, v, lxw, tseg);
-                if (D == 3) {
-#pragma unroll
-                    for (int a = 0; a < NS; ++a) v[a] = r1[j * NS + a];
-                    xrow_add<NS>(s2 + 2 * W + row, v, lxw, tseg);
-                }
-            }
+        // the stage is free once every warp is done with it
+        if (block_bar_or(fail)) { fail = 1; break; }
+        if (producer && pc.valid) {
+            k2_stage<D>(pc, pt, stage + st * C::kFields * C::kPitch, bar + st);
+            pc = next_chunk(tcs, nrows, pc, C::kCap);
+            ++issued;
         }
-        __syncwarp();
-        if (staged) {
-            for (uint32_t i = lane; i < re - rb; i += 32)
-#pragma unroll
-                for (int d = 0; d < D; ++d) pt.v[d][rb + i] = wst[d * kStageCap + i];
-        }
-        __syncwarp();
+        c = next_chunk(tcs, nrows, c, C::kCap);
+    }
+    if (fail && producer) {
+        // drain the copies still in flight before the block's memory is reused
+        for (int j = i; j < issued; ++j) mbar_wait(bar + (j & 1), (uint32_t)(j >> 1) & 1u);
     }
     vmax = warp_max(vmax);
     if (lane == 0) atomic_max_nonneg(&clk->vmax_bits, (double)sqrtf(vmax));
-    if (err) atomicOr(&clk->err, ERR_TILE);
+    if (err || fail) atomicOr(&clk->err, (err ? ERR_TILE : 0) | (fail ? ERR_TIMEOUT : 0));
     __syncthreads();
+    if (fail) return;
     flush_window<D, P>(G, so, s2, D, out);
 }
 
 template <int D, int P, bool PER>
-__global__ void __launch_bounds__(kSpanThreads, 3) k_grid_g2p_span(Geom G, Particles<float> pt,
-                                                                   Grid<float, float> gr, FieldPtrs out,
-                                                                   const uint32_t* __restrict__ cs, Clock* clk)
+__global__ void __launch_bounds__(K2Cfg<D>::kThreads, 4) k_grid_g2p_span(Geom G, Particles<float> pt,
+                                                                         Grid<float, float> gr, FieldPtrs out,
+                                                                         const uint32_t* __restrict__ cs, Clock* clk)
 {
     grid_g2p_span_tile<D, P, PER>(G, pt, gr, out, cs, clk, blockIdx.x);
 }
