@@ -294,7 +294,7 @@ struct Impl {
         }
         if (which & 4) {
             if constexpr (kFast)
-                k_g2pd_fast<D, P><<<G.ntiles, 256, smem(G, 2), st>>>(G, pt, gr, cs, s->clk, ro);
+                k_g2pd_fast<D, P><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, pt, gr, cs, s->clk, ro);
             else
                 k_g2pd<D, P, R, A><<<G.ntiles, kThreads, smem(G, 2), st>>>(G, pt, gr, cs, s->clk, ro);
             s->launches += 1;
@@ -361,7 +361,7 @@ struct Impl {
                 if (per) kb_grid_g2p_span<D, P, true><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
                 else kb_grid_g2p_span<D, P, false><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
             } else {
-                kb_g2pd_fast<D, P><<<ntl, 256, sm, st>>>(d, tl);
+                kb_g2pd_fast<D, P><<<ntl, kG2PDThreads, sm, st>>>(d, tl);
             }
         } else {
             if (stage == 0) kb_p2g<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);

@@ -687,6 +687,8 @@ __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 4) k_grid_g2p_span(Geom G,
 
 // ------------------------------- K3: G2PD + particle update + move + key
 
+constexpr int kG2PDThreads = 128;
+
 template <int D, int P>
 __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<float>& pt, const Grid<float, float>& gr,
                                                const uint32_t* __restrict__ cs, Clock* clk, const Reorder& ro,
@@ -930,7 +932,7 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
 }
 
 template <int D, int P>
-__global__ void __launch_bounds__(256) k_g2pd_fast(Geom G, Particles<float> pt, Grid<float, float> gr,
+__global__ void __launch_bounds__(kG2PDThreads) k_g2pd_fast(Geom G, Particles<float> pt, Grid<float, float> gr,
                                                    const uint32_t* __restrict__ cs, Clock* clk, Reorder ro)
 {
     g2pd_fast_tile<D, P>(G, pt, gr, cs, clk, ro, blockIdx.x);

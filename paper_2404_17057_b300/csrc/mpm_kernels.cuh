@@ -111,9 +111,7 @@ __device__ __forceinline__ int ring_bit(const Geom& G, uint32_t t, const int old
 __device__ __forceinline__ uint32_t record_key(const Geom& G, const Reorder& ro, Clock* clk, uint32_t key,
                                                bool recycled, uint32_t k, int tile, const int old[3], int& err)
 {
-    const unsigned m = __activemask();
-    const unsigned peers = __match_any_sync(m, key);
-    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&ro.count[key], (uint32_t)__popc(peers));
+    atomicAdd(&ro.count[key], 1u);
     if (recycled) {
         const unsigned slot = atomicAdd(&clk->nfar, 1u);
         if (slot < ro.far_cap) ro.far[slot] = make_uint2(key, k);
