@@ -35,16 +35,18 @@ __host__ inline size_t reorder_smem(const Geom& G)
     return ((kReorderWarps + 2) * T + kReorderCap + 4 * nr + 2 + kReorderWarps) * 4 + kReorderCap * 2;
 }
 
+// The recycle count (gen) is read only by recycling, so problems without an
+// inflow face do not move it.
 template <class R>
 __device__ __forceinline__ void copy_particle(const Particles<R>& in, const Particles<R>& out, int D, uint32_t q,
-                                              uint32_t j)
+                                              uint32_t j, bool with_gen)
 {
     R xv[6];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         if (a < D) { xv[a] = in.x[a][q]; xv[3 + a] = in.v[a][q]; }
     const R M = in.M[q], rho = in.rho[q], E = in.E[q], Q = in.Q[q];
-    const uint32_t id = in.id[q], gen = in.gen[q];
+    const uint32_t id = in.id[q], gen = with_gen ? in.gen[q] : 0u;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         if (a < D) { out.x[a][j] = xv[a]; out.v[a][j] = xv[3 + a]; }
@@ -53,14 +55,14 @@ __device__ __forceinline__ void copy_particle(const Particles<R>& in, const Part
     out.E[j] = E;
     out.Q[j] = Q;
     out.id[j] = id;
-    out.gen[j] = gen;
+    if (with_gen) out.gen[j] = gen;
 }
 
 // Copy kB particles per lane, q[u] -> j[u] where ok[u]: all loads first, so
 // that 12 kB independent loads per lane are in flight.
 template <int kB, class R>
 __device__ __forceinline__ void copy_batch(const Particles<R>& in, const Particles<R>& out, int D, const uint32_t* q,
-                                           const uint32_t* j, const bool* ok)
+                                           const uint32_t* j, const bool* ok, bool with_gen)
 {
     R xv[kB][6], M[kB], rho[kB], E[kB], Q[kB];
     uint32_t id[kB], gen[kB];
@@ -75,7 +77,7 @@ __device__ __forceinline__ void copy_batch(const Particles<R>& in, const Particl
         E[u] = in.E[q[u]];
         Q[u] = in.Q[q[u]];
         id[u] = in.id[q[u]];
-        gen[u] = in.gen[q[u]];
+        gen[u] = with_gen ? in.gen[q[u]] : 0u;
     }
 #pragma unroll
     for (int u = 0; u < kB; ++u) {
@@ -88,7 +90,7 @@ __device__ __forceinline__ void copy_batch(const Particles<R>& in, const Particl
         out.E[j[u]] = E[u];
         out.Q[j[u]] = Q[u];
         out.id[j[u]] = id[u];
-        out.gen[j[u]] = gen[u];
+        if (with_gen) out.gen[j[u]] = gen[u];
     }
 }
 
@@ -142,7 +144,7 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
     if (!clk->active) {
         // no step was taken: same order, same cell starts
         const uint32_t b = cs_old[K0], e = cs_old[K0 + Tvol];
-        for (uint32_t j = b + tid; j < e; j += kReorderThreads) copy_particle(in, out, D, j, j);
+        for (uint32_t j = b + tid; j < e; j += kReorderThreads) copy_particle(in, out, D, j, j, G.inflow_face >= 0);
         const int last = (t == G.ntiles - 1) ? 1 : 0;
         for (int k = tid; k < Tvol + last; k += kReorderThreads) cs_new[K0 + k] = cs_old[K0 + k];
         return;
@@ -341,7 +343,7 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
                 if (valid && lane == leader) wc[kl] = bv + __popc(peers);
                 __syncwarp();
             }
-            copy_batch<kB>(in, out, D, qv, pv, okv);
+            copy_batch<kB>(in, out, D, qv, pv, okv, G.inflow_face >= 0);
         }
         __syncthreads();
         for (int k = tid; k < kReorderWarps * Tvol; k += kReorderThreads) cnt[k] = 0u;
@@ -367,7 +369,7 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
             while (j > fb && in.id[perm[j - 1]] > vid) { perm[j] = perm[j - 1]; --j; }
             perm[j] = v;
         }
-        for (uint32_t i = fb; i < fe; ++i) copy_particle(in, out, D, perm[i], i);
+        for (uint32_t i = fb; i < fe; ++i) copy_particle(in, out, D, perm[i], i, true);
     }
     if (err) atomicOr(&clk->err, err);
 }
