@@ -105,12 +105,22 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi takes a moment to start: let its first sample arrive,
+            # then keep only samples taken from the start of the timed region
+            t0 = time.perf_counter()
+            while not self.rows and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.01)
+            self.first = len(self.rows)
         except Exception:
             self.proc = None
+
+    def mark(self):
+        """The timed region starts now."""
+        self.first = len(self.rows)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -123,6 +133,7 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        self.rows = self.rows[getattr(self, "first", 0):]
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
         try:
             sm = [float(r[1]) for r in self.rows if len(r) >= 9]
@@ -305,6 +316,23 @@ def sweep(args):
     return out
 
 
+def max_over_ranks(ms: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time (the job ends when its last rank does)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_p: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job particle-steps/s: every rank advances its own replica of
+    n_p particles for `steps` steps (weak scaling); ms is the slowest rank's
+    time."""
+    return n_p * steps * world / (ms / 1e3)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -331,13 +359,13 @@ def main():
     sim = M.Simulation.from_problem(p)
     st = torch.cuda.ExternalStream(sim.stream)
     sim.step(args.warmup)
-    sim.profile(True)
-    sim.profile_read(reset=True)
     clocks = ClockSampler(local)
+    clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark()
+    # the timed region: the production path (one CUDA graph per step)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)
@@ -346,21 +374,25 @@ def main():
     sim.sync()
     torch.cuda.synchronize()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        dist.barrier()
+    # per-phase device times: the same steps again with events between phases
+    prof_steps = max(1, min(args.steps, 10))
+    sim.profile(True)
+    sim.profile_read(reset=True)
+    sim.step(prof_steps)
     phase_ms, counts = sim.profile_read(reset=True)
+    sim.profile(False)
     sizes = sim.sizes()
     n_n = sizes["nodes"]
-    value = n_p * args.steps * world / (ms / 1e3)
+    value = job_value(n_p, args.steps, world, ms)
 
     dim = p.cfg["dim"]
     s = 8 if args.precision == "fp64" else 4
     alg = algorithmic_bytes(dim, s, n_p, n_n)
     names = ["p2g", "grid_g2p", "g2pd"]
-    per_launch_ms = {nme: phase_ms[i] / args.steps for i, nme in enumerate(names)}
+    per_launch_ms = {nme: phase_ms[i] / prof_steps for i, nme in enumerate(names)}
     dom = max(names, key=lambda k: per_launch_ms[k])
     hbm, which = peaks()
     ach = alg[dom] / (per_launch_ms[dom] / 1e3) / 1e9
@@ -389,8 +421,8 @@ def main():
                      "k1_k2_k3_gbs": k123_gbs, "k1_k2_k3_frac": k123_gbs / hbm,
                      "k1_k2_k3_frac_nominal_7.7TB": k123_gbs / NOMINAL_HBM},
         "phase_ms_per_step": {"p2g": per_launch_ms["p2g"], "grid_g2p": per_launch_ms["grid_g2p"],
-                              "g2pd": per_launch_ms["g2pd"], "time_advance": phase_ms[3] / args.steps,
-                              "reorder": phase_ms[4] / args.steps},
+                              "g2pd": per_launch_ms["g2pd"], "time_advance": phase_ms[3] / prof_steps,
+                              "reorder": phase_ms[4] / prof_steps, "profiled_steps": prof_steps},
         "algorithmic_bytes": alg,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": ck,
