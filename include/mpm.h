@@ -215,9 +215,11 @@ mpm_status mpm_sort_keys_static(const uint32_t* keys, int64_t n, int64_t nkeys, 
  *   mpm_batch_step_async  queue nsteps steps of every member (a member whose
  *                     step budget or t_end is reached idles).  Changing the
  *                     members re-records the graph at the next call.
- *   mpm_batch_sync    wait for the batch's work; a member whose kernels
- *                     raised an error is poisoned and the first such status
- *                     is returned.
+ *   mpm_batch_sync    wait for the batch's work and return the status of
+ *                     the first member whose kernels raised an error (its
+ *                     further batched steps do nothing); that member reports
+ *                     its own status at its first call after it leaves the
+ *                     batch, and is poisoned from then on.
  *   mpm_batch_destroy removes all members and releases the batch.
  * Members are grouped by kernel variant (dimension, degree, precision,
  * periodicity); each group's stages are single launches. */

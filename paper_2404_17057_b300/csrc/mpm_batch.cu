@@ -354,19 +354,15 @@ mpm_status mpm_batch_sync(mpm_batch* b)
         for (mpm_sim* s : b->members) s->poisoned = true;
         return bfail(b, MPM_ECUDA, "synchronize");
     }
+    // a failed member's error bits stay in its clock: it idles in the batch,
+    // and its own first call after leaving reports the status and poisons it
     mpm_status first = MPM_OK;
     for (size_t i = 0; i < b->members.size(); ++i) {
         const int e = c[i].err;
-        if (!e) continue;
-        mpm_sim* s = b->members[i];
-        s->poisoned = true;
-        mpm_status st = (e & ERR_CFL) ? MPM_ECFL : (e & ERR_NONFINITE) ? MPM_ENONFINITE
-                      : (e & ERR_TIMEOUT) ? MPM_ETIMEOUT : MPM_ESTATE;
-        s->err = "error raised in a batched step";
-        if (first == MPM_OK) {
-            first = st;
-            b->err = "a member raised an error in a batched step";
-        }
+        if (!e || first != MPM_OK) continue;
+        first = (e & ERR_CFL) ? MPM_ECFL : (e & ERR_NONFINITE) ? MPM_ENONFINITE
+              : (e & ERR_TIMEOUT) ? MPM_ETIMEOUT : MPM_ESTATE;
+        b->err = "member " + std::to_string(i) + " raised an error in a batched step";
     }
     return first;
 }

@@ -261,4 +261,24 @@ def request_problem(req: dict) -> Problem:
         p = cylinder(nx=n, ny=n // 2, radius=req["radius"], mach=req["mach"], seed=req["seed"],
                      precision=req["precision"], steps=req["steps"])
     p.steps = int(req["steps"])
+    if "cfl" in req:
+        p.cfg["cfl"] = float(req["cfl"])
+    if req["precision"] == "fp32_fixed64":
+        p.cfg["fixed_unit"] = normalised_fixed_units(p)
     return p
+
+
+def normalised_fixed_units(p) -> list[float]:
+    """Fixed-point units scaled to the problem (the normalised reading of the
+    'scale 2^-32 per unit' option): mass unit = mean particle mass, momentum
+    unit = mass unit x (|v| + c) of the faster of the two states, force unit =
+    momentum unit / the first CFL step.  A contribution of one particle then
+    spans about 2^32 quanta, whatever the resolution."""
+    cfg = p.cfg
+    g = float(cfg.get("gamma", 1.4))
+    um = float(np.mean(p.mass))
+    c = np.sqrt(np.maximum(g * (g - 1.0) * p.e, 0.0))
+    s = float(np.max(np.sqrt((p.v ** 2).sum(axis=0)) + c))
+    umom = um * s
+    dt0 = float(cfg.get("cfl", 0.4)) * float(cfg["h"]) / s
+    return [um, umom, umom / dt0]

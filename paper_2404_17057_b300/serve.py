@@ -54,9 +54,10 @@ class Result:
     done: float
     particles: int
     steps: int
-    rho: np.ndarray
-    ids: np.ndarray
-    conservation: np.ndarray
+    rho: np.ndarray | None
+    ids: np.ndarray | None
+    conservation: np.ndarray | None
+    error: str = ""
 
     @property
     def latency(self) -> float:
@@ -64,11 +65,17 @@ class Result:
 
 
 def _summary(results: list[Result], t0: float, t1: float) -> dict:
-    lat = np.array([r.latency for r in results])
-    ps = sum(r.particles * r.steps for r in results)
-    return {"solves": len(results), "seconds": t1 - t0, "solves_per_s": len(results) / (t1 - t0),
-            "particle_steps_per_s": ps / (t1 - t0), "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean())}
+    ok = [r for r in results if not r.error]
+    lat = np.array([r.latency for r in ok]) if ok else np.zeros(1)
+    ps = sum(r.particles * r.steps for r in ok)
+    return {"solves": len(ok), "failed": len(results) - len(ok), "seconds": t1 - t0,
+            "solves_per_s": len(ok) / (t1 - t0), "particle_steps_per_s": ps / (t1 - t0),
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "errors": sorted({r.error for r in results if r.error})}
+
+
+def _failed(req, arrival, admitted, n, steps, err: str) -> Result:
+    return Result(req["id"], arrival, admitted, time.perf_counter(), n, steps, None, None, None, err)
 
 
 def _finish(sim, req, arrival, admitted, n, steps) -> Result:
@@ -115,8 +122,12 @@ class Server:
                     continue
                 if ev is not None:
                     # a chunk has completed: account it, retire finished members
-                    batch.sync()
                     ev = None
+                    try:
+                        batch.sync()
+                    except M.MPMError:
+                        active = self._drop_failed(batch, active, results)
+                        used = sum(a["bytes"] for a in active)
                     still = []
                     for a in active:
                         a["left"] -= a["running"]
@@ -156,6 +167,28 @@ class Server:
         t1 = time.perf_counter()
         return results, _summary(results, t0, t1)
 
+    @staticmethod
+    def _drop_failed(batch, active, results):
+        """A member raised an error (its state is then poisoned): take every
+        member out, retire the failed ones with their error, put the others
+        back with the steps they have left."""
+        keep = []
+        for a in active:
+            batch.remove(a["sim"])
+            try:
+                a["sim"].sync()
+            except M.MPMError as e:
+                results.append(_failed(a["req"], a["arrival"], a["admitted"], a["n"], a["steps"], e.status))
+                a["sim"].close()
+                continue
+            keep.append(a)
+        for a in keep:
+            # budget after the chunk that has just completed (the caller then
+            # accounts that chunk); a finished member is retired before any
+            # further step, so a budget of one is never used
+            batch.add(a["sim"], max(a["left"] - a["running"], 1))
+        return keep
+
 
 def run_sequential(requests: list[dict], realtime: bool = True, tuner=None) -> tuple[list[Result], dict]:
     """One request at a time in arrival order with the same kernels."""
@@ -172,9 +205,12 @@ def run_sequential(requests: list[dict], realtime: bool = True, tuner=None) -> t
             prob.cfg["tile"] = tuner.tile_for(prob)
         admitted = time.perf_counter()
         sim = M.Simulation.from_problem(prob)
-        sim.step(prob.steps)
         arrival = t0 + (r["arrival"] if realtime else 0.0)
-        results.append(_finish(sim, r, arrival, admitted, prob.n_particles, prob.steps))
+        try:
+            sim.step(prob.steps)
+            results.append(_finish(sim, r, arrival, admitted, prob.n_particles, prob.steps))
+        except M.MPMError as e:
+            results.append(_failed(r, arrival, admitted, prob.n_particles, prob.steps, e.status))
         sim.close()
     t1 = time.perf_counter()
     return results, _summary(results, t0, t1)

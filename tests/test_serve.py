@@ -41,3 +41,34 @@ def test_mix_equals_alone_bit_for_bit():
         assert np.array_equal(r.rho[np.argsort(r.ids)], b.rho[np.argsort(b.ids)])
         assert np.array_equal(r.conservation, b.conservation)
     assert stats["p99_s"] >= stats["p50_s"] > 0
+
+
+@pytest.mark.gpu
+def test_a_failing_request_is_retired_and_the_others_finish():
+    """A request whose time step violates the method's CFL rule (one span per
+    step) fails with MPM_ECFL in the mix; the server retires it with that
+    error and the other requests still equal their solo runs."""
+    pytest.importorskip("torch")
+    from paper_2404_17057_b300 import serve as S
+    reqs = I.serving_stream(count=4, seed=11, steps=30, side_lo=64, side_hi=128)
+    reqs[1] = dict(reqs[1], cfl=5.0)
+    mixed, stats = S.Server(chunk=7).run(reqs, realtime=False)
+    alone, _ = S.run_sequential(reqs, realtime=False)
+    m = {r.rid: r for r in mixed}
+    a = {r.rid: r for r in alone}
+    assert m[reqs[1]["id"]].error == "MPM_ECFL" == a[reqs[1]["id"]].error
+    assert stats["failed"] == 1 and stats["solves"] == 3
+    for r in reqs:
+        if r["id"] == reqs[1]["id"]:
+            continue
+        x, y = m[r["id"]], a[r["id"]]
+        assert not x.error and np.array_equal(x.rho[np.argsort(x.ids)], y.rho[np.argsort(y.ids)])
+
+
+def test_serving_problems_use_normalised_fixed_point_units():
+    reqs = I.serving_stream(count=6, seed=3, steps=10, side_lo=64, side_hi=128)
+    for r in reqs:
+        p = I.request_problem(r)
+        um, umom, uf = p.cfg["fixed_unit"]
+        assert um == pytest.approx(float(np.mean(p.mass)))
+        assert umom > um > 0 and uf > umom
