@@ -120,3 +120,24 @@ def test_cylinder_1024_full_size_sampled():
            (1.3, 0.5 * h)]
     samples = [int(np.argmin(((p.x - np.array(q)[:, None]) ** 2).sum(axis=0))) for q in pts]
     check(p, 1e-4, samples)
+
+
+def test_blast_front_follows_sedov_taylor_on_the_gpu():
+    """The C3 physics of the FP32 GPU path on its own: a 64^3 blast's shock
+    front is within 5% of the Sedov-Taylor radius xi0 (E t^2/rho)^(1/5) at
+    t = 0.02..0.04 and grows as t^(2/5) (same measure as the oracle pin)."""
+    from test_oracle_pins import _blast_front, _gold
+    g = _gold("sedov_taylor.txt")
+    xi0, ex = g["xi0_gamma_1_4"][0], g["exponent"][0]
+    n = 64
+    p = I.blast(n=n, radius_cells=1.5)
+    s = M.Simulation.from_problem(p)
+    fronts = {}
+    for t in (0.02, 0.03, 0.04):
+        s.step(100000, t_end=t)
+        rf, peak = _blast_front(s, n)
+        fronts[t] = rf
+        assert abs(rf / (xi0 * t ** ex) - 1.0) < 0.05, (t, rf)
+        assert 1.5 < peak < 6.0
+    s.close()
+    assert abs(fronts[0.04] / fronts[0.02] / 2.0 ** ex - 1.0) < 0.04

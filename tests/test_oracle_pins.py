@@ -458,3 +458,48 @@ def test_shock_tube_without_viscosity_oscillates_more():
         r = rho[o].reshape(-1, 8).mean(axis=1)      # average over one column of particles
         return np.abs(np.diff(r)).sum()
     assert tv(0.0, 0.0) > 1.2 * tv(1.0, 1.0)
+
+
+# ------------------------------------------------------ Sedov-Taylor (C3)
+
+def _blast_front(sim, n):
+    """Shock front of a centred blast: the outer radius where the spherically
+    averaged density falls half way from its peak back to ambient (1)."""
+    x = sim.read("X")
+    rho = sim.read("RHO")
+    r = np.sqrt(((x - 0.5) ** 2).sum(axis=0))
+    bins = np.linspace(0.0, 0.5, n + 1)
+    k = np.digitize(r, bins) - 1
+    prof = np.array([rho[k == i].mean() if np.any(k == i) else 1.0 for i in range(n)])
+    kp = int(np.argmax(prof))
+    half = 0.5 * (1.0 + prof[kp])
+    kf = kp
+    while kf + 1 < n - 1 and prof[kf + 1] > half:
+        kf += 1
+    c0, c1 = 0.5 * (bins[kf] + bins[kf + 1]), 0.5 * (bins[kf + 1] + bins[kf + 2])
+    return c0 + (prof[kf] - half) / (prof[kf] - prof[kf + 1]) * (c1 - c0), prof[kp]
+
+
+@pytest.mark.slow
+def test_blast_shock_front_follows_sedov_taylor():
+    """C3 physics: a point blast of energy E in gas of density 1 drives a
+    shock whose radius grows as t^(2/5) with the similarity constant xi0
+    (Taylor 1950).  24^3 cells, 2^3 particles per cell, degree 2, FP64: the
+    half-rise front is within 5% of xi0 (E t^2/rho)^(1/5) at t = 0.02..0.04,
+    and R(0.04)/R(0.02) within 4% of 2^(2/5).  A dropped pressure term, a
+    wrong EOS or energy update, or mis-scaled weights move the front."""
+    g = _gold("sedov_taylor.txt")
+    xi0, ex = g["xi0_gamma_1_4"][0], g["exponent"][0]
+    n = 24
+    p = I.blast(n=n, precision="fp64", radius_cells=1.5)
+    s = O.OracleSim(p.cfg)
+    s.add_particles(p.x, p.v, p.mass, p.rho, p.e)
+    fronts = {}
+    for t in (0.02, 0.03, 0.04):
+        s.step(100000, t_end=t)
+        rf, peak = _blast_front(s, n)
+        fronts[t] = rf
+        rs = xi0 * t ** ex                 # E = rho = 1: (E t^2 / rho)^(1/5) = t^(2/5)
+        assert abs(rf / rs - 1.0) < 0.05, (t, rf, rs)
+        assert 1.5 < peak < 6.0            # compressed, below the strong-shock limit (g+1)/(g-1)
+    assert abs(fronts[0.04] / fronts[0.02] / 2.0 ** ex - 1.0) < 0.04
