@@ -705,6 +705,7 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
     int so[3];
     tile_origin(G, tile, so);
     const float dt = (float)clk->dt_cur;
+    const bool bc = window_has_bc(G, gr.mask, so);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         int idx[3];
         const int64_t node = slot_node<P>(G, so, i, idx);
@@ -717,9 +718,11 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
                 f[a] = gr.f[a][node];
                 m2[a] = gr.mv2[a][node];
             }
-            node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, mv, 0);
-            node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
-            node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, m2, 0);
+            if (bc) {
+                node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, mv, 0);
+                node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
+                node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, m2, 0);
+            }
         }
         const float im = m != 0.f ? __frcp_rn(m) : 0.f;
         float vb[3];

@@ -321,6 +321,19 @@ __device__ __forceinline__ void node_bc(const Geom& G, const uint8_t* mask, cons
     }
 }
 
+// Whether any node of the window of the tile at so[] needs node_bc: an
+// obstacle mask exists, or the window reaches a node on or beyond a
+// non-periodic face.
+__device__ __forceinline__ bool window_has_bc(const Geom& G, const uint8_t* mask, const int so[3])
+{
+    if (mask) return true;
+    for (int a = 0; a < G.dim; ++a) {
+        if (G.per[a]) continue;
+        if (so[a] <= G.g[a] || so[a] + G.W[a] - 1 >= G.n[a] + G.g[a]) return true;
+    }
+    return false;
+}
+
 template <class R>
 __device__ __forceinline__ uint32_t key_of(const Geom& G, const int sp[3])
 {
