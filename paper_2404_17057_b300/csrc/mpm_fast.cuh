@@ -6,13 +6,17 @@
 // here one thread owns one span: it sums its particles' contributions in
 // registers (tensor products of 1D weights, two fields per packed f32x2 FMA)
 // and adds each node of the span once into the tile's shared-memory window.
-// A warp owns one x-row of 32 spans, so those adds never collide or share a
-// bank.  The window then goes to global memory once, as 16-byte vector
+// A warp owns 32 consecutive spans (one or more x-rows of the tile); the
+// x-neighbours of a row are summed by shuffles first, so the adds never
+// collide.  The window then goes to global memory once, as 16-byte vector
 // reductions along the (padded, 16-byte aligned) node rows.
 //
 // G2P-type work (the gathers of steps iv-viii) keeps one thread per particle:
 // lanes of one span read the same node records (a broadcast), and the sums
-// are factored along the axes (x first, then y, then z).
+// are factored along the axes (x first, then y, then z).  K2 stages its row
+// chunks of particles in shared memory with bulk copies and runs both kinds
+// of work on them: the gather per particle, then the momentum scatter per
+// span.
 #pragma once
 #include "mpm_kernels.cuh"
 #include "mpm_tma.cuh"
@@ -37,20 +41,6 @@ __device__ __forceinline__ void weights1d(float fx, float* w, float* dw)
         dw[0] = -1.0f;
         dw[1] = 1.0f;
     }
-}
-
-// Span and weights along one axis; the span uses the same rounding rule as
-// the sort key, so it always matches the particle's place in the order.
-// Returns the local span inside the tile, or -1.
-template <int P>
-__device__ __forceinline__ int axis_fast(const Geom& G, int a, float x, int so, float* w, float* dw)
-{
-    float xi;
-    const int c = span_of<float, P>(G, a, x, xi);
-    const float fx = __fsub_rn(xi, (float)(c - (P == 2 ? 1 : 0)));
-    weights1d<P>(fx, w, dw);
-    const int l = wrap_span(G, a, c) - so;
-    return (l >= 0 && l < G.T[a]) ? l : -1;
 }
 
 // Offset and weights of a particle along one axis when its span is known
@@ -78,10 +68,10 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // Node lx gets v[0] of its own span, v[1] of span lx - 1 and v[2] of span
 // lx - 2 (warp shuffles); the last two lanes of a segment also carry the
 // halo nodes T0 and T0 + 1.  All lanes of the warp must call this together.
-// Same as xrow_add with plain read-add-write instead of atomics: valid when
-// no other warp writes this field of the window at the same time.  Within
-// the instruction every lane writes a different node (lanes of different
-// row segments use different node rows for the same (b, c)).
+// Plain read-add-write: valid when no other warp writes this field of the
+// window at the same time.  Within the instruction every lane writes a
+// different node (lanes of different row segments use different node rows
+// for the same (b, c)).
 template <int NS>
 __device__ __forceinline__ void xrow_rmw(float* row, const float* v, int lx, int T0)
 {
@@ -101,27 +91,6 @@ __device__ __forceinline__ void xrow_rmw(float* row, const float* v, int lx, int
         }
     } else {
         if (lx == T0 - 1) row[T0] += v[NS - 1];
-    }
-}
-
-template <int NS>
-__device__ __forceinline__ void xrow_add(float* row, const float* v, int lx, int T0)
-{
-    float s = v[0];
-#pragma unroll
-    for (int a = 1; a < NS; ++a) {
-        const float u = __shfl_up_sync(0xffffffffu, v[a], a);
-        if (lx >= a) s += u;
-    }
-    atomicAdd(row + lx, s);
-    if (NS == 3) {
-        // node T0 = v[1] of lane T0-1 + v[2] of lane T0-2 (added by lane T0-1);
-        // node T0+1 = v[2] of lane T0-1 (added by lane T0-2)
-        const float u2 = __shfl_up_sync(0xffffffffu, v[2], 1);
-        const float d2 = __shfl_down_sync(0xffffffffu, v[2], 1);
-        if (lx >= T0 - 2) atomicAdd(row + (lx == T0 - 1 ? T0 : T0 + 1), lx == T0 - 1 ? v[1] + u2 : d2);
-    } else {
-        if (lx == T0 - 1) atomicAdd(row + T0, v[NS - 1]);
     }
 }
 
@@ -189,28 +158,6 @@ __device__ __forceinline__ void flush_window(const Geom& G, const int so[3], con
                 if (v != 0.f) atomicAdd(row + gx, v);
             }
         }
-    }
-}
-
-// Particle state one P2G step reads, loaded one particle ahead.
-template <int D>
-struct PState {
-    float x[3], v[3], M, rho, E, Q;
-};
-
-template <int D, bool FORCE>
-__device__ __forceinline__ void load_state(const Particles<float>& pt, uint32_t k, PState<D>& s)
-{
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        s.x[a] = pt.x[a][k];
-        s.v[a] = pt.v[a][k];
-    }
-    s.M = pt.M[k];
-    if (FORCE) {
-        s.rho = pt.rho[k];
-        s.E = pt.E[k];
-        s.Q = pt.Q[k];
     }
 }
 
