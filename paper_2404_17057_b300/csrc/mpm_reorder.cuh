@@ -163,7 +163,8 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
         }
     }
     const int ny = hi[1] - lo[1] + 1 + nex[1], nz = hi[2] - lo[2] + 1 + nex[2];
-    const int nrows = ny * nz, nr = 3 * nrows;
+    const int nrows = ny * nz;
+    int nr = 3 * nrows;
     // ring parts that particles entered this tile from (set by the G2PD step)
     __shared__ unsigned long long rbits[kReorderMaxRanges / 64];
     for (int w = tid; w < kReorderMaxRanges / 64; w += kReorderThreads)
@@ -209,34 +210,53 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
         }
     }
     __syncthreads();
-    for (int i = tid; i < nr; i += kReorderThreads) {
-        const uint32_t si = ustart[i];
-        int rank = 0;
-        for (int j = 0; j < nr; ++j) {
-            const uint32_t sj = ustart[j];
-            rank += (sj < si || (sj == si && j < i)) ? 1 : 0;
-        }
-        sstart[rank] = si;
-        soff[rank] = ulen[i];    // length for now; prefix below
-    }
-    __syncthreads();
+    // the non-empty ranges, ordered by old index (one warp: typically the
+    // tile's own rows and a few ring parts)
+    __shared__ int nr_used;
     if (warp == 0) {
-        uint32_t carry = 0;
+        const uint32_t lt = (1u << lane) - 1u;
+        int k = 0;
         for (int b = 0; b < nr; b += 32) {
+            // in place: an entry moves to a position at or before its own
             const int i = b + lane;
-            const uint32_t v = i < nr ? soff[i] : 0u;
+            const uint32_t st = i < nr ? ustart[i] : 0u, ln = i < nr ? ulen[i] : 0u;
+            const uint32_t m = __ballot_sync(0xffffffffu, ln > 0u);
+            if (ln > 0u) {
+                ustart[k + __popc(m & lt)] = st;
+                ulen[k + __popc(m & lt)] = ln;
+            }
+            k += __popc(m);
+        }
+        __syncwarp();
+        // non-empty ranges are disjoint: their starts differ
+        for (int i = lane; i < k; i += 32) {
+            const uint32_t si = ustart[i];
+            int rank = 0;
+            for (int j = 0; j < k; ++j) rank += ustart[j] < si ? 1 : 0;
+            sstart[rank] = si;
+            soff[rank] = ulen[i];    // length for now; prefix below
+        }
+        __syncwarp();
+        uint32_t carry = 0;
+        for (int b = 0; b < k; b += 32) {
+            const int i = b + lane;
+            const uint32_t v = i < k ? soff[i] : 0u;
             uint32_t s = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t u = __shfl_up_sync(0xffffffffu, s, o);
                 if (lane >= o) s += u;
             }
-            if (i < nr) soff[i] = carry + s - v;
+            if (i < k) soff[i] = carry + s - v;
             carry += __shfl_sync(0xffffffffu, s, 31);
         }
-        if (lane == 0) soff[nr] = carry;
+        if (lane == 0) {
+            soff[k] = carry;
+            nr_used = k;
+        }
     }
     __syncthreads();
+    nr = nr_used;
     const uint32_t C = soff[nr];
     const int lsh = G.tsh[0] + G.tsh[1] + G.tsh[2];
     const uint32_t lmask = (uint32_t)Tvol - 1u;
