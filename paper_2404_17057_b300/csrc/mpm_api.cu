@@ -211,14 +211,16 @@ struct Impl {
     // The single-precision float-atomic path runs the span-per-thread kernels
     // of mpm_fast.cuh; the fixed-point and FP64 paths the generic ones.
     static constexpr bool kFast = std::is_same<R, float>::value && std::is_same<A, float>::value;
+    // G2PD reads the grid once into its window, so the fixed-point mode runs
+    // the single-precision kernel too (the int64 sums are converted there)
+    static constexpr bool kFast3 = std::is_same<R, float>::value;
     static size_t smem(const Geom& G, int kernel)
     {
         const size_t W = (size_t)G.Wvol;
+        if (kernel == 2 && kFast3) return (D == 3 ? 24 : 16) * W;
         if (kFast) {
             if (kernel == 0) return (1 + 2 * D) * W * sizeof(float);
-            if (kernel == 1)
-                return (K2Cfg<D>::kHeadFloats + tile_cs_words(G)) * sizeof(float) + 16 * W + D * W * sizeof(float);
-            return (D == 3 ? 24 : 16) * W;
+            return (K2Cfg<D>::kHeadFloats + tile_cs_words(G)) * sizeof(float) + 16 * W + D * W * sizeof(float);
         }
         if (kernel == 0) return (1 + 2 * D) * W * sizeof(A);
         if (kernel == 1) return align16(D * W * sizeof(R)) + D * W * sizeof(A);
@@ -242,18 +244,19 @@ struct Impl {
         };
         cudaError_t e = allow((const void*)k_reorder<D, R>, reorder_smem(G));
         if (e != cudaSuccess) return e;
+        if constexpr (kFast3) e = allow((const void*)k_g2pd_fast<D, P, A>, smem(G, 2));
+        else e = allow((const void*)k_g2pd<D, P, R, A>, smem(G, 2));
+        if (e != cudaSuccess) return e;
         if constexpr (kFast) {
-            const void* f[5] = {(const void*)k_p2g_span<D, P, true>, (const void*)k_p2g_span<D, P, false>,
-                                (const void*)k_grid_g2p_span<D, P, true>, (const void*)k_grid_g2p_span<D, P, false>,
-                                (const void*)k_g2pd_fast<D, P>};
-            const size_t z[5] = {smem(G, 0), smem(G, 0), smem(G, 1), smem(G, 1), smem(G, 2)};
-            for (int i = 0; i < 5; ++i)
+            const void* f[4] = {(const void*)k_p2g_span<D, P, true>, (const void*)k_p2g_span<D, P, false>,
+                                (const void*)k_grid_g2p_span<D, P, true>, (const void*)k_grid_g2p_span<D, P, false>};
+            const size_t z[4] = {smem(G, 0), smem(G, 0), smem(G, 1), smem(G, 1)};
+            for (int i = 0; i < 4; ++i)
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
             return cudaSuccess;
         } else {
             if ((e = allow((const void*)k_p2g<D, P, R, A>, smem(G, 0))) != cudaSuccess) return e;
-            if ((e = allow((const void*)k_grid_g2p<D, P, R, A>, smem(G, 1))) != cudaSuccess) return e;
-            return allow((const void*)k_g2pd<D, P, R, A>, smem(G, 2));
+            return allow((const void*)k_grid_g2p<D, P, R, A>, smem(G, 1));
         }
     }
     // which bit 0: zero + P2G, bit 1: grid + G2P + P2G, bit 2: G2PD + update
@@ -293,8 +296,8 @@ struct Impl {
             s->launches += 1;
         }
         if (which & 4) {
-            if constexpr (kFast)
-                k_g2pd_fast<D, P><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, pt, gr, cs, s->clk, ro);
+            if constexpr (kFast3)
+                k_g2pd_fast<D, P, A><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, pt, gr, cs, s->clk, ro);
             else
                 k_g2pd<D, P, R, A><<<G.ntiles, kThreads, smem(G, 2), st>>>(G, pt, gr, cs, s->clk, ro);
             s->launches += 1;
@@ -353,20 +356,22 @@ struct Impl {
             kb_reorder<D, R, A><<<ntl, kReorderThreads, sm, st>>>(d, tl);
             return;
         }
+        if (stage == 2) {
+            if constexpr (kFast3) kb_g2pd_fast<D, P, A><<<ntl, kG2PDThreads, sm, st>>>(d, tl);
+            else kb_g2pd<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
+            return;
+        }
         if constexpr (kFast) {
             if (stage == 0) {
                 if (per) kb_p2g_span<D, P, true><<<ntl, kP2GThreads, sm, st>>>(d, tl);
                 else kb_p2g_span<D, P, false><<<ntl, kP2GThreads, sm, st>>>(d, tl);
-            } else if (stage == 1) {
+            } else {
                 if (per) kb_grid_g2p_span<D, P, true><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
                 else kb_grid_g2p_span<D, P, false><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
-            } else {
-                kb_g2pd_fast<D, P><<<ntl, kG2PDThreads, sm, st>>>(d, tl);
             }
         } else {
             if (stage == 0) kb_p2g<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
-            else if (stage == 1) kb_grid_g2p<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
-            else kb_g2pd<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
+            else kb_grid_g2p<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
         }
     }
     // Allow every batched kernel the device's whole shared memory (a limit,
@@ -388,18 +393,19 @@ struct Impl {
         };
         cudaError_t e = allow((const void*)kb_reorder<D, R, A>, sm[3]);
         if (e != cudaSuccess) return e;
+        if constexpr (kFast3) e = allow((const void*)kb_g2pd_fast<D, P, A>, sm[2]);
+        else e = allow((const void*)kb_g2pd<D, P, R, A>, sm[2]);
+        if (e != cudaSuccess) return e;
         if constexpr (kFast) {
-            const void* f[5] = {(const void*)kb_p2g_span<D, P, true>, (const void*)kb_p2g_span<D, P, false>,
-                                (const void*)kb_grid_g2p_span<D, P, true>, (const void*)kb_grid_g2p_span<D, P, false>,
-                                (const void*)kb_g2pd_fast<D, P>};
-            const size_t z[5] = {sm[0], sm[0], sm[1], sm[1], sm[2]};
-            for (int i = 0; i < 5; ++i)
+            const void* f[4] = {(const void*)kb_p2g_span<D, P, true>, (const void*)kb_p2g_span<D, P, false>,
+                                (const void*)kb_grid_g2p_span<D, P, true>, (const void*)kb_grid_g2p_span<D, P, false>};
+            const size_t z[4] = {sm[0], sm[0], sm[1], sm[1]};
+            for (int i = 0; i < 4; ++i)
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
             return cudaSuccess;
         } else {
             if ((e = allow((const void*)kb_p2g<D, P, R, A>, sm[0])) != cudaSuccess) return e;
-            if ((e = allow((const void*)kb_grid_g2p<D, P, R, A>, sm[1])) != cudaSuccess) return e;
-            return allow((const void*)kb_g2pd<D, P, R, A>, sm[2]);
+            return allow((const void*)kb_grid_g2p<D, P, R, A>, sm[1]);
         }
     }
     static void keys(mpm_sim* s, int b, cudaStream_t st)

@@ -165,12 +165,12 @@ __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 3)
     grid_g2p_span_tile<D, P, PER>(p.G, p.pt[par], p.gr, p.g2p_out, p.cs[par], p.clk, r.tile);
 }
 
-template <int D, int P>
-__global__ void __launch_bounds__(kG2PDThreads) kb_g2pd_fast(const BatchProb<float, float>* __restrict__ bp,
-                                                    const TileRef* __restrict__ tl)
+template <int D, int P, class A>
+__global__ void __launch_bounds__(kG2PDThreads) kb_g2pd_fast(const BatchProb<float, A>* __restrict__ bp,
+                                                             const TileRef* __restrict__ tl)
 {
-    MPM_BATCH_PROLOGUE(float, float)
-    g2pd_fast_tile<D, P>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, p.ro, r.tile);
+    MPM_BATCH_PROLOGUE(float, A)
+    g2pd_fast_tile<D, P, A>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, p.ro, r.tile);
 }
 
 template <int D, class R, class A>

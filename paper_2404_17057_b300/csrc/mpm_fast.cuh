@@ -636,8 +636,9 @@ __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 4) k_grid_g2p_span(Geom G,
 
 constexpr int kG2PDThreads = 128;
 
-template <int D, int P>
-__device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<float>& pt, const Grid<float, float>& gr,
+// A: grid accumulator type (float, or int64 fixed point read back as float).
+template <int D, int P, class A>
+__device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<float>& pt, const Grid<A, float>& gr,
                                                const uint32_t* __restrict__ cs, Clock* clk, const Reorder& ro,
                                                const int tile)
 {
@@ -658,12 +659,12 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
         const int64_t node = slot_node<P>(G, so, i, idx);
         float mv[3] = {0.f, 0.f, 0.f}, f[3] = {0.f, 0.f, 0.f}, m2[3] = {0.f, 0.f, 0.f}, m = 0.f;
         if (node >= 0) {
-            m = gr.m[node];
+            m = Acc<A>::to_real(gr.m[node], G.dqscale[0]);
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                mv[a] = gr.mv[a][node];
-                f[a] = gr.f[a][node];
-                m2[a] = gr.mv2[a][node];
+                mv[a] = Acc<A>::to_real(gr.mv[a][node], G.dqscale[1]);
+                f[a] = Acc<A>::to_real(gr.f[a][node], G.dqscale[2]);
+                m2[a] = Acc<A>::to_real(gr.mv2[a][node], G.dqscale[1]);
             }
             if (bc) {
                 node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, mv, 0);
@@ -881,11 +882,11 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
     }
 }
 
-template <int D, int P>
-__global__ void __launch_bounds__(kG2PDThreads) k_g2pd_fast(Geom G, Particles<float> pt, Grid<float, float> gr,
-                                                   const uint32_t* __restrict__ cs, Clock* clk, Reorder ro)
+template <int D, int P, class A>
+__global__ void __launch_bounds__(kG2PDThreads) k_g2pd_fast(Geom G, Particles<float> pt, Grid<A, float> gr,
+                                                            const uint32_t* __restrict__ cs, Clock* clk, Reorder ro)
 {
-    g2pd_fast_tile<D, P>(G, pt, gr, cs, clk, ro, blockIdx.x);
+    g2pd_fast_tile<D, P, A>(G, pt, gr, cs, clk, ro, blockIdx.x);
 }
 
 }  // namespace mpm
