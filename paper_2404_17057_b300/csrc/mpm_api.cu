@@ -214,6 +214,9 @@ struct Impl {
     // G2PD reads the grid once into its window, so the fixed-point mode runs
     // the single-precision kernel too (the int64 sums are converted there)
     static constexpr bool kFast3 = std::is_same<R, float>::value;
+    // 2D fixed point: P2G by the span-per-lane int64 kernel
+    static constexpr bool kFixed1 = D == 2 && std::is_same<R, float>::value && std::is_same<A, long long>::value;
+    static_assert(!(kFixed1 && kFast), "one P2G kernel per mode");
     static size_t smem(const Geom& G, int kernel)
     {
         const size_t W = (size_t)G.Wvol;
@@ -255,7 +258,9 @@ struct Impl {
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
             return cudaSuccess;
         } else {
-            if ((e = allow((const void*)k_p2g<D, P, R, A>, smem(G, 0))) != cudaSuccess) return e;
+            if constexpr (kFixed1) e = allow((const void*)k_p2g_fixed<P>, smem(G, 0));
+            else e = allow((const void*)k_p2g<D, P, R, A>, smem(G, 0));
+            if (e != cudaSuccess) return e;
             return allow((const void*)k_grid_g2p<D, P, R, A>, smem(G, 1));
         }
     }
@@ -276,6 +281,8 @@ struct Impl {
                     k_p2g_span<D, P, true><<<G.ntiles, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk);
                 else
                     k_p2g_span<D, P, false><<<G.ntiles, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk);
+            } else if constexpr (kFixed1) {
+                k_p2g_fixed<P><<<G.ntiles, kP2GFixedThreads, smem(G, 0), st>>>(G, pt, gr, cs, s->clk);
             } else {
                 k_p2g<D, P, R, A><<<G.ntiles, kThreads, smem(G, 0), st>>>(G, pt, gr, cs, s->clk);
             }
@@ -369,6 +376,9 @@ struct Impl {
                 if (per) kb_grid_g2p_span<D, P, true><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
                 else kb_grid_g2p_span<D, P, false><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
             }
+        } else if constexpr (kFixed1) {
+            if (stage == 0) kb_p2g_fixed<P><<<ntl, kP2GFixedThreads, sm, st>>>(d, tl);
+            else kb_grid_g2p<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
         } else {
             if (stage == 0) kb_p2g<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
             else kb_grid_g2p<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
@@ -404,7 +414,9 @@ struct Impl {
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
             return cudaSuccess;
         } else {
-            if ((e = allow((const void*)kb_p2g<D, P, R, A>, sm[0])) != cudaSuccess) return e;
+            if constexpr (kFixed1) e = allow((const void*)kb_p2g_fixed<P>, sm[0]);
+            else e = allow((const void*)kb_p2g<D, P, R, A>, sm[0]);
+            if (e != cudaSuccess) return e;
             return allow((const void*)kb_grid_g2p<D, P, R, A>, sm[1]);
         }
     }
@@ -1308,4 +1320,5 @@ void mpm_destroy(mpm_sim* s)
 
 // The allocation-free re-order entry point (same translation unit).
 #include "mpm_noalloc.cu"
+#include "mpm_selfcheck.cu"
 #include "mpm_batch.cu"

@@ -72,19 +72,19 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // window at the same time.  Within the instruction every lane writes a
 // different node (lanes of different row segments use different node rows
 // for the same (b, c)).
-template <int NS>
-__device__ __forceinline__ void xrow_rmw(float* row, const float* v, int lx, int T0)
+template <int NS, class T>
+__device__ __forceinline__ void xrow_rmw(T* row, const T* v, int lx, int T0)
 {
-    float s = v[0];
+    T s = v[0];
 #pragma unroll
     for (int a = 1; a < NS; ++a) {
-        const float u = __shfl_up_sync(0xffffffffu, v[a], a);
+        const T u = __shfl_up_sync(0xffffffffu, v[a], a);
         if (lx >= a) s += u;
     }
     row[lx] += s;
     if (NS == 3) {
-        const float u2 = __shfl_up_sync(0xffffffffu, v[2], 1);
-        const float d2 = __shfl_down_sync(0xffffffffu, v[2], 1);
+        const T u2 = __shfl_up_sync(0xffffffffu, v[2], 1);
+        const T d2 = __shfl_down_sync(0xffffffffu, v[2], 1);
         if (lx >= T0 - 2) {
             const int o = lx == T0 - 1 ? T0 : T0 + 1;
             row[o] += lx == T0 - 1 ? v[1] + u2 : d2;
@@ -368,6 +368,188 @@ __global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, Particles<f
                                                               const uint32_t* __restrict__ cs, Clock* clk)
 {
     p2g_span_tile<D, P, PER>(G, pt, out, cs, clk, blockIdx.x);
+}
+
+// -------------------------------------------- K1, fixed point (2D)
+//
+// The P2G of the fixed-point mode with the span-per-lane layout of K1: each
+// contribution is formed exactly as in the generic kernel (same weights,
+// same binary32 order, quantised with the same rounding), so the int64 sums
+// -- exact and order independent -- are bit-identical to it.  A lane sums
+// its span's quanta in registers; warp 0 owns {m, M V_x, M V_y}, warp 1
+// {f_x, f_y}; each completed row goes into an int64 window (x-neighbours
+// summed by shuffles first), which is added to the grid once per node.
+//
+// Rounding to int64 costs about as much as the rest of the kernel, so a
+// particle whose every quantised contribution is bounded by 2^31 in
+// magnitude (checked from its largest weight, with a factor 2 margin for the
+// roundings) takes the 32-bit conversion, which is exact there; the others
+// take the full rounding.
+
+// Largest |w| and |dw| over the support nodes of one axis.
+template <int NS>
+__device__ __forceinline__ void axis_bounds(const AxisSup<float>& s, float& wm, float& dm)
+{
+    wm = fabsf(s.w[0]);
+    dm = fabsf(s.dw[0]);
+#pragma unroll
+    for (int k = 1; k < NS; ++k) {
+        wm = fmaxf(wm, fabsf(s.w[k]));
+        dm = fmaxf(dm, fabsf(s.dw[k]));
+    }
+}
+
+template <bool SMALL>
+__device__ __forceinline__ long long quantise(float c, float s)
+{
+    const float v = __fmul_rn(c, s);
+    if constexpr (SMALL) return (long long)__float2int_rn(v);
+    else return f2ll_rn(v);
+}
+
+// One particle's quanta into the lane sums: group 0 {M w, M V_x w, M V_y w}
+// (a = {M, M V_x, M V_y}), group 1 {F g_x, F g_y} (a[0] = F).
+template <int P, int GROUP, bool SMALL>
+__device__ __forceinline__ void fixed_contribs(const Geom& G, const AxisSup<float>* sx, const float* a,
+                                               long long (&q)[GROUP == 0 ? 3 : 2][(P + 1) * (P + 1)])
+{
+    typedef Op<float> O;
+    constexpr int NS = P + 1;
+#pragma unroll
+    for (int ky = 0; ky < NS; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < NS; ++kx) {
+            float w, g[3];
+            node_weights<float, 2>(sx, kx, ky, 0, w, g);
+            const int i = ky * NS + kx;
+            if constexpr (GROUP == 0) {
+                q[0][i] += quantise<SMALL>(O::mul(a[0], w), G.qscale[0]);
+                q[1][i] += quantise<SMALL>(O::mul(a[1], w), G.qscale[1]);
+                q[2][i] += quantise<SMALL>(O::mul(a[2], w), G.qscale[1]);
+            } else {
+                q[0][i] += quantise<SMALL>(O::mul(a[0], g[0]), G.qscale[2]);
+                q[1][i] += quantise<SMALL>(O::mul(a[0], g[1]), G.qscale[2]);
+            }
+        }
+}
+
+template <int P, int GROUP>
+__device__ __forceinline__ int p2g_fixed_group(const Geom& G, const Particles<float>& pt,
+                                               const uint32_t* __restrict__ cs, int64_t kb, const int so[3],
+                                               long long* win)
+{
+    typedef Op<float> O;
+    constexpr int NS = P + 1, NN = NS * NS, NQ = GROUP == 0 ? 3 : 2;
+    constexpr float kSmall = 1073741824.f;     // 2^30
+    const int W = G.Wvol, W0 = G.W[0];
+    const int lane = threadIdx.x & 31;
+    const float gm1 = (float)(G.gamma - 1.0), ih = (float)G.inv_h;
+    const int nrows = G.Tvol >> 5;
+    const int tseg = G.T[0] < 32 ? G.T[0] : 32;
+    const int lxw = lane & (tseg - 1);
+    int err = 0;
+    for (int r = 0; r < nrows; ++r) {
+        const int s = (r << 5) + lane;
+        const uint32_t b = cs[kb + s], e = cs[kb + s + 1];
+        const int lx = s & (G.T[0] - 1);
+        const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
+        if (__all_sync(0xffffffffu, b == e)) continue;
+        long long q[NQ][NN];
+#pragma unroll
+        for (int f = 0; f < NQ; ++f)
+#pragma unroll
+            for (int i = 0; i < NN; ++i) q[f][i] = 0;
+        for (uint32_t k = b; k < e; ++k) {
+            AxisSup<float> sx[3];
+            axis_support<float, P>(G, 0, pt.x[0][k], so[0], sx[0]);
+            axis_support<float, P>(G, 1, pt.x[1][k], so[1], sx[1]);
+            if (sx[0].l != lx || sx[1].l != ly) { err = 1; continue; }
+            sx[2].l = 0;
+            sx[2].w[0] = 1.f;
+            sx[2].dw[0] = 0.f;
+            float wm0, dm0, wm1, dm1;
+            axis_bounds<NS>(sx[0], wm0, dm0);
+            axis_bounds<NS>(sx[1], wm1, dm1);
+            const float M = pt.M[k];
+            float a[3];
+            bool small;
+            if constexpr (GROUP == 0) {
+                a[0] = M;
+                a[1] = O::mul(M, pt.v[0][k]);
+                a[2] = O::mul(M, pt.v[1][k]);
+                // NaN or infinity fails every comparison: full rounding
+                const float wb = wm0 * wm1;
+                small = (M * G.qscale[0] * wb < kSmall) & (fabsf(a[1]) * G.qscale[1] * wb < kSmall) &
+                        (fabsf(a[2]) * G.qscale[1] * wb < kSmall);
+            } else {
+                const float rho = pt.rho[k];
+                const float Pk = O::mul(O::mul(gm1, rho), pt.E[k]);
+                const float vol = O::dvd(M, rho);
+                a[0] = O::mul(O::mul(O::add(Pk, pt.Q[k]), vol), ih);
+                a[1] = a[2] = 0.f;
+                const float gb = fmaxf(dm0 * wm1, wm0 * dm1);
+                small = fabsf(a[0]) * G.qscale[2] * gb < kSmall;
+            }
+            if (small) fixed_contribs<P, GROUP, true>(G, sx, a, q);
+            else fixed_contribs<P, GROUP, false>(G, sx, a, q);
+        }
+        const int base = ly * W0 + lx - lxw;
+#pragma unroll
+        for (int ky = 0; ky < NS; ++ky) {
+#pragma unroll
+            for (int f = 0; f < NQ; ++f) {
+                long long v[NS];
+#pragma unroll
+                for (int c = 0; c < NS; ++c) v[c] = q[f][ky * NS + c];
+                // window fields: 0 m, 1 M V_x, 2 M V_y, 3 f_x, 4 f_y
+                xrow_rmw<NS, long long>(win + ((GROUP == 0 ? 0 : 3) + f) * W + base + ky * W0, v, lxw, tseg);
+            }
+        }
+    }
+    return err;
+}
+
+template <int P>
+__device__ __forceinline__ void p2g_fixed_tile(const Geom& G, const Particles<float>& pt,
+                                               const Grid<long long, float>& gr, const uint32_t* __restrict__ cs,
+                                               Clock* clk, const int tile)
+{
+    if (!clk->active) return;
+    const int64_t kb = (int64_t)tile * G.Tvol;
+    if (cs[kb] == cs[kb + G.Tvol]) return;
+    extern __shared__ __align__(16) long long swin[];
+    constexpr int NF = 5;
+    const int W = G.Wvol;
+    for (int i = threadIdx.x; i < NF * W; i += blockDim.x) swin[i] = 0;
+    __syncthreads();
+    int so[3];
+    tile_origin(G, tile, so);
+    // each warp is the only writer of its fields of the window
+    const int err = (threadIdx.x >> 5) == 0 ? p2g_fixed_group<P, 0>(G, pt, cs, kb, so, swin)
+                                            : p2g_fixed_group<P, 1>(G, pt, cs, kb, so, swin);
+    if (err) atomicOr(&clk->err, ERR_TILE);
+    __syncthreads();
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        int idx[3];
+        const int64_t node = slot_node<P>(G, so, i, idx);
+        if (node < 0) continue;
+        long long* dst[NF] = {gr.m, gr.mv[0], gr.mv[1], gr.f[0], gr.f[1]};
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const long long v = swin[f * W + i];
+            if (v != 0) Acc<long long>::add(dst[f] + node, v);
+        }
+    }
+}
+
+constexpr int kP2GFixedThreads = 64;
+
+template <int P>
+__global__ void __launch_bounds__(kP2GFixedThreads, 8) k_p2g_fixed(Geom G, Particles<float> pt,
+                                                                   Grid<long long, float> gr,
+                                                                   const uint32_t* __restrict__ cs, Clock* clk)
+{
+    p2g_fixed_tile<P>(G, pt, gr, cs, clk, blockIdx.x);
 }
 
 // ----------------------------------------- K2: grid update + G2P + P2G

@@ -181,9 +181,28 @@ template <> struct Acc<double> {
     static __device__ __forceinline__ void add(double* p, double v) { atomicAdd(p, v); }
     static __device__ __forceinline__ double to_real(double a, float) { return a; }
 };
+// Round a binary32 value to the nearest int64 (ties to even), from the
+// IEEE 754 binary32 layout, in 32-bit integer and single-precision
+// operations: below 2^23 in magnitude the value fits int32 and the 32-bit
+// conversion rounds it; from 2^23 on it is an integer, its 24-bit significand
+// shifted left by (biased exponent - 150).  Out of range: saturates to the
+// int64 limits; NaN: the int64 minimum.  The 64-bit conversion instruction is avoided because
+// it issues at a small fraction of the 32-bit rate.
+__device__ __forceinline__ long long f2ll_rn(float v)
+{
+    const uint32_t b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xffu) - 150;
+    const int small = __float2int_rn(v);
+    const unsigned long long sig = (unsigned long long)((b & 0x7fffffu) | 0x800000u) << (e < 0 ? 0 : (e > 39 ? 39 : e));
+    const long long big = (b >> 31) ? -(long long)sig : (long long)sig;
+    long long r = e < 0 ? (long long)small : big;
+    if (e > 39) r = (v == v && !(b >> 31)) ? 0x7fffffffffffffffll : (long long)0x8000000000000000ull;
+    return r;
+}
+
 template <> struct Acc<long long> {
     // Fixed point: a binary32 contribution c becomes round(c * 2^32/U).
-    static __device__ __forceinline__ long long from(float c, float s) { return __float2ll_rn(__fmul_rn(c, s)); }
+    static __device__ __forceinline__ long long from(float c, float s) { return f2ll_rn(__fmul_rn(c, s)); }
     static __device__ __forceinline__ void add(long long* p, long long v)
     {
         atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));

@@ -1,0 +1,59 @@
+// mpm_selfcheck.cu -- mpm_check_fixed_rounding: the fixed-point quantiser
+// against the device's own float-to-int64 conversion, on every binary32 input.
+//
+// Compiled into the same translation unit as mpm_api.cu (included at its end).
+
+namespace mpm {
+
+constexpr int kCheckThreads = 256;
+
+__global__ void __launch_bounds__(kCheckThreads) k_check_f2ll(unsigned long long* bad, uint32_t* first)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    unsigned long long n = 0;
+    uint32_t f = 0xffffffffu;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (1ull << 32); i += stride) {
+        const float v = __uint_as_float((uint32_t)i);
+        if (f2ll_rn(v) != __float2ll_rn(v)) {
+            ++n;
+            if ((uint32_t)i < f) f = (uint32_t)i;
+        }
+    }
+    if (n) {
+        atomicAdd(bad, n);
+        atomicMin(first, f);
+    }
+}
+
+}  // namespace mpm
+
+extern "C" mpm_status mpm_check_fixed_rounding(uint64_t* mismatches, uint32_t* first)
+{
+    using namespace mpm;
+    if (!mismatches || !first) return fail(nullptr, MPM_EINVAL, "mpm_check_fixed_rounding: NULL pointer");
+    struct Out {
+        unsigned long long bad;
+        uint32_t first;
+    };
+    Out* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(Out));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, MPM_ENOMEM, "mpm_check_fixed_rounding: cudaMalloc failed");
+    }
+    Out h = {0ull, 0xffffffffu};
+    e = cudaMemcpy(d, &h, sizeof h, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_check_f2ll<<<148 * 8, kCheckThreads>>>(&d->bad, &d->first);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, MPM_ECUDA, std::string("mpm_check_fixed_rounding: ") + cudaGetErrorString(e));
+    }
+    *mismatches = h.bad;
+    *first = h.first;
+    return MPM_OK;
+}

@@ -268,15 +268,20 @@ def request_problem(req: dict) -> Problem:
     return p
 
 
+MASS_UNIT_PER_PARTICLE = 8.0
+
+
 def normalised_fixed_units(p) -> list[float]:
     """Fixed-point units scaled to the problem (the normalised reading of the
-    'scale 2^-32 per unit' option): mass unit = mean particle mass, momentum
-    unit = mass unit x (|v| + c) of the faster of the two states, force unit =
-    momentum unit / the first CFL step.  A contribution of one particle then
-    spans about 2^32 quanta, whatever the resolution."""
+    'scale 2^-32 per unit' option): mass unit = 8 x the mean particle mass,
+    momentum unit = mass unit x (|v| + c) of the faster of the two states,
+    force unit = momentum unit / the first CFL step.  A contribution of one
+    particle then spans about 2^29 quanta, whatever the resolution: still 32
+    times finer than binary32, and below 2^31, where the P2G quantises with
+    32-bit conversions."""
     cfg = p.cfg
     g = float(cfg.get("gamma", 1.4))
-    um = float(np.mean(p.mass))
+    um = MASS_UNIT_PER_PARTICLE * float(np.mean(p.mass))
     c = np.sqrt(np.maximum(g * (g - 1.0) * p.e, 0.0))
     s = float(np.max(np.sqrt((p.v ** 2).sum(axis=0)) + c))
     umom = um * s

@@ -27,7 +27,7 @@ STATUS = {0: "MPM_OK", 1: "MPM_EINVAL", 2: "MPM_ENOMEM", 3: "MPM_ECUDA", 4: "MPM
 EXPORTS = ["mpm_create", "mpm_add_particles", "mpm_set_obstacle_mask", "mpm_cfl_dt", "mpm_step",
            "mpm_step_async", "mpm_sync", "mpm_read_state", "mpm_read_grid_fixed", "mpm_field_size",
            "mpm_conservation", "mpm_sizes", "mpm_profile", "mpm_profile_read", "mpm_stream",
-           "mpm_last_error", "mpm_destroy", "mpm_sort_keys_static", "mpm_batch_create", "mpm_batch_add",
+           "mpm_last_error", "mpm_destroy", "mpm_sort_keys_static", "mpm_check_fixed_rounding", "mpm_batch_create", "mpm_batch_add",
            "mpm_batch_remove", "mpm_batch_step_async", "mpm_batch_sync", "mpm_batch_info", "mpm_batch_stream",
            "mpm_batch_last_error", "mpm_batch_destroy"]
 SORT_STATIC_MAX_KEYS = 262144
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
     L.mpm_destroy.argtypes = [vp]
     L.mpm_destroy.restype = None
     L.mpm_sort_keys_static.argtypes = [vp, i64, i64, vp, vp, vp]
+    L.mpm_check_fixed_rounding.argtypes = [P(C.c_uint64), P(C.c_uint32)]
     L.mpm_batch_create.argtypes = [vp, P(vp)]
     L.mpm_batch_add.argtypes = [vp, vp, i64, d, d]
     L.mpm_batch_remove.argtypes = [vp, vp]
@@ -297,6 +298,15 @@ def mpm_sort_keys_static(keys_ptr: int, n: int, nkeys: int, perm_ptr: int, cell_
     foreign memory pool, latency-critical loops).  n is capped at
     SORT_STATIC_MAX_KEYS; concurrent calls on one device must not overlap."""
     _check(load().mpm_sort_keys_static(keys_ptr, int(n), int(nkeys), perm_ptr, cell_start_ptr, stream or None))
+
+
+def mpm_check_fixed_rounding() -> tuple[int, int]:
+    """(mismatches, first mismatching bit pattern) of the fixed-point
+    quantiser against the device's float-to-int64 conversion over all 2^32
+    binary32 inputs; (0, 0xffffffff) when they agree everywhere."""
+    bad, first = C.c_uint64(0), C.c_uint32(0)
+    _check(load().mpm_check_fixed_rounding(C.byref(bad), C.byref(first)))
+    return int(bad.value), int(first.value)
 
 
 def _bcheck(code: int, bh=None):

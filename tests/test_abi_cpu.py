@@ -51,3 +51,4 @@ def test_null_handles_are_rejected_without_a_device():
     assert L.mpm_batch_step_async(None, 1) == 1
     assert L.mpm_batch_sync(None) == 1
     L.mpm_batch_destroy(None)
+    assert L.mpm_check_fixed_rounding(None, None) == 1

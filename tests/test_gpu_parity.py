@@ -149,6 +149,37 @@ def test_fixed_point_p2g_bit_exact(dim, degree, n, bc):
 
 
 @pytest.mark.parametrize("dim,degree,n,bc", P2G_CASES)
+def test_fixed_point_p2g_bit_exact_with_large_quanta(dim, degree, n, bc):
+    # units near the typical contribution: quantised values straddle 2^31,
+    # so particles take both the 32-bit and the full int64 rounding
+    p = random_problem(dim, degree, n, bc, 15013, 13, "fp32_fixed64")
+    h = p.cfg["h"]
+    p.cfg["fixed_unit"] = [h ** dim, 0.1 * h ** dim, 0.8 * h ** (dim - 1)]
+    sim = gpu_sim(p)
+    sim.step(1, dt=1e-6)
+    gm, gmv, gf = O.p2g_fixed32(p.cfg, p.x, p.v, p.mass, p.rho, p.e, unit=p.cfg["fixed_unit"])
+    # largest mass contribution of each particle, in units of 2^32 quanta:
+    # some are above 1/2 (beyond int32), some below 1/4 (32-bit path)
+    xi = (p.x - np.asarray(p.cfg["origin"][:dim])[:, None]) / h
+    if degree == 2:
+        f = xi - np.floor(xi + 0.5) + 1.0
+        wmax = np.maximum.reduce([0.5 * (1.5 - f) ** 2, 0.75 - (f - 1.0) ** 2, 0.5 * (f - 0.5) ** 2])
+    else:
+        f = xi - np.floor(xi)
+        wmax = np.maximum(1.0 - f, f)
+    top = p.mass / h ** dim * wmax.prod(axis=0)
+    assert top.max() > 0.5 and top.min() < 0.25
+    for name, ref in (("GRID_M", gm), ("GRID_MV", gmv), ("GRID_F", gf)):
+        assert np.array_equal(sim.read_fixed(name), ref), name
+    sim.close()
+
+
+def test_fixed_point_rounding_is_the_device_conversion():
+    # the quantiser's own rounding against cvt.rni.s64.f32 on all 2^32 inputs
+    assert M.mpm_check_fixed_rounding() == (0, 0xFFFFFFFF)
+
+
+@pytest.mark.parametrize("dim,degree,n,bc", P2G_CASES)
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_float_p2g_matches_oracle(dim, degree, n, bc, precision):
     p = random_problem(dim, degree, n, bc, 15013, 12, precision)

@@ -70,5 +70,5 @@ def test_serving_problems_use_normalised_fixed_point_units():
     for r in reqs:
         p = I.request_problem(r)
         um, umom, uf = p.cfg["fixed_unit"]
-        assert um == pytest.approx(float(np.mean(p.mass)))
+        assert um == pytest.approx(I.MASS_UNIT_PER_PARTICLE * float(np.mean(p.mass)))
         assert umom > um > 0 and uf > umom
