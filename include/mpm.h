@@ -196,12 +196,13 @@ mpm_status mpm_sort_keys_static(const uint32_t* keys, int64_t n, int64_t nkeys, 
 
 /* Self-check of the fixed-point quantiser (MPM_FP32_FIXED64).  That mode
  * turns every binary32 P2G contribution c into the int64 round(c * S), ties
- * to even, with the library's own rounding routine (built from the IEEE 754
- * binary32 layout in 32-bit operations).  This call evaluates that routine
- * and the device's float-to-int64 conversion instruction on all 2^32
- * binary32 bit patterns on the current device and returns, in host memory,
- * the number of patterns where the two differ (*mismatches) and the smallest
- * such pattern (*first, 0xffffffff if none).  Synchronous; allocates 16 bytes
+ * to even.  Where a particle's quantised contributions are bounded by 2^31
+ * in magnitude the kernels round with the 32-bit float-to-int conversion
+ * (the 64-bit one is much slower).  This call evaluates both conversions on
+ * every binary32 bit pattern v with |v| < 2^31 on the current device and
+ * returns, in host memory, the number of patterns where they differ
+ * (*mismatches) and the smallest such pattern (*first, 0xffffffff if
+ * none).  Synchronous; allocates 16 bytes
  * of device memory for the call.  Errors: MPM_EINVAL (NULL pointer),
  * MPM_ENOMEM, MPM_ECUDA. */
 mpm_status mpm_check_fixed_rounding(uint64_t* mismatches, uint32_t* first);

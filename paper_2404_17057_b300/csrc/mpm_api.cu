@@ -214,7 +214,7 @@ struct Impl {
     // G2PD reads the grid once into its window, so the fixed-point mode runs
     // the single-precision kernel too (the int64 sums are converted there)
     static constexpr bool kFast3 = std::is_same<R, float>::value;
-    // 2D fixed point: P2G by the span-per-lane int64 kernel
+    // 2D fixed point: P2G and grid + G2P + P2G by the span-per-lane int64 kernels
     static constexpr bool kFixed1 = D == 2 && std::is_same<R, float>::value && std::is_same<A, long long>::value;
     static_assert(!(kFixed1 && kFast), "one P2G kernel per mode");
     static size_t smem(const Geom& G, int kernel)
@@ -258,9 +258,11 @@ struct Impl {
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
             return cudaSuccess;
         } else {
-            if constexpr (kFixed1) e = allow((const void*)k_p2g_fixed<P>, smem(G, 0));
-            else e = allow((const void*)k_p2g<D, P, R, A>, smem(G, 0));
-            if (e != cudaSuccess) return e;
+            if constexpr (kFixed1) {
+                if ((e = allow((const void*)k_p2g_fixed<P>, smem(G, 0))) != cudaSuccess) return e;
+                return allow((const void*)k_grid_g2p_fixed<P>, smem(G, 1));
+            }
+            if ((e = allow((const void*)k_p2g<D, P, R, A>, smem(G, 0))) != cudaSuccess) return e;
             return allow((const void*)k_grid_g2p<D, P, R, A>, smem(G, 1));
         }
     }
@@ -297,6 +299,8 @@ struct Impl {
                 else
                     k_grid_g2p_span<D, P, false><<<G.ntiles, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, pt, gr, o, cs,
                                                                                               s->clk);
+            } else if constexpr (kFixed1) {
+                k_grid_g2p_fixed<P><<<G.ntiles, kG2PFixedThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
             } else {
                 k_grid_g2p<D, P, R, A><<<G.ntiles, kThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
             }
@@ -378,7 +382,7 @@ struct Impl {
             }
         } else if constexpr (kFixed1) {
             if (stage == 0) kb_p2g_fixed<P><<<ntl, kP2GFixedThreads, sm, st>>>(d, tl);
-            else kb_grid_g2p<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
+            else kb_grid_g2p_fixed<P><<<ntl, kG2PFixedThreads, sm, st>>>(d, tl);
         } else {
             if (stage == 0) kb_p2g<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
             else kb_grid_g2p<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
@@ -414,9 +418,11 @@ struct Impl {
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
             return cudaSuccess;
         } else {
-            if constexpr (kFixed1) e = allow((const void*)kb_p2g_fixed<P>, sm[0]);
-            else e = allow((const void*)kb_p2g<D, P, R, A>, sm[0]);
-            if (e != cudaSuccess) return e;
+            if constexpr (kFixed1) {
+                if ((e = allow((const void*)kb_p2g_fixed<P>, sm[0])) != cudaSuccess) return e;
+                return allow((const void*)kb_grid_g2p_fixed<P>, sm[1]);
+            }
+            if ((e = allow((const void*)kb_p2g<D, P, R, A>, sm[0])) != cudaSuccess) return e;
             return allow((const void*)kb_grid_g2p<D, P, R, A>, sm[1]);
         }
     }

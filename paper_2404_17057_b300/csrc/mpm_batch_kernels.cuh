@@ -165,6 +165,14 @@ __global__ void __launch_bounds__(kP2GFixedThreads, 6) kb_p2g_fixed(const BatchP
     p2g_fixed_tile<P>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, r.tile);
 }
 
+template <int P>
+__global__ void __launch_bounds__(kG2PFixedThreads, 4)
+    kb_grid_g2p_fixed(const BatchProb<float, long long>* __restrict__ bp, const TileRef* __restrict__ tl)
+{
+    MPM_BATCH_PROLOGUE(float, long long)
+    grid_g2p_fixed_tile<P>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, r.tile);
+}
+
 template <int D, int P, bool PER>
 __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 3)
     kb_grid_g2p_span(const BatchProb<float, float>* __restrict__ bp, const TileRef* __restrict__ tl)

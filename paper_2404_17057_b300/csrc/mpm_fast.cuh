@@ -72,7 +72,21 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // window at the same time.  Within the instruction every lane writes a
 // different node (lanes of different row segments use different node rows
 // for the same (b, c)).
-template <int NS, class T>
+template <bool ATOMIC>
+__device__ __forceinline__ void sh_add(float* p, float v)
+{
+    if constexpr (ATOMIC) atomicAdd(p, v);
+    else *p += v;
+}
+template <bool ATOMIC>
+__device__ __forceinline__ void sh_add(long long* p, long long v)
+{
+    if constexpr (ATOMIC) atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+    else *p += v;
+}
+
+// ATOMIC: rows that other warps may update at the same time.
+template <int NS, class T, bool ATOMIC = false>
 __device__ __forceinline__ void xrow_rmw(T* row, const T* v, int lx, int T0)
 {
     T s = v[0];
@@ -81,16 +95,16 @@ __device__ __forceinline__ void xrow_rmw(T* row, const T* v, int lx, int T0)
         const T u = __shfl_up_sync(0xffffffffu, v[a], a);
         if (lx >= a) s += u;
     }
-    row[lx] += s;
+    sh_add<ATOMIC>(row + lx, s);
     if (NS == 3) {
         const T u2 = __shfl_up_sync(0xffffffffu, v[2], 1);
         const T d2 = __shfl_down_sync(0xffffffffu, v[2], 1);
         if (lx >= T0 - 2) {
             const int o = lx == T0 - 1 ? T0 : T0 + 1;
-            row[o] += lx == T0 - 1 ? v[1] + u2 : d2;
+            sh_add<ATOMIC>(row + o, lx == T0 - 1 ? v[1] + u2 : d2);
         }
     } else {
-        if (lx == T0 - 1) row[T0] += v[NS - 1];
+        if (lx == T0 - 1) sh_add<ATOMIC>(row + T0, v[NS - 1]);
     }
 }
 
@@ -384,28 +398,7 @@ __global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, Particles<f
 // particle whose every quantised contribution is bounded by 2^31 in
 // magnitude (checked from its largest weight, with a factor 2 margin for the
 // roundings) takes the 32-bit conversion, which is exact there; the others
-// take the full rounding.
-
-// Largest |w| and |dw| over the support nodes of one axis.
-template <int NS>
-__device__ __forceinline__ void axis_bounds(const AxisSup<float>& s, float& wm, float& dm)
-{
-    wm = fabsf(s.w[0]);
-    dm = fabsf(s.dw[0]);
-#pragma unroll
-    for (int k = 1; k < NS; ++k) {
-        wm = fmaxf(wm, fabsf(s.w[k]));
-        dm = fmaxf(dm, fabsf(s.dw[k]));
-    }
-}
-
-template <bool SMALL>
-__device__ __forceinline__ long long quantise(float c, float s)
-{
-    const float v = __fmul_rn(c, s);
-    if constexpr (SMALL) return (long long)__float2int_rn(v);
-    else return f2ll_rn(v);
-}
+// take the 64-bit one.
 
 // One particle's quanta into the lane sums: group 0 {M w, M V_x w, M V_y w}
 // (a = {M, M V_x, M V_y}), group 1 {F g_x, F g_y} (a[0] = F).
@@ -423,12 +416,12 @@ __device__ __forceinline__ void fixed_contribs(const Geom& G, const AxisSup<floa
             node_weights<float, 2>(sx, kx, ky, 0, w, g);
             const int i = ky * NS + kx;
             if constexpr (GROUP == 0) {
-                q[0][i] += quantise<SMALL>(O::mul(a[0], w), G.qscale[0]);
-                q[1][i] += quantise<SMALL>(O::mul(a[1], w), G.qscale[1]);
-                q[2][i] += quantise<SMALL>(O::mul(a[2], w), G.qscale[1]);
+                q[0][i] += Acc<long long>::from_t<SMALL>(O::mul(a[0], w), G.qscale[0]);
+                q[1][i] += Acc<long long>::from_t<SMALL>(O::mul(a[1], w), G.qscale[1]);
+                q[2][i] += Acc<long long>::from_t<SMALL>(O::mul(a[2], w), G.qscale[1]);
             } else {
-                q[0][i] += quantise<SMALL>(O::mul(a[0], g[0]), G.qscale[2]);
-                q[1][i] += quantise<SMALL>(O::mul(a[0], g[1]), G.qscale[2]);
+                q[0][i] += Acc<long long>::from_t<SMALL>(O::mul(a[0], g[0]), G.qscale[2]);
+                q[1][i] += Acc<long long>::from_t<SMALL>(O::mul(a[0], g[1]), G.qscale[2]);
             }
         }
 }
@@ -440,7 +433,6 @@ __device__ __forceinline__ int p2g_fixed_group(const Geom& G, const Particles<fl
 {
     typedef Op<float> O;
     constexpr int NS = P + 1, NN = NS * NS, NQ = GROUP == 0 ? 3 : 2;
-    constexpr float kSmall = 1073741824.f;     // 2^30
     const int W = G.Wvol, W0 = G.W[0];
     const int lane = threadIdx.x & 31;
     const float gm1 = (float)(G.gamma - 1.0), ih = (float)G.inv_h;
@@ -479,8 +471,8 @@ __device__ __forceinline__ int p2g_fixed_group(const Geom& G, const Particles<fl
                 a[2] = O::mul(M, pt.v[1][k]);
                 // NaN or infinity fails every comparison: full rounding
                 const float wb = wm0 * wm1;
-                small = (M * G.qscale[0] * wb < kSmall) & (fabsf(a[1]) * G.qscale[1] * wb < kSmall) &
-                        (fabsf(a[2]) * G.qscale[1] * wb < kSmall);
+                small = (M * G.qscale[0] * wb < kSmallQuanta) & (fabsf(a[1]) * G.qscale[1] * wb < kSmallQuanta) &
+                        (fabsf(a[2]) * G.qscale[1] * wb < kSmallQuanta);
             } else {
                 const float rho = pt.rho[k];
                 const float Pk = O::mul(O::mul(gm1, rho), pt.E[k]);
@@ -488,7 +480,7 @@ __device__ __forceinline__ int p2g_fixed_group(const Geom& G, const Particles<fl
                 a[0] = O::mul(O::mul(O::add(Pk, pt.Q[k]), vol), ih);
                 a[1] = a[2] = 0.f;
                 const float gb = fmaxf(dm0 * wm1, wm0 * dm1);
-                small = fabsf(a[0]) * G.qscale[2] * gb < kSmall;
+                small = fabsf(a[0]) * G.qscale[2] * gb < kSmallQuanta;
             }
             if (small) fixed_contribs<P, GROUP, true>(G, sx, a, q);
             else fixed_contribs<P, GROUP, false>(G, sx, a, q);
@@ -550,6 +542,136 @@ __global__ void __launch_bounds__(kP2GFixedThreads, 8) k_p2g_fixed(Geom G, Parti
                                                                    const uint32_t* __restrict__ cs, Clock* clk)
 {
     p2g_fixed_tile<P>(G, pt, gr, cs, clk, blockIdx.x);
+}
+
+// -------------------------------- K2, fixed point (2D): grid + G2P + P2G
+//
+// The generic kernel's arithmetic in the span-per-lane layout: the tile's
+// acceleration window is built as there; a lane then takes the particles of
+// its span one by one -- G2P sum in the same node order, V' written back,
+// M V' quantised into int64 register sums for the span's support nodes --
+// and each warp adds its completed rows into the shared int64 window (with
+// shared atomics: the rows of different warps overlap in y), which is added
+// to the grid once per node.
+constexpr int kG2PFixedThreads = 128;
+
+template <int P>
+__device__ __forceinline__ void grid_g2p_fixed_tile(const Geom& G, const Particles<float>& pt,
+                                                    const Grid<long long, float>& gr,
+                                                    const uint32_t* __restrict__ cs, Clock* clk, const int tile)
+{
+    typedef Op<float> O;
+    if (!clk->active) return;
+    const int64_t kb = (int64_t)tile * G.Tvol;
+    if (cs[kb] == cs[kb + G.Tvol]) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = G.Wvol, W0 = G.W[0];
+    float* sA = reinterpret_cast<float*>(smem_raw);
+    long long* s2 = reinterpret_cast<long long*>(smem_raw + ((sizeof(float) * 2 * W + 15) & ~size_t(15)));
+    int so[3];
+    tile_origin(G, tile, so);
+    accel_window<2, P, float, long long>(G, gr, so, sA, s2);
+    __syncthreads();
+    constexpr int NS = P + 1, NN = NS * NS;
+    const float dt = (float)clk->dt_cur;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int nrows = G.Tvol >> 5;
+    const int tseg = G.T[0] < 32 ? G.T[0] : 32;
+    const int lxw = lane & (tseg - 1);
+    float vmax = 0.f;
+    int err = 0;
+    for (int r = warp; r < nrows; r += nwarps) {
+        const int s = (r << 5) + lane;
+        const uint32_t b = cs[kb + s], e = cs[kb + s + 1];
+        const int lx = s & (G.T[0] - 1);
+        const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
+        if (__all_sync(0xffffffffu, b == e)) continue;
+        long long q[2][NN];
+#pragma unroll
+        for (int f = 0; f < 2; ++f)
+#pragma unroll
+            for (int i = 0; i < NN; ++i) q[f][i] = 0;
+        for (uint32_t k = b; k < e; ++k) {
+            AxisSup<float> sx[3];
+            axis_support<float, P>(G, 0, pt.x[0][k], so[0], sx[0]);
+            axis_support<float, P>(G, 1, pt.x[1][k], so[1], sx[1]);
+            if (sx[0].l != lx || sx[1].l != ly) { err = 1; continue; }
+            sx[2].l = 0;
+            sx[2].w[0] = 1.f;
+            sx[2].dw[0] = 0.f;
+            float acc[2] = {0.f, 0.f};
+#pragma unroll
+            for (int ky = 0; ky < NS; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < NS; ++kx) {
+                    float w, g[3];
+                    node_weights<float, 2>(sx, kx, ky, 0, w, g);
+                    const int slot = (ly + ky) * W0 + lx + kx;
+                    acc[0] = O::add(acc[0], O::mul(w, sA[slot]));
+                    acc[1] = O::add(acc[1], O::mul(w, sA[W + slot]));
+                }
+            const float M = pt.M[k];
+            float MV[2], v2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const float vn = O::add(pt.v[a][k], O::mul(dt, acc[a]));
+                pt.v[a][k] = vn;
+                MV[a] = O::mul(M, vn);
+                v2 = O::add(v2, O::mul(vn, vn));
+            }
+            vmax = fmaxf(vmax, O::sqr(v2));
+            float wm0, dm0, wm1, dm1;
+            axis_bounds<NS>(sx[0], wm0, dm0);
+            axis_bounds<NS>(sx[1], wm1, dm1);
+            const float bnd = fmaxf(fabsf(MV[0]), fabsf(MV[1])) * G.qscale[1] * (wm0 * wm1);
+            auto scatter = [&](auto small) {
+                constexpr bool SM = decltype(small)::value;
+#pragma unroll
+                for (int ky = 0; ky < NS; ++ky)
+#pragma unroll
+                    for (int kx = 0; kx < NS; ++kx) {
+                        float w, g[3];
+                        node_weights<float, 2>(sx, kx, ky, 0, w, g);
+                        q[0][ky * NS + kx] += Acc<long long>::from_t<SM>(O::mul(MV[0], w), G.qscale[1]);
+                        q[1][ky * NS + kx] += Acc<long long>::from_t<SM>(O::mul(MV[1], w), G.qscale[1]);
+                    }
+            };
+            if (bnd < kSmallQuanta) scatter(std::true_type{});
+            else scatter(std::false_type{});
+        }
+        const int base = ly * W0 + lx - lxw;
+#pragma unroll
+        for (int ky = 0; ky < NS; ++ky)
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                long long v[NS];
+#pragma unroll
+                for (int c = 0; c < NS; ++c) v[c] = q[f][ky * NS + c];
+                xrow_rmw<NS, long long, true>(s2 + f * W + base + ky * W0, v, lxw, tseg);
+            }
+    }
+    vmax = warp_max(vmax);
+    if (lane == 0) atomic_max_nonneg(&clk->vmax_bits, (double)vmax);
+    if (err) atomicOr(&clk->err, ERR_TILE);
+    __syncthreads();
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        int idx[3];
+        const int64_t node = slot_node<P>(G, so, i, idx);
+        if (node < 0) continue;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const long long v = s2[a * W + i];
+            if (v != 0) Acc<long long>::add(gr.mv2[a] + node, v);
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kG2PFixedThreads, 4) k_grid_g2p_fixed(Geom G, Particles<float> pt,
+                                                                        Grid<long long, float> gr,
+                                                                        const uint32_t* __restrict__ cs, Clock* clk)
+{
+    grid_g2p_fixed_tile<P>(G, pt, gr, cs, clk, blockIdx.x);
 }
 
 // ----------------------------------------- K2: grid update + G2P + P2G

@@ -14,6 +14,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <type_traits>
 
 namespace mpm {
 
@@ -172,37 +173,41 @@ template <> struct Op<double> {
 // ---------------------------------------------------- accumulator types
 template <class A> struct Acc;
 template <> struct Acc<float> {
+    static constexpr bool kFixed = false;
     static __device__ __forceinline__ float from(float c, float) { return c; }
+    template <bool>
+    static __device__ __forceinline__ float from_t(float c, float) { return c; }
     static __device__ __forceinline__ void add(float* p, float v) { atomicAdd(p, v); }
     static __device__ __forceinline__ float to_real(float a, float) { return a; }
 };
 template <> struct Acc<double> {
+    static constexpr bool kFixed = false;
     static __device__ __forceinline__ double from(double c, float) { return c; }
+    template <bool>
+    static __device__ __forceinline__ double from_t(double c, float) { return c; }
     static __device__ __forceinline__ void add(double* p, double v) { atomicAdd(p, v); }
     static __device__ __forceinline__ double to_real(double a, float) { return a; }
 };
-// Round a binary32 value to the nearest int64 (ties to even), from the
-// IEEE 754 binary32 layout, in 32-bit integer and single-precision
-// operations: below 2^23 in magnitude the value fits int32 and the 32-bit
-// conversion rounds it; from 2^23 on it is an integer, its 24-bit significand
-// shifted left by (biased exponent - 150).  Out of range: saturates to the
-// int64 limits; NaN: the int64 minimum.  The 64-bit conversion instruction is avoided because
-// it issues at a small fraction of the 32-bit rate.
-__device__ __forceinline__ long long f2ll_rn(float v)
+// Fixed-point rounding of a quantised value v = c * S to int64, ties to
+// even.  The 64-bit conversion issues at a small fraction of the 32-bit
+// rate, so values known to lie below 2^31 in magnitude (SMALL) take the
+// 32-bit conversion, which is exact there.
+template <bool SMALL>
+__device__ __forceinline__ long long round_ll(float v)
 {
-    const uint32_t b = __float_as_uint(v);
-    const int e = (int)((b >> 23) & 0xffu) - 150;
-    const int small = __float2int_rn(v);
-    const unsigned long long sig = (unsigned long long)((b & 0x7fffffu) | 0x800000u) << (e < 0 ? 0 : (e > 39 ? 39 : e));
-    const long long big = (b >> 31) ? -(long long)sig : (long long)sig;
-    long long r = e < 0 ? (long long)small : big;
-    if (e > 39) r = (v == v && !(b >> 31)) ? 0x7fffffffffffffffll : (long long)0x8000000000000000ull;
-    return r;
+    if constexpr (SMALL) return (long long)__float2int_rn(v);
+    else return __float2ll_rn(v);
 }
 
 template <> struct Acc<long long> {
+    static constexpr bool kFixed = true;
     // Fixed point: a binary32 contribution c becomes round(c * 2^32/U).
-    static __device__ __forceinline__ long long from(float c, float s) { return f2ll_rn(__fmul_rn(c, s)); }
+    static __device__ __forceinline__ long long from(float c, float s) { return round_ll<false>(__fmul_rn(c, s)); }
+    template <bool SMALL>
+    static __device__ __forceinline__ long long from_t(float c, float s)
+    {
+        return round_ll<SMALL>(__fmul_rn(c, s));
+    }
     static __device__ __forceinline__ void add(long long* p, long long v)
     {
         atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
@@ -267,6 +272,25 @@ __device__ __forceinline__ void axis_support(const Geom& G, int a, R x, int tile
     int l = wrap_span(G, a, c) - tile_span0;
     s.l = (l >= 0 && l < G.T[a]) ? l : -1;
 }
+
+// Largest |w| and |dw| over the support nodes of one axis.
+template <int NS, class R>
+__device__ __forceinline__ void axis_bounds(const AxisSup<R>& s, R& wm, R& dm)
+{
+    wm = fabs(s.w[0]);
+    dm = fabs(s.dw[0]);
+#pragma unroll
+    for (int k = 1; k < NS; ++k) {
+        wm = fmax(wm, fabs(s.w[k]));
+        dm = fmax(dm, fabs(s.dw[k]));
+    }
+}
+
+// Fixed point: a particle may round its contributions with the 32-bit
+// conversion when each bound (|factor| x S x largest weight) is below 2^30,
+// a factor 2 under 2^31 for the roundings of the contribution and of the
+// bound itself.  NaN and infinity fail the comparison.
+constexpr float kSmallQuanta = 1073741824.f;
 
 __device__ __forceinline__ void tile_origin(const Geom& G, int tile, int so[3])
 {
@@ -448,22 +472,50 @@ __device__ __forceinline__ void p2g_tile(const Geom& G, const Particles<R>& pt, 
         R MV[3];
 #pragma unroll
         for (int a = 0; a < D; ++a) MV[a] = O::mul(M, pt.v[a][k]);
+        auto scatter = [&](auto small) {
+            constexpr bool SM = decltype(small)::value;
 #pragma unroll
-        for (int kz = 0; kz < (D == 3 ? NS : 1); ++kz)
+            for (int kz = 0; kz < (D == 3 ? NS : 1); ++kz)
 #pragma unroll
-            for (int ky = 0; ky < NS; ++ky)
+                for (int ky = 0; ky < NS; ++ky)
 #pragma unroll
-                for (int kx = 0; kx < NS; ++kx) {
-                    R w, g[3];
-                    node_weights<R, D>(sx, kx, ky, kz, w, g);
-                    const int slot = ((sx[2].l + kz) * G.W[1] + sx[1].l + ky) * G.W[0] + sx[0].l + kx;
-                    Acc<A>::add(&s[slot], Acc<A>::from(O::mul(M, w), G.qscale[0]));
+                    for (int kx = 0; kx < NS; ++kx) {
+                        R w, g[3];
+                        node_weights<R, D>(sx, kx, ky, kz, w, g);
+                        const int slot = ((sx[2].l + kz) * G.W[1] + sx[1].l + ky) * G.W[0] + sx[0].l + kx;
+                        Acc<A>::add(&s[slot], Acc<A>::template from_t<SM>(O::mul(M, w), G.qscale[0]));
 #pragma unroll
-                    for (int a = 0; a < D; ++a) {
-                        Acc<A>::add(&s[(1 + a) * W + slot], Acc<A>::from(O::mul(MV[a], w), G.qscale[1]));
-                        Acc<A>::add(&s[(1 + D + a) * W + slot], Acc<A>::from(O::mul(F, g[a]), G.qscale[2]));
+                        for (int a = 0; a < D; ++a) {
+                            Acc<A>::add(&s[(1 + a) * W + slot],
+                                        Acc<A>::template from_t<SM>(O::mul(MV[a], w), G.qscale[1]));
+                            Acc<A>::add(&s[(1 + D + a) * W + slot],
+                                        Acc<A>::template from_t<SM>(O::mul(F, g[a]), G.qscale[2]));
+                        }
                     }
-                }
+        };
+        if constexpr (Acc<A>::kFixed) {
+            R wm[3], dm[3];
+#pragma unroll
+            for (int a = 0; a < D; ++a) axis_bounds<NS>(sx[a], wm[a], dm[a]);
+            R wb = wm[0], gb = (R)0, mvb = (R)0;
+#pragma unroll
+            for (int a = 1; a < D; ++a) wb *= wm[a];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                R ga = dm[a];
+#pragma unroll
+                for (int b = 0; b < D; ++b)
+                    if (b != a) ga *= wm[b];
+                gb = fmax(gb, ga);
+                mvb = fmax(mvb, fabs(MV[a]));
+            }
+            const bool small = (M * G.qscale[0] * wb < kSmallQuanta) & (mvb * G.qscale[1] * wb < kSmallQuanta) &
+                               (fabs(F) * G.qscale[2] * gb < kSmallQuanta);
+            if (small) scatter(std::true_type{});
+            else scatter(std::false_type{});
+        } else {
+            scatter(std::false_type{});
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -491,23 +543,13 @@ __global__ void __launch_bounds__(256) k_p2g(Geom G, Particles<R> pt, Grid<A, R>
 
 // ----------------------------------------------- grid update + G2P + P2G
 
+// G2P window of a tile: the acceleration a = f/m after the force boundary
+// conditions (D x W values), and the momentum accumulators set to zero.
 template <int D, int P, class R, class A>
-__device__ __forceinline__ void grid_g2p_tile(const Geom& G, const Particles<R>& pt, const Grid<A, R>& gr,
-                                              const uint32_t* cellstart, Clock* clk, const int tile)
+__device__ __forceinline__ void accel_window(const Geom& G, const Grid<A, R>& gr, const int so[3], R* sA, A* s2)
 {
     typedef Op<R> O;
-    if (!clk->active) return;
-    const uint32_t beg = cellstart[(int64_t)tile * G.Tvol];
-    const uint32_t end = cellstart[(int64_t)(tile + 1) * G.Tvol];
-    if (beg == end) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int W = G.Wvol;
-    R* sA = reinterpret_cast<R*>(smem_raw);                       // D x W: f/m after BC
-    // D x W momentum P2G accumulators, 16-byte aligned (8-byte atomics)
-    A* s2 = reinterpret_cast<A*>(smem_raw + ((sizeof(R) * D * W + 15) & ~size_t(15)));
-    int so[3];
-    tile_origin(G, tile, so);
-    const R dt = (R)clk->dt_cur;
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         int idx[3];
         int64_t node = slot_node<P>(G, so, i, idx);
@@ -525,6 +567,26 @@ __device__ __forceinline__ void grid_g2p_tile(const Geom& G, const Particles<R>&
             s2[a * W + i] = A(0);
         }
     }
+}
+
+template <int D, int P, class R, class A>
+__device__ __forceinline__ void grid_g2p_tile(const Geom& G, const Particles<R>& pt, const Grid<A, R>& gr,
+                                              const uint32_t* cellstart, Clock* clk, const int tile)
+{
+    typedef Op<R> O;
+    if (!clk->active) return;
+    const uint32_t beg = cellstart[(int64_t)tile * G.Tvol];
+    const uint32_t end = cellstart[(int64_t)(tile + 1) * G.Tvol];
+    if (beg == end) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = G.Wvol;
+    R* sA = reinterpret_cast<R*>(smem_raw);                       // D x W: f/m after BC
+    // D x W momentum P2G accumulators, 16-byte aligned (8-byte atomics)
+    A* s2 = reinterpret_cast<A*>(smem_raw + ((sizeof(R) * D * W + 15) & ~size_t(15)));
+    int so[3];
+    tile_origin(G, tile, so);
+    const R dt = (R)clk->dt_cur;
+    accel_window<D, P, R, A>(G, gr, so, sA, s2);
     __syncthreads();
     constexpr int NS = P + 1;
     R vmax = (R)0;
@@ -561,19 +623,36 @@ __device__ __forceinline__ void grid_g2p_tile(const Geom& G, const Particles<R>&
             v2 = O::add(v2, O::mul(vn, vn));
         }
         vmax = fmax(vmax, O::sqr(v2));
+        auto scatter = [&](auto small) {
+            constexpr bool SM = decltype(small)::value;
 #pragma unroll
-        for (int kz = 0; kz < (D == 3 ? NS : 1); ++kz)
+            for (int kz = 0; kz < (D == 3 ? NS : 1); ++kz)
 #pragma unroll
-            for (int ky = 0; ky < NS; ++ky)
+                for (int ky = 0; ky < NS; ++ky)
 #pragma unroll
-                for (int kx = 0; kx < NS; ++kx) {
-                    R w, g[3];
-                    node_weights<R, D>(sx, kx, ky, kz, w, g);
-                    const int slot = ((sx[2].l + kz) * G.W[1] + sx[1].l + ky) * G.W[0] + sx[0].l + kx;
+                    for (int kx = 0; kx < NS; ++kx) {
+                        R w, g[3];
+                        node_weights<R, D>(sx, kx, ky, kz, w, g);
+                        const int slot = ((sx[2].l + kz) * G.W[1] + sx[1].l + ky) * G.W[0] + sx[0].l + kx;
 #pragma unroll
-                    for (int a = 0; a < D; ++a)
-                        Acc<A>::add(&s2[a * W + slot], Acc<A>::from(O::mul(MV[a], w), G.qscale[1]));
-                }
+                        for (int a = 0; a < D; ++a)
+                            Acc<A>::add(&s2[a * W + slot], Acc<A>::template from_t<SM>(O::mul(MV[a], w), G.qscale[1]));
+                    }
+        };
+        if constexpr (Acc<A>::kFixed) {
+            R wb = (R)1, mvb = (R)0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                R wm, dm;
+                axis_bounds<NS>(sx[a], wm, dm);
+                wb *= wm;
+                mvb = fmax(mvb, fabs(MV[a]));
+            }
+            if (mvb * G.qscale[1] * wb < kSmallQuanta) scatter(std::true_type{});
+            else scatter(std::false_type{});
+        } else {
+            scatter(std::false_type{});
+        }
     }
     // block max of |V'| for the CFL rule
     vmax = warp_max(vmax);

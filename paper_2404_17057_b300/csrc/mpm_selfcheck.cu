@@ -1,5 +1,6 @@
-// mpm_selfcheck.cu -- mpm_check_fixed_rounding: the fixed-point quantiser
-// against the device's own float-to-int64 conversion, on every binary32 input.
+// mpm_selfcheck.cu -- mpm_check_fixed_rounding: the 32-bit rounding path of
+// the fixed-point quantiser against the 64-bit conversion, on every binary32
+// input it is used for.
 //
 // Compiled into the same translation unit as mpm_api.cu (included at its end).
 
@@ -14,7 +15,9 @@ __global__ void __launch_bounds__(kCheckThreads) k_check_f2ll(unsigned long long
     uint32_t f = 0xffffffffu;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (1ull << 32); i += stride) {
         const float v = __uint_as_float((uint32_t)i);
-        if (f2ll_rn(v) != __float2ll_rn(v)) {
+        // every input the P2G bound admits to the 32-bit path: |v| < 2^31
+        if (!(fabsf(v) < 2147483648.f)) continue;
+        if (round_ll<true>(v) != round_ll<false>(v)) {
             ++n;
             if ((uint32_t)i < f) f = (uint32_t)i;
         }

@@ -302,8 +302,9 @@ def mpm_sort_keys_static(keys_ptr: int, n: int, nkeys: int, perm_ptr: int, cell_
 
 def mpm_check_fixed_rounding() -> tuple[int, int]:
     """(mismatches, first mismatching bit pattern) of the fixed-point
-    quantiser against the device's float-to-int64 conversion over all 2^32
-    binary32 inputs; (0, 0xffffffff) when they agree everywhere."""
+    quantiser's 32-bit rounding against the float-to-int64 conversion over
+    every binary32 input below 2^31 in magnitude; (0, 0xffffffff) when they
+    agree everywhere."""
     bad, first = C.c_uint64(0), C.c_uint32(0)
     _check(load().mpm_check_fixed_rounding(C.byref(bad), C.byref(first)))
     return int(bad.value), int(first.value)

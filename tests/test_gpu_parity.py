@@ -175,7 +175,7 @@ def test_fixed_point_p2g_bit_exact_with_large_quanta(dim, degree, n, bc):
 
 
 def test_fixed_point_rounding_is_the_device_conversion():
-    # the quantiser's own rounding against cvt.rni.s64.f32 on all 2^32 inputs
+    # 32-bit rounding against the 64-bit conversion on every |v| < 2^31
     assert M.mpm_check_fixed_rounding() == (0, 0xFFFFFFFF)
 
 
