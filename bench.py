@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--config", default="blast", choices=["blast", "cylinder"])
     ap.add_argument("--n", type=int, default=0, help="override the grid size (cells per axis / x cells)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_fixed64", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_coloured", "fp32_fixed64", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", type=int, default=0,
                     help="also run the serving stream with this many requests (batched vs one at a time)")
@@ -77,17 +77,20 @@ def problem(args):
     return p, cfg
 
 
-def algorithmic_bytes(dim, s, n_p, n_n):
-    """Bytes each kernel must move at minimum (one read/write per word).
+def algorithmic_bytes(dim, s, n_p, n_n, g=None):
+    """Bytes each kernel must move at minimum (one read/write per word); s is
+    the particle word size, g the grid word size (8 for the int64 grid of the
+    fixed-point mode; default s).
     K1 P2G: particles read x,v,M,rho,e,q (2d+4 words); nodes written m,mv,f (2d+1).
     K2 grid+G2P+P2G: particles read x,v,M (2d+1), write v (d); nodes read m,f (1+d), write mv2 (d).
     K3 G2PD+update: particles read x,rho,e,q (d+3), write x,rho,e,q (d+3) and a 4-byte key;
                     nodes read m,mv,f,mv2 (1+3d).
     zeroing: nodes written (1+3d)."""
-    k1 = n_p * (2 * dim + 4) * s + n_n * (2 * dim + 1) * s
-    k2 = n_p * (3 * dim + 1) * s + n_n * (1 + 2 * dim) * s
-    k3 = n_p * ((2 * dim + 6) * s + 4) + n_n * (1 + 3 * dim) * s
-    zero = n_n * (1 + 3 * dim) * s
+    g = s if g is None else g
+    k1 = n_p * (2 * dim + 4) * s + n_n * (2 * dim + 1) * g
+    k2 = n_p * (3 * dim + 1) * s + n_n * (1 + 2 * dim) * g
+    k3 = n_p * ((2 * dim + 6) * s + 4) + n_n * (1 + 3 * dim) * g
+    zero = n_n * (1 + 3 * dim) * g
     return {"p2g": k1 + zero, "grid_g2p": k2, "g2pd": k3}
 
 
@@ -391,7 +394,7 @@ def main():
 
     dim = p.cfg["dim"]
     s = 8 if args.precision == "fp64" else 4
-    alg = algorithmic_bytes(dim, s, n_p, n_n)
+    alg = algorithmic_bytes(dim, s, n_p, n_n, 8 if args.precision in ("fp64", "fp32_fixed64") else 4)
     names = ["p2g", "grid_g2p", "g2pd"]
     per_launch_ms = {nme: phase_ms[i] / prof_steps for i, nme in enumerate(names)}
     dom = max(names, key=lambda k: per_launch_ms[k])
@@ -413,8 +416,8 @@ def main():
     line = {
         "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp32_fixed64": "f32+i64",
-                                                           "fp64": "f64"}[args.precision],
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp32_coloured": "f32",
+                                                           "fp32_fixed64": "f32+i64", "fp64": "f64"}[args.precision],
         "data": "synthetic", "config": meta,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
                      "frac": ach / hbm, "peak_source": which,

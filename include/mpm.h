@@ -69,7 +69,20 @@ typedef enum {
 } mpm_status;
 
 typedef enum { MPM_BC_WALL = 0, MPM_BC_PERIODIC = 1, MPM_BC_INFLOW = 2, MPM_BC_OUTFLOW = 3 } mpm_bc;
-typedef enum { MPM_FP32 = 0, MPM_FP32_FIXED64 = 1, MPM_FP64 = 2 } mpm_precision;
+/* MPM_FP32: float atomics on the grid (fastest; the order of the float
+ *   sums into a node varies between runs).
+ * MPM_FP32_FIXED64: binary32 contributions quantised to int64 (exact,
+ *   order-independent sums: bit-reproducible).
+ * MPM_FP64: everything in binary64 (float atomics).
+ * MPM_FP32_COLOURED: MPM_FP32 arithmetic, with the two node-scattering
+ *   kernels run in colour passes over the tiles (tile coordinate parities;
+ *   a third colour for the last tile of an odd periodic axis) whose node
+ *   windows never overlap, so each node receives its sums in a fixed order:
+ *   bit-reproducible FP32 without fixed point (the grid colouring that
+ *   Sec. 5, Discussion and conclusion, proposes, on tiles instead of cells).  Needs every tile edge >= degree and a
+ *   periodic axis to hold at least two whole tiles (MPM_EUNSUPPORTED), and
+ *   cannot join a batch. */
+typedef enum { MPM_FP32 = 0, MPM_FP32_FIXED64 = 1, MPM_FP64 = 2, MPM_FP32_COLOURED = 3 } mpm_precision;
 
 /* Fields for mpm_read_state / mpm_field_size. */
 enum {

@@ -65,6 +65,8 @@ struct mpm_sim {
     void* nrm = nullptr;           // d x nodes of type R
     Clock* clk = nullptr;
     uint32_t* cs[2] = {nullptr, nullptr};   // cell starts of particle buffer b
+    uint32_t* col_tiles = nullptr;          // colour passes: tiles grouped by colour
+    std::vector<int> col_off;               // colour c: col_tiles[col_off[c] .. col_off[c+1])
     uint32_t* count = nullptr;              // particles per new span (step re-order)
     uint32_t* cscan_part = nullptr;         // scan partials over the spans
     uint32_t* perm = nullptr;               // old index of each re-ordered particle
@@ -206,6 +208,14 @@ Grid<A, R> grid_view(const mpm_sim* s)
     return g;
 }
 
+// Colour passes of a coloured simulation (one pass over all tiles otherwise).
+int ncolours(const mpm_sim* s) { return s->col_off.empty() ? 1 : (int)s->col_off.size() - 1; }
+const uint32_t* colour_tiles(const mpm_sim* s, int c) { return s->col_off.empty() ? nullptr : s->col_tiles + s->col_off[c]; }
+unsigned colour_blocks(const mpm_sim* s, int c)
+{
+    return s->col_off.empty() ? (unsigned)s->G.ntiles : (unsigned)(s->col_off[c + 1] - s->col_off[c]);
+}
+
 template <int D, int P, class R, class A>
 struct Impl {
     // The single-precision float-atomic path runs the span-per-thread kernels
@@ -279,10 +289,15 @@ struct Impl {
                 (uint4*)s->grid, (int64_t)(s->grid_bytes / 16), &s->clk->active);
             if constexpr (kFast) {
                 const FieldPtrs o = p2g_fields(gr);
-                if (G.per[0] | G.per[1] | G.per[2])
-                    k_p2g_span<D, P, true><<<G.ntiles, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk);
-                else
-                    k_p2g_span<D, P, false><<<G.ntiles, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk);
+                const bool per = G.per[0] | G.per[1] | G.per[2];
+                for (int c = 0; c < ncolours(s); ++c) {
+                    const uint32_t* tl = colour_tiles(s, c);
+                    const unsigned nb = colour_blocks(s, c);
+                    if (nb == 0) continue;
+                    if (per) k_p2g_span<D, P, true><<<nb, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk, tl);
+                    else k_p2g_span<D, P, false><<<nb, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk, tl);
+                }
+                s->launches += ncolours(s) - 1;
             } else if constexpr (kFixed1) {
                 k_p2g_fixed<P><<<G.ntiles, kP2GFixedThreads, smem(G, 0), st>>>(G, pt, gr, cs, s->clk);
             } else {
@@ -293,12 +308,19 @@ struct Impl {
         if (which & 2) {
             if constexpr (kFast) {
                 const FieldPtrs o = g2p_fields(gr);
-                if (G.per[0] | G.per[1] | G.per[2])
-                    k_grid_g2p_span<D, P, true><<<G.ntiles, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, pt, gr, o, cs,
-                                                                                              s->clk);
-                else
-                    k_grid_g2p_span<D, P, false><<<G.ntiles, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, pt, gr, o, cs,
-                                                                                              s->clk);
+                const bool per = G.per[0] | G.per[1] | G.per[2];
+                for (int c = 0; c < ncolours(s); ++c) {
+                    const uint32_t* tl = colour_tiles(s, c);
+                    const unsigned nb = colour_blocks(s, c);
+                    if (nb == 0) continue;
+                    if (per)
+                        k_grid_g2p_span<D, P, true><<<nb, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, pt, gr, o, cs,
+                                                                                                s->clk, tl);
+                    else
+                        k_grid_g2p_span<D, P, false><<<nb, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, pt, gr, o, cs,
+                                                                                                 s->clk, tl);
+                }
+                s->launches += ncolours(s) - 1;
             } else if constexpr (kFixed1) {
                 k_grid_g2p_fixed<P><<<G.ntiles, kG2PFixedThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
             } else {
@@ -472,7 +494,7 @@ const Vtbl* vtbl_of()
 template <int D, int P>
 const Vtbl* vtbl_prec(int prec)
 {
-    if (prec == MPM_FP32) return vtbl_of<D, P, float, float>();
+    if (prec == MPM_FP32 || prec == MPM_FP32_COLOURED) return vtbl_of<D, P, float, float>();
     if (prec == MPM_FP32_FIXED64) return vtbl_of<D, P, float, long long>();
     return vtbl_of<D, P, double, double>();
 }
@@ -493,7 +515,7 @@ mpm_status make_geom(const mpm_config* c, Geom* G, std::string* why)
     if (!(c->h > 0.0) || !std::isfinite(c->h)) { *why = "h must be > 0"; return MPM_EINVAL; }
     if (!(c->gamma > 1.0)) { *why = "gamma must be > 1"; return MPM_EINVAL; }
     if (!(c->cfl > 0.0)) { *why = "cfl must be > 0"; return MPM_EINVAL; }
-    if (c->precision < 0 || c->precision > 2) { *why = "bad precision"; return MPM_EINVAL; }
+    if (c->precision < 0 || c->precision > 3) { *why = "bad precision"; return MPM_EINVAL; }
     if (c->sort_interval != 1) { *why = "sort_interval must be 1 (tiled kernels need key order)"; return MPM_EUNSUPPORTED; }
     G->dim = c->dim;
     G->p = c->degree;
@@ -522,6 +544,15 @@ mpm_status make_geom(const mpm_config* c, Geom* G, std::string* why)
         while ((1 << G->tsh[a]) < G->T[a]) ++G->tsh[a];
         G->nt[a] = (G->S[a] + G->T[a] - 1) / G->T[a];
         G->W[a] = G->T[a] + G->p;
+        if (c->precision == MPM_FP32_COLOURED) {
+            // same-colour tiles are two apart: their windows (tile + degree
+            // nodes) must not meet, nor may a window wrap onto itself
+            if (G->T[a] < G->p) { *why = "colouring needs tile edges >= degree"; return MPM_EUNSUPPORTED; }
+            if (G->per[a] && (G->n[a] % G->T[a] != 0 || G->n[a] < 2 * G->T[a])) {
+                *why = "colouring needs a periodic axis of at least two whole tiles";
+                return MPM_EUNSUPPORTED;
+            }
+        }
         G->lo[a] = c->origin[a];
         G->hi[a] = c->origin[a] + c->n[a] * c->h;
     }
@@ -721,6 +752,39 @@ mpm_status collect_profile(mpm_sim* s)
     return MPM_OK;
 }
 
+// Colour passes of MPM_FP32_COLOURED: the tiles grouped by the parities of
+// their coordinates, so that two tiles of one colour are at least two tiles
+// apart along some axis and their node windows (tile + degree nodes) never
+// meet; on a periodic axis with an odd tile count the last tile takes a
+// third colour (tile 0 is its neighbour across the seam).  Empty colours are
+// dropped; each list is in tile order.
+mpm_status build_colours(mpm_sim* s)
+{
+    const Geom& G = s->G;
+    int nc[3];
+    for (int a = 0; a < 3; ++a) nc[a] = G.nt[a] < 2 ? 1 : ((G.per[a] && (G.nt[a] & 1)) ? 3 : 2);
+    auto colour = [&](int a, int t) { return nc[a] == 1 ? 0 : (nc[a] == 3 && t == G.nt[a] - 1 ? 2 : (t & 1)); };
+    std::vector<std::vector<uint32_t>> lists((size_t)nc[0] * nc[1] * nc[2]);
+    for (int tz = 0; tz < G.nt[2]; ++tz)
+        for (int ty = 0; ty < G.nt[1]; ++ty)
+            for (int tx = 0; tx < G.nt[0]; ++tx) {
+                const int c = (colour(2, tz) * nc[1] + colour(1, ty)) * nc[0] + colour(0, tx);
+                lists[c].push_back((uint32_t)((tz * G.nt[1] + ty) * G.nt[0] + tx));
+            }
+    std::vector<uint32_t> flat;
+    flat.reserve(G.ntiles);
+    s->col_off.assign(1, 0);
+    for (const auto& l : lists) {
+        if (l.empty()) continue;
+        flat.insert(flat.end(), l.begin(), l.end());
+        s->col_off.push_back((int)flat.size());
+    }
+    s->col_tiles = (uint32_t*)dalloc(s, flat.size() * 4);
+    if (!s->col_tiles) return fail(s, MPM_ENOMEM, "device allocation failed");
+    CK(cudaMemcpy(s->col_tiles, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice), "colour list");
+    return MPM_OK;
+}
+
 }  // namespace
 
 // ================================================================== ABI
@@ -742,7 +806,7 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
     if (st != MPM_OK) { delete s; return fail(nullptr, st, why); }
     s->vt = select_vtbl(cfg->dim, cfg->degree, cfg->precision);
     s->rsize = cfg->precision == MPM_FP64 ? 8 : 4;
-    s->asize = cfg->precision == MPM_FP32 ? 4 : 8;
+    s->asize = (cfg->precision == MPM_FP32 || cfg->precision == MPM_FP32_COLOURED) ? 4 : 8;
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         cudaGetLastError();
         delete s;
@@ -803,6 +867,14 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
         cudaGetLastError();
         mpm_destroy(s);
         return fail(nullptr, MPM_ECUDA, "device initialisation failed");
+    }
+    if (cfg->precision == MPM_FP32_COLOURED) {
+        st = build_colours(s);
+        if (st != MPM_OK) {
+            const std::string m = s->err;
+            mpm_destroy(s);
+            return fail(nullptr, st, m);
+        }
     }
     *out = s;
     return MPM_OK;
@@ -1024,7 +1096,9 @@ static int64_t step_launch_count(const mpm_sim* s)
 {
     // prepare, zero, 3 step kernels, finalize; re-order: 3 scan kernels,
     // recycled placement (inflow only), tile moves
-    return 6 + 4 + (s->far_cap ? 1 : 0);
+    // a coloured simulation launches the two scattering kernels once per colour
+    const int extra = s->col_off.empty() ? 0 : 2 * ((int)s->col_off.size() - 2);
+    return 6 + 4 + (s->far_cap ? 1 : 0) + extra;
 }
 
 mpm_status mpm_step_async(mpm_sim* s, int64_t nsteps, double dt, double t_end)
@@ -1286,8 +1360,9 @@ mpm_status mpm_profile_read(mpm_sim* s, double out[8], int64_t counts[8], int re
     }
     if (counts) {
         // per-step launch counts of each phase (fixed by the configuration)
-        counts[0] = 2;   // zero + P2G
-        counts[1] = 1;
+        const int ncol = s->col_off.empty() ? 1 : (int)s->col_off.size() - 1;
+        counts[0] = 1 + ncol;   // zero + P2G
+        counts[1] = ncol;
         counts[2] = 1;
         counts[3] = 1;   // finalize (prepare counted with the step)
         counts[4] = 4 + (s->far_cap ? 1 : 0);

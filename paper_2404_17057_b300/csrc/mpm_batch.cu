@@ -267,6 +267,7 @@ mpm_status mpm_batch_add(mpm_batch* b, mpm_sim* s, int64_t nsteps, double dt, do
     if (nsteps <= 0 || !std::isfinite(dt) || !std::isfinite(t_end)) return bfail(b, MPM_EINVAL, "bad step arguments");
     if (s->device != b->device) return bfail(b, MPM_EINVAL, "simulation and batch are on different devices");
     if (s->profiling) return bfail(b, MPM_EUNSUPPORTED, "profiling is per simulation; disable it first");
+    if (!s->col_off.empty()) return bfail(b, MPM_EUNSUPPORTED, "a coloured simulation runs its own colour passes");
     mpm_status st = ensure_cfl(s);
     if (st != MPM_OK) return bfail(b, st, s->err);
     s->started = true;

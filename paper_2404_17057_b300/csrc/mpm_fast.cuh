@@ -377,11 +377,14 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
     flush_window<D, P>(G, so, sm, NF, out);
 }
 
+// tiles: the tiles of one colour pass (block b runs tiles[b]), or NULL (block
+// b runs tile b)
 template <int D, int P, bool PER>
 __global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, Particles<float> pt, FieldPtrs out,
-                                                              const uint32_t* __restrict__ cs, Clock* clk)
+                                                              const uint32_t* __restrict__ cs, Clock* clk,
+                                                              const uint32_t* __restrict__ tiles)
 {
-    p2g_span_tile<D, P, PER>(G, pt, out, cs, clk, blockIdx.x);
+    p2g_span_tile<D, P, PER>(G, pt, out, cs, clk, tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x);
 }
 
 // -------------------------------------------- K1, fixed point (2D)
@@ -931,9 +934,10 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
 template <int D, int P, bool PER>
 __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 4) k_grid_g2p_span(Geom G, Particles<float> pt,
                                                                          Grid<float, float> gr, FieldPtrs out,
-                                                                         const uint32_t* __restrict__ cs, Clock* clk)
+                                                                         const uint32_t* __restrict__ cs, Clock* clk,
+                                                                         const uint32_t* __restrict__ tiles)
 {
-    grid_g2p_span_tile<D, P, PER>(G, pt, gr, out, cs, clk, blockIdx.x);
+    grid_g2p_span_tile<D, P, PER>(G, pt, gr, out, cs, clk, tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x);
 }
 
 // ------------------------------- K3: G2PD + particle update + move + key

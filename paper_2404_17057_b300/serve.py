@@ -33,7 +33,7 @@ def footprint_bytes(prob) -> int:
     d = int(cfg["dim"])
     p = int(cfg["degree"])
     real = 8 if cfg.get("precision") == "fp64" else 4
-    acc = 4 if cfg.get("precision", "fp32") == "fp32" else 8
+    acc = 4 if cfg.get("precision", "fp32") in ("fp32", "fp32_coloured") else 8
     n = prob.n_particles
     nodes = 1
     spans = 1

@@ -52,3 +52,23 @@ def test_null_handles_are_rejected_without_a_device():
     assert L.mpm_batch_sync(None) == 1
     L.mpm_batch_destroy(None)
     assert L.mpm_check_fixed_rounding(None, None) == 1
+
+
+def test_coloured_mode_rejects_overlapping_colour_windows_without_a_device():
+    # configuration checks run before any CUDA call
+    from paper_2404_17057_b300 import inputs as I
+    L = M.load()
+    bad = [
+        # tile edge 1 < degree 2: same-colour windows would meet
+        I.base_config(3, [32, 32, 32], 1 / 32, ["wall"] * 6, precision="fp32_coloured", tile=[32, 8, 1]),
+        # periodic axis of 40 cells is not a whole number of 32-span tiles
+        I.base_config(2, [40, 16], 1 / 40, ["periodic"] * 4, precision="fp32_coloured", tile=[32, 8, 1]),
+        # periodic axis of one tile: the window wraps onto itself
+        I.base_config(2, [32, 16], 1 / 32, ["periodic"] * 4, precision="fp32_coloured", tile=[32, 8, 1]),
+    ]
+    for cfg in bad:
+        h = ctypes.c_void_p()
+        assert L.mpm_create(ctypes.byref(M.make_config(cfg)), ctypes.byref(h)) == 7
+        assert not h.value
+    bad_prec = I.base_config(2, [64, 16], 1 / 64, ["wall"] * 4, precision=4)
+    assert L.mpm_create(ctypes.byref(M.make_config(bad_prec)), ctypes.byref(ctypes.c_void_p())) == 1

@@ -179,6 +179,51 @@ def test_fixed_point_rounding_is_the_device_conversion():
     assert M.mpm_check_fixed_rounding() == (0, 0xFFFFFFFF)
 
 
+# colour passes: 2 or 3 colours per axis (48 = 3 tiles of 16 on a periodic
+# axis takes a third colour), ragged non-periodic tiles, degree 1 and 2
+COLOURED_CASES = [
+    (2, 2, [70, 37], ["inflow", "outflow", "wall", "wall"], (32, 8, 0)),
+    (3, 2, [48, 16, 8], ["periodic"] * 6, (16, 8, 4)),
+    (3, 1, [21, 13, 9], ["wall"] * 6, (8, 4, 4)),
+]
+
+
+@pytest.mark.parametrize("dim,degree,n,bc,tile", COLOURED_CASES)
+def test_coloured_p2g_matches_oracle(dim, degree, n, bc, tile):
+    p = random_problem(dim, degree, n, bc, 15013, 14, "fp32_coloured", tile)
+    sim = gpu_sim(p)
+    sim.step(1, dt=1e-6)
+    gm, gmv, gf = O.p2g(p.cfg, p.x, p.v, p.mass, p.rho, p.e)
+    for name, ref in (("GRID_M", gm), ("GRID_MV", gmv), ("GRID_F", gf)):
+        got = sim.read(name)
+        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), name
+    sim.close()
+
+
+@pytest.mark.parametrize("dim,degree,n,bc,tile", COLOURED_CASES)
+def test_coloured_steps_are_bit_reproducible(dim, degree, n, bc, tile):
+    p = random_problem(dim, degree, n, bc, 15013, 15, "fp32_coloured", tile)
+    outs = []
+    for _ in range(2):
+        g = gpu_sim(p)
+        g.step(30)
+        outs.append([g.read(f) for f in ("X", "V", "RHO", "E", "Q", "ID", "GRID_MV2")])
+        g.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_coloured_simulation_cannot_join_a_batch():
+    p = random_problem(2, 2, [64, 32], ["wall"] * 4, 1000, 16, "fp32_coloured")
+    sim = gpu_sim(p)
+    b = M.Batch()
+    with pytest.raises(M.MPMError) as e:
+        b.add(sim, 5)
+    assert e.value.status == "MPM_EUNSUPPORTED"
+    b.close()
+    sim.close()
+
+
 @pytest.mark.parametrize("dim,degree,n,bc", P2G_CASES)
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_float_p2g_matches_oracle(dim, degree, n, bc, precision):
@@ -248,8 +293,9 @@ def test_fp64_blast_3d_matches_oracle():
     g.close()
 
 
-def test_fp32_cylinder_100_steps_within_target():
-    p = f32(I.cylinder(nx=128, ny=64, seed=1, precision="fp32"))
+@pytest.mark.parametrize("precision", ["fp32", "fp32_coloured"])
+def test_fp32_cylinder_100_steps_within_target(precision):
+    p = f32(I.cylinder(nx=128, ny=64, seed=1, precision=precision))
     g, o = gpu_sim(p), oracle_sim(p)
     g.step(100)
     o.step(100)
@@ -268,8 +314,9 @@ def test_fp32_fixed_cylinder_100_steps_within_target():
     g.close()
 
 
-def test_fp32_blast_3d_100_steps_within_target():
-    p = f32(I.blast(n=16, precision="fp32"))
+@pytest.mark.parametrize("precision", ["fp32", "fp32_coloured"])
+def test_fp32_blast_3d_100_steps_within_target(precision):
+    p = f32(I.blast(n=16, precision=precision))
     g, o = gpu_sim(p), oracle_sim(p)
     g.step(100)
     o.step(100)
@@ -277,8 +324,9 @@ def test_fp32_blast_3d_100_steps_within_target():
     g.close()
 
 
-def test_fixed_point_is_bit_reproducible():
-    p = f32(I.cylinder(nx=96, ny=48, seed=3, precision="fp32_fixed64"))
+@pytest.mark.parametrize("precision", ["fp32_fixed64", "fp32_coloured"])
+def test_fixed_point_and_coloured_are_bit_reproducible(precision):
+    p = f32(I.cylinder(nx=96, ny=48, seed=3, precision=precision))
     outs = []
     for _ in range(2):
         g = gpu_sim(p)
