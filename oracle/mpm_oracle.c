@@ -343,6 +343,114 @@ int oracle_set_obstacle_mask(oracle_sim* s, const uint8_t* mask, const double* n
     return OR_OK;
 }
 
+/* ------------------------------------------- obstacle from a point profile */
+
+/* Signed distance of the point (X, Y) to the boundary made of closed loops of
+ * points (Eq. sdf): the boundary is the union of the loops' edges (vertex k
+ * to vertex k+1, the last back to the first); |sd| is the distance to its
+ * nearest point (*qx, *qy), found edge by edge, the first edge winning ties;
+ * sd < 0 inside, where a ray towards +x crosses the edges an odd number of
+ * times (even-odd rule, so inner loops are holes). */
+static double profile_sd(int64_t nloops, const int64_t* len, const double* px, const double* py, double X,
+                         double Y, double* qx, double* qy)
+{
+    double best = INFINITY;
+    int inside = 0;
+    int64_t base = 0;
+    *qx = X;
+    *qy = Y;
+    for (int64_t l = 0; l < nloops; ++l) {
+        for (int64_t k = 0; k < len[l]; ++k) {
+            int64_t a = base + k, b = base + (k + 1) % len[l];
+            double ex = px[b] - px[a], ey = py[b] - py[a];
+            double wx = X - px[a], wy = Y - py[a];
+            /* nearest point of the edge: a + t (b - a), t clamped to [0, 1] */
+            double L2 = ex * ex + ey * ey;
+            double t = L2 > 0.0 ? (wx * ex + wy * ey) / L2 : 0.0;
+            if (t < 0.0) t = 0.0;
+            if (t > 1.0) t = 1.0;
+            double cx = px[a] + t * ex, cy = py[a] + t * ey;
+            double dx = X - cx, dy = Y - cy;
+            double d2 = dx * dx + dy * dy;
+            if (d2 < best) { best = d2; *qx = cx; *qy = cy; }
+            /* crossing of the ray y = Y, x > X with this edge */
+            if ((py[a] > Y) != (py[b] > Y)) {
+                double xc = px[a] + (Y - py[a]) * ex / ey;
+                if (X < xc) inside ^= 1;
+            }
+        }
+        base += len[l];
+    }
+    double d = sqrt(best);
+    return inside ? -d : d;
+}
+
+int oracle_obstacle_profile(const oracle_config* cfg, int64_t nloops, const int64_t* loop_len, const double* pts,
+                            uint8_t* mask, double* normals, double* sd)
+{
+    geom G;
+    int st = geom_init(cfg, &G);
+    if (st != OR_OK) return st;
+    if (G.dim != 2 || nloops < 1 || !loop_len || !pts || !mask || !normals || !sd) return OR_EINVAL;
+    int64_t np = 0;
+    for (int64_t l = 0; l < nloops; ++l) {
+        if (loop_len[l] < 3) return OR_EINVAL;
+        np += loop_len[l];
+    }
+    const double* px = pts;
+    const double* py = pts + np;
+    for (int64_t k = 0; k < 2 * np; ++k)
+        if (!isfinite(pts[k])) return OR_EINVAL;
+    const int64_t nn = G.nnode;
+    double* qx = (double*)malloc((size_t)nn * sizeof(double));
+    double* qy = (double*)malloc((size_t)nn * sizeof(double));
+    if (!qx || !qy) { free(qx); free(qy); return OR_ENOMEM; }
+    /* 1. sd at every stored node, node i at lo + (i - g) h per axis */
+    for (int64_t j = 0; j < G.N[1]; ++j)
+        for (int64_t i = 0; i < G.N[0]; ++i) {
+            int64_t node = j * G.N[0] + i;
+            double X = G.lo[0] + (double)(i - G.g[0]) * G.h;
+            double Y = G.lo[1] + (double)(j - G.g[1]) * G.h;
+            sd[node] = profile_sd(nloops, loop_len, px, py, X, Y, &qx[node], &qy[node]);
+        }
+    /* 2. obstacle cells: a corner with sd <= 0; their corner nodes are masked */
+    memset(mask, 0, (size_t)nn);
+    for (int64_t cy = 0; cy < G.n[1]; ++cy)
+        for (int64_t cx = 0; cx < G.n[0]; ++cx) {
+            int64_t corner[4];
+            int hit = 0;
+            for (int c = 0; c < 4; ++c) {
+                int64_t ix = cx + (c & 1), iy = cy + (c >> 1);
+                ix = G.per[0] ? imod(ix, G.n[0]) : ix + G.g[0];
+                iy = G.per[1] ? imod(iy, G.n[1]) : iy + G.g[1];
+                corner[c] = iy * G.N[0] + ix;
+                if (sd[corner[c]] <= 0.0) hit = 1;
+            }
+            if (hit)
+                for (int c = 0; c < 4; ++c) mask[corner[c]] = 1;
+        }
+    /* 3. n = grad sd on masked nodes: (X - Q)/|X - Q| outside, (Q - X)/|X - Q|
+     *    inside (pointing out of the obstacle); 0 on the boundary itself */
+    for (int64_t j = 0; j < G.N[1]; ++j)
+        for (int64_t i = 0; i < G.N[0]; ++i) {
+            int64_t node = j * G.N[0] + i;
+            double nx = 0.0, ny = 0.0;
+            double d = fabs(sd[node]);
+            if (mask[node] && d > 0.0) {
+                double X = G.lo[0] + (double)(i - G.g[0]) * G.h;
+                double Y = G.lo[1] + (double)(j - G.g[1]) * G.h;
+                double s = sd[node] < 0.0 ? -1.0 : 1.0;
+                nx = s * ((X - qx[node]) / d);
+                ny = s * ((Y - qy[node]) / d);
+            }
+            normals[node] = nx;
+            normals[nn + node] = ny;
+        }
+    free(qx);
+    free(qy);
+    return OR_OK;
+}
+
 /* Obstacle projection, eqs. normali1/normali2: subtract the inward part. */
 void oracle_obstacle_project(int dim, const double* x, const double* n, double* out)
 {

@@ -99,6 +99,13 @@ int oracle_p2g_fixed32(const oracle_config* cfg, int64_t n, const float* x, cons
 
 /* Obstacle projection of one vector (eqs. normali1/normali2). */
 void oracle_obstacle_project(int dim, const double* x, const double* n, double* out);
+/* Obstacle of a 2D problem from closed loops of boundary points (Eq. sdf):
+ * loop l has loop_len[l] >= 3 points, pts = all x then all y (SoA, 2 x total).
+ * Per stored node: sd[node] (negative inside, even-odd rule), mask[node] = 1
+ * on the corner nodes of cells with a corner at sd <= 0, normals (2 x nodes,
+ * SoA) = grad sd on masked nodes, 0 elsewhere. */
+int oracle_obstacle_profile(const oracle_config* cfg, int64_t nloops, const int64_t* loop_len, const double* pts,
+                            uint8_t* mask, double* normals, double* sd);
 
 /* Philox-4x32-10 block function. */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

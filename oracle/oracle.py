@@ -82,6 +82,7 @@ def lib():
         L.oracle_p2g_fixed32.argtypes = [P(_Config), i64] + [vp] * 10
         L.oracle_obstacle_project.argtypes = [C.c_int, vp, vp, vp]
         L.oracle_obstacle_project.restype = None
+        L.oracle_obstacle_profile.argtypes = [P(_Config), i64, vp, vp, vp, vp, vp]
         L.oracle_philox4x32_10.argtypes = [vp, vp, vp]
         L.oracle_philox4x32_10.restype = None
         L.oracle_riemann_exact.argtypes = [d] * 7 + [i64, vp, vp, vp, vp, vp]
@@ -223,6 +224,21 @@ def _grid_sizes(cfg: dict):
     z = s.sizes()
     s.close()
     return z["nodes"], z["keys"]
+
+
+def obstacle_profile(cfg: dict, loops):
+    """Node mask, normals (2, nodes) and signed distance of a 2D obstacle given
+    as closed loops of boundary points, each a (2, k) array (Eq. sdf)."""
+    loops = [np.asarray(l, dtype=np.float64) for l in loops]
+    lens = np.array([l.shape[1] for l in loops], dtype=np.int64)
+    pts = np.ascontiguousarray(np.concatenate(loops, axis=1))
+    nn, _ = _grid_sizes(cfg)
+    mask = np.empty(nn, dtype=np.uint8)
+    nrm = np.empty(2 * nn)
+    sd = np.empty(nn)
+    _check(lib().oracle_obstacle_profile(C.byref(_cfg(cfg)), len(loops), _ptr(lens), _ptr(pts), _ptr(mask),
+                                         _ptr(nrm), _ptr(sd)), "obstacle_profile")
+    return mask, nrm.reshape(2, nn), sd
 
 
 def p2g(cfg: dict, x, v, mass, rho, e, q=None, dense: bool = False):

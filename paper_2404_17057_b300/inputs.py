@@ -40,6 +40,7 @@ class Problem:
     steps: int = 0
     t_end: float = 0.0
     meta: dict = field(default_factory=dict)
+    profile: list | None = None         # closed loops of obstacle boundary points, (2, k) each
 
     @property
     def n_particles(self) -> int:
@@ -172,6 +173,69 @@ def cylinder(nx=1024, ny=512, lx=2.0, center=(0.4, 0.5), radius=0.05, mach=3.0, 
     mask, nrm = cylinder_mask(cfg, center, radius)
     return Problem("cylinder", cfg, x, v, mass, rho, e, mask=mask, normals=nrm, steps=steps,
                    meta={"center": center, "radius": radius, "mach": mach})
+
+
+def naca4_symmetric(thickness=0.12, chord=0.1, npts=200, alpha_deg=0.0, leading_edge=(0.0, 0.0)):
+    """Closed boundary loop (2, 2 npts - 1) of a symmetric NACA 4-digit
+    aerofoil: half-thickness y_t = 5 t c (0.2969 sqrt(s) - 0.1260 s - 0.3516 s^2
+    + 0.2843 s^3 - 0.1015 s^4) at s = x/c (the published 4-digit series
+    formula), cosine-spaced s, upper surface from the trailing edge to the
+    nose, lower surface back (counter-clockwise); the loop closes across the
+    blunt trailing edge.  Pitched nose-up by alpha about the leading edge.  Stands in for the OAT15a point file of the
+    aerofoil case, which is not available."""
+    s = 0.5 * (1.0 - np.cos(np.linspace(0.0, np.pi, npts)))
+    yt = 5.0 * thickness * chord * (0.2969 * np.sqrt(s) - 0.1260 * s - 0.3516 * s ** 2 + 0.2843 * s ** 3
+                                    - 0.1015 * s ** 4)
+    xs = s * chord
+    upper = np.stack([xs[::-1], yt[::-1]])
+    lower = np.stack([xs[1:], -yt[1:]])
+    loop = np.concatenate([upper, lower], axis=1)
+    a = -np.deg2rad(alpha_deg)
+    rot = np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]])
+    return rot @ loop + np.asarray(leading_edge, dtype=np.float64)[:, None]
+
+
+def inside_loops(x, loops):
+    """Even-odd point-in-polygon test of points (2, N) against closed loops
+    (used to leave no particle inside an obstacle)."""
+    inside = np.zeros(x.shape[1], dtype=bool)
+    for loop in loops:
+        a = np.asarray(loop, dtype=np.float64)
+        b = np.roll(a, -1, axis=1)
+        for k in range(a.shape[1]):
+            ax, ay, bx, by = a[0, k], a[1, k], b[0, k], b[1, k]
+            cross = (ay > x[1]) != (by > x[1])
+            with np.errstate(divide="ignore", invalid="ignore"):
+                xc = ax + (x[1] - ay) * (bx - ax) / (by - ay)
+            inside ^= cross & (x[0] < xc)
+    return inside
+
+
+def aerofoil(nx=600, ny=405, lx=0.4, mach=0.73, alpha_deg=25.0, chord=0.1, leading_edge=(0.1, 0.15),
+             rho0=1.4, p0=1.0, ppa=3, npts=200, seed=2, steps=1000, degree=2, precision="fp32", cfl=0.4,
+             **kw) -> Problem:
+    """Transonic flow past an aerofoil (Sec. 4.1): [0, 0.4] x [0, 0.27], inflow
+    at -x with v = (Mach, 0) (c = 1 for rho = 1.4, p = 1), outflow on the other
+    faces, free stream everywhere at t = 0, 3 x 3 stratified ppc (9 ppc, about
+    2.2M particles at 600 x 405 = 243k cells); the obstacle is a NACA 0012
+    profile (stand-in for the OAT15a point file) at angle of attack alpha,
+    handed to the library as a point loop."""
+    h = lx / nx
+    cfg = base_config(2, [nx, ny], h, ["inflow", "outflow", "outflow", "outflow"], degree=degree, cfl=cfl,
+                      inflow_rho=rho0, inflow_p=p0, inflow_v=[mach, 0.0, 0.0], seed=seed,
+                      precision=precision, **kw)
+    loop = naca4_symmetric(0.12, chord, npts, alpha_deg, leading_edge)
+    rng = np.random.default_rng(seed)
+    x = _stratified([nx, ny], h, ppa, 2, rng)
+    x = np.ascontiguousarray(x[:, ~inside_loops(x, [loop])])
+    N = x.shape[1]
+    rho = np.full(N, rho0)
+    v = np.zeros((2, N))
+    v[0] = mach
+    mass = rho * h * h / (ppa * ppa)
+    e = np.full(N, p0 / ((cfg["gamma"] - 1.0) * rho0))
+    return Problem("aerofoil", cfg, x, v, mass, rho, e, steps=steps, profile=[loop],
+                   meta={"mach": mach, "alpha_deg": alpha_deg, "chord": chord})
 
 
 def blast(n=256, ppa=2, energy=1.0, rho0=1.0, p0=1e-5, steps=200, degree=2, precision="fp32",

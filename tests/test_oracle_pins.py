@@ -503,3 +503,107 @@ def test_blast_shock_front_follows_sedov_taylor():
         assert abs(rf / rs - 1.0) < 0.05, (t, rf, rs)
         assert 1.5 < peak < 6.0            # compressed, below the strong-shock limit (g+1)/(g-1)
     assert abs(fronts[0.04] / fronts[0.02] / 2.0 ** ex - 1.0) < 0.04
+
+
+# ------------------------------------------------ obstacle from a point profile
+
+def _node_xy(cfg):
+    xy = I.node_coords(cfg)
+    return xy[0], xy[1]
+
+
+def _box_sd(X, Y, c, hw, ang):
+    """Closed-form signed distance to a square of half-width hw centred at c,
+    rotated by ang, and its gradient."""
+    ca, sa = np.cos(ang), np.sin(ang)
+    u = ca * (X - c[0]) + sa * (Y - c[1])
+    w = -sa * (X - c[0]) + ca * (Y - c[1])
+    qu, qw = np.abs(u) - hw, np.abs(w) - hw
+    out = np.hypot(np.maximum(qu, 0), np.maximum(qw, 0))
+    ins = np.minimum(np.maximum(qu, qw), 0.0)
+    sd = out + ins
+    # gradient in local coordinates, then rotated back
+    gu = np.where(sd > 0, np.maximum(qu, 0) / np.where(out > 0, out, 1), (qu >= qw).astype(float))
+    gw = np.where(sd > 0, np.maximum(qw, 0) / np.where(out > 0, out, 1), (qw > qu).astype(float))
+    gu, gw = gu * np.sign(u), gw * np.sign(w)
+    return sd, np.stack([ca * gu - sa * gw, sa * gu + ca * gw]), np.abs(qu - qw)
+
+
+def test_profile_sd_of_a_rotated_square_is_the_box_distance():
+    cfg = I.base_config(2, [64, 48], 1 / 64, ["wall"] * 4)
+    c, hw, ang = (0.47, 0.36), 0.17, np.deg2rad(30.0)
+    corners = np.array([[-hw, hw, hw, -hw], [-hw, -hw, hw, hw]])
+    rot = np.array([[np.cos(ang), -np.sin(ang)], [np.sin(ang), np.cos(ang)]])
+    loop = rot @ corners + np.array(c)[:, None]
+    mask, nrm, sd = O.obstacle_profile(cfg, [loop])
+    X, Y = _node_xy(cfg)
+    ref, grad, gap = _box_sd(X, Y, c, hw, ang)
+    assert np.abs(sd - ref).max() < 1e-13
+    # normals are grad sd where it is defined (away from the medial axis and
+    # from the boundary itself)
+    ok = (mask == 1) & (np.abs(sd) > 1e-9) & (gap > 1e-6)
+    assert ok.sum() > 100
+    assert np.abs(nrm[:, ok] - grad[:, ok]).max() < 1e-12
+    assert np.all(nrm[:, mask == 0] == 0.0)
+
+
+def test_profile_of_a_polygonal_circle_converges_to_the_circle():
+    cfg = I.base_config(2, [96, 64], 1 / 64, ["wall"] * 4)
+    c, r, k = (0.71, 0.5), 0.2031, 4096
+    th = 2 * np.pi * np.arange(k) / k
+    loop = np.stack([c[0] + r * np.cos(th), c[1] + r * np.sin(th)])
+    mask, nrm, sd = O.obstacle_profile(cfg, [loop])
+    X, Y = _node_xy(cfg)
+    dist = np.hypot(X - c[0], Y - c[1])
+    # the polygon lies between the circle and its chords: sag r (1 - cos(pi/k))
+    assert np.abs(sd - (dist - r)).max() <= r * (1 - np.cos(np.pi / k)) + 1e-14
+    far = (mask == 1) & (dist > 2 * cfg["h"])
+    radial = np.stack([X - c[0], Y - c[1]]) / np.where(dist > 0, dist, 1)
+    assert np.min(np.sum(nrm[:, far] * radial[:, far], axis=0)) > 1 - 1e-5
+    # the obstacle cells are those of the analytic cylinder helper
+    am, _ = I.cylinder_mask(cfg, c, r)
+    assert np.array_equal(mask, am)
+
+
+def test_profile_ignores_orientation_and_start_vertex():
+    cfg = I.base_config(2, [50, 40], 1 / 50, ["wall"] * 4)
+    loop = I.naca4_symmetric(0.12, 0.5, 120, 7.0, (0.2, 0.4))
+    m0, n0, s0 = O.obstacle_profile(cfg, [loop])
+    for other in (loop[:, ::-1], np.roll(loop, 37, axis=1)):
+        m1, n1, s1 = O.obstacle_profile(cfg, [other])
+        assert np.abs(s1 - s0).max() < 1e-15
+        assert np.array_equal(m1, m0)
+        assert np.abs(n1 - n0).max() < 1e-9
+
+
+def test_profile_inner_loops_are_holes():
+    cfg = I.base_config(2, [40, 40], 1 / 40, ["wall"] * 4)
+    outer = np.array([[0.2, 0.8, 0.8, 0.2], [0.2, 0.2, 0.8, 0.8]])
+    inner = np.array([[0.4, 0.6, 0.6, 0.4], [0.4, 0.4, 0.6, 0.6]])
+    _, _, sd = O.obstacle_profile(cfg, [outer, inner])
+    X, Y = _node_xy(cfg)
+    ring = (np.maximum(np.abs(X - 0.5), np.abs(Y - 0.5)) > 0.1 + 1e-9) & \
+           (np.maximum(np.abs(X - 0.5), np.abs(Y - 0.5)) < 0.3 - 1e-9)
+    hole = np.maximum(np.abs(X - 0.5), np.abs(Y - 0.5)) < 0.1 - 1e-9
+    assert np.all(sd[ring] < 0) and np.all(sd[hole] > 0)
+    # inside the hole the distance is to the inner square
+    assert np.allclose(sd[hole], 0.1 - np.maximum(np.abs(X - 0.5), np.abs(Y - 0.5))[hole], atol=1e-14)
+
+
+def test_profile_of_a_symmetric_aerofoil_is_mirror_symmetric():
+    # NACA 0012 at zero incidence with its chord on a node row: sd(x, y0 + k h)
+    # = sd(x, y0 - k h), and the normals mirror
+    cfg = I.base_config(2, [64, 32], 1 / 64, ["wall"] * 4)
+    shape, off = I.node_shape(cfg)
+    y0 = (16 - off[1] + off[1]) * cfg["h"]       # physical node row 16
+    loop = I.naca4_symmetric(0.12, 0.6, 150, 0.0, (0.2, y0))
+    mask, nrm, sd = O.obstacle_profile(cfg, [loop])
+    S = sd.reshape(shape[1], shape[0])
+    Mk = mask.reshape(shape[1], shape[0])
+    Ny = nrm[1].reshape(shape[1], shape[0])
+    j0 = 16 + off[1]
+    for k in range(1, 12):
+        assert np.abs(S[j0 + k] - S[j0 - k]).max() < 1e-15
+        assert np.array_equal(Mk[j0 + k], Mk[j0 - k])
+        assert np.abs(Ny[j0 + k] + Ny[j0 - k]).max() < 1e-9
+    assert Mk.sum() > 50
