@@ -143,6 +143,32 @@ mpm_status mpm_add_particles(mpm_sim* sim, int64_t n, const double* x, const dou
  * (MPM_EINVAL): recycled particles are placed there. */
 mpm_status mpm_set_obstacle_mask(mpm_sim* sim, const uint8_t* node_mask, const double* normals);
 
+/* Obstacle of a 2D problem from closed loops of boundary points (the
+ * aerofoil case of Sec. 4.1 reads its profile from a point file; Eq. sdf).
+ *   nloops       >= 1
+ *   loop_len     nloops counts, each >= 3; at most 2^24 points in all
+ *   pts          host, 2 x total points: all x, then all y; loop l is the
+ *                next loop_len[l] points, its edges join consecutive points
+ *                and the last to the first (either orientation)
+ *   mask_out     optional host output (NULL: not returned), one byte per
+ *                stored node: the mask that was installed
+ *   normals_out  optional, 2 x nodes doubles (SoA): the normals installed
+ *   sd_out       optional, nodes doubles: the signed distance
+ * Computed on the device in binary64, every operation rounded separately:
+ * per stored node, sd = distance to the nearest point of the edges (the
+ * first edge wins ties), negative inside by the even-odd rule (inner loops
+ * are holes); cells with a corner at sd <= 0 are obstacle cells and their
+ * corner nodes are masked; normals = grad sd on masked nodes, (X - Q)/|X - Q|
+ * outside and (Q - X)/|X - Q| inside for the nearest boundary point Q (so
+ * they point out of the obstacle), 0 on the boundary and on unmasked nodes.
+ * Along a periodic axis the profile is not repeated.  The result replaces
+ * the obstacle as mpm_set_obstacle_mask would, with the same checks.
+ * Synchronous.  Errors: MPM_EINVAL (fewer than 3 points in a loop,
+ * non-finite points, obstacle nodes next to an inflow face),
+ * MPM_EUNSUPPORTED (3D), MPM_ENOMEM, MPM_ECUDA, MPM_ESTATE. */
+mpm_status mpm_set_obstacle_profile(mpm_sim* sim, int64_t nloops, const int64_t* loop_len, const double* pts,
+                                    uint8_t* mask_out, double* normals_out, double* sd_out);
+
 /* The CFL step (eq. CFL with Sec. 4.1's form) for the next step: from the
  * initial state before the first step, else from the last step. */
 mpm_status mpm_cfl_dt(mpm_sim* sim, double* dt_out);

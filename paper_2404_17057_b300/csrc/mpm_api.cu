@@ -787,6 +787,8 @@ mpm_status build_colours(mpm_sim* s)
 
 }  // namespace
 
+static mpm_status set_obstacle(mpm_sim* s, const uint8_t* mask, const double* normals);
+
 // ================================================================== ABI
 
 extern "C" {
@@ -1002,6 +1004,14 @@ mpm_status mpm_set_obstacle_mask(mpm_sim* s, const uint8_t* mask, const double* 
     if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
     if (s->poisoned) return fail(s, MPM_ESTATE, "simulation is poisoned: " + s->err);
     if (!mask || !normals) return fail(s, MPM_EINVAL, "NULL input array");
+    return set_obstacle(s, mask, normals);
+}
+
+}  // extern "C"
+
+// Checks a host node mask and normals (stored-node order) and installs them.
+static mpm_status set_obstacle(mpm_sim* s, const uint8_t* mask, const double* normals)
+{
     const Geom& G = s->G;
     const int64_t nn = G.nnode;
     const int d = G.dim;
@@ -1043,6 +1053,8 @@ mpm_status mpm_set_obstacle_mask(mpm_sim* s, const uint8_t* mask, const double* 
     drop_graphs(s);
     return MPM_OK;
 }
+
+extern "C" {
 
 static mpm_status ensure_cfl(mpm_sim* s)
 {
@@ -1402,4 +1414,5 @@ void mpm_destroy(mpm_sim* s)
 // The allocation-free re-order entry point (same translation unit).
 #include "mpm_noalloc.cu"
 #include "mpm_selfcheck.cu"
+#include "mpm_obstacle.cu"
 #include "mpm_batch.cu"

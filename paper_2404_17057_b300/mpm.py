@@ -24,12 +24,12 @@ FIELDS = {"X": 0, "V": 1, "M": 2, "RHO": 3, "E": 4, "P": 5, "Q": 6, "ID": 7, "KE
 STATUS = {0: "MPM_OK", 1: "MPM_EINVAL", 2: "MPM_ENOMEM", 3: "MPM_ECUDA", 4: "MPM_ESTATE",
           5: "MPM_ENONFINITE", 6: "MPM_ETIMEOUT", 7: "MPM_EUNSUPPORTED", 8: "MPM_ECFL"}
 
-EXPORTS = ["mpm_create", "mpm_add_particles", "mpm_set_obstacle_mask", "mpm_cfl_dt", "mpm_step",
-           "mpm_step_async", "mpm_sync", "mpm_read_state", "mpm_read_grid_fixed", "mpm_field_size",
-           "mpm_conservation", "mpm_sizes", "mpm_profile", "mpm_profile_read", "mpm_stream",
-           "mpm_last_error", "mpm_destroy", "mpm_sort_keys_static", "mpm_check_fixed_rounding", "mpm_batch_create", "mpm_batch_add",
-           "mpm_batch_remove", "mpm_batch_step_async", "mpm_batch_sync", "mpm_batch_info", "mpm_batch_stream",
-           "mpm_batch_last_error", "mpm_batch_destroy"]
+EXPORTS = ["mpm_create", "mpm_add_particles", "mpm_set_obstacle_mask", "mpm_set_obstacle_profile",
+           "mpm_cfl_dt", "mpm_step", "mpm_step_async", "mpm_sync", "mpm_read_state", "mpm_read_grid_fixed",
+           "mpm_field_size", "mpm_conservation", "mpm_sizes", "mpm_profile", "mpm_profile_read", "mpm_stream",
+           "mpm_last_error", "mpm_destroy", "mpm_sort_keys_static", "mpm_check_fixed_rounding",
+           "mpm_batch_create", "mpm_batch_add", "mpm_batch_remove", "mpm_batch_step_async", "mpm_batch_sync",
+           "mpm_batch_info", "mpm_batch_stream", "mpm_batch_last_error", "mpm_batch_destroy"]
 SORT_STATIC_MAX_KEYS = 262144
 SORT_STATIC_MAX_SPANS = 16777216
 
@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH):
     L.mpm_create.argtypes = [P(mpm_config), P(vp)]
     L.mpm_add_particles.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     L.mpm_set_obstacle_mask.argtypes = [vp, vp, vp]
+    L.mpm_set_obstacle_profile.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     L.mpm_cfl_dt.argtypes = [vp, P(d)]
     L.mpm_step.argtypes = [vp, i64, d, d]
     L.mpm_step_async.argtypes = [vp, i64, d, d]
@@ -255,6 +256,19 @@ def mpm_read_grid_fixed(h, field, dim: int | None = None) -> np.ndarray:
     return out
 
 
+def mpm_set_obstacle_profile(h, loops):
+    loops = [np.asarray(l, dtype=np.float64) for l in loops]
+    lens = np.ascontiguousarray([l.shape[1] for l in loops], dtype=np.int64)
+    pts = np.ascontiguousarray(np.concatenate(loops, axis=1))
+    nn = mpm_field_size(h, FIELDS["GRID_M"])
+    mask = np.empty(nn, dtype=np.uint8)
+    nrm = np.empty(2 * nn)
+    sd = np.empty(nn)
+    _check(load().mpm_set_obstacle_profile(h, len(loops), _ptr(lens), _ptr(pts), _ptr(mask), _ptr(nrm), _ptr(sd)),
+           h)
+    return mask, nrm.reshape(2, nn), sd
+
+
 def mpm_conservation(h) -> np.ndarray:
     out = np.empty(5, dtype=np.float64)
     _check(load().mpm_conservation(h, _ptr(out)), h)
@@ -369,6 +383,8 @@ class Simulation:
         s.add_particles(prob.x, prob.v, prob.mass, prob.rho, prob.e)
         if prob.mask is not None:
             s.set_obstacle_mask(prob.mask, prob.normals)
+        if getattr(prob, "profile", None):
+            s.set_obstacle_profile(prob.profile)
         return s
 
     @property
@@ -380,6 +396,11 @@ class Simulation:
 
     def set_obstacle_mask(self, mask, normals):
         mpm_set_obstacle_mask(self._h, mask, normals)
+
+    def set_obstacle_profile(self, loops):
+        """Obstacle from closed loops of boundary points, each (2, k); returns
+        the installed mask, normals (2, nodes) and the signed distance."""
+        return mpm_set_obstacle_profile(self._h, loops)
 
     def cfl_dt(self) -> float:
         return mpm_cfl_dt(self._h)

@@ -52,6 +52,7 @@ def test_null_handles_are_rejected_without_a_device():
     assert L.mpm_batch_sync(None) == 1
     L.mpm_batch_destroy(None)
     assert L.mpm_check_fixed_rounding(None, None) == 1
+    assert L.mpm_set_obstacle_profile(None, 1, None, None, None, None, None) == 1
 
 
 def test_coloured_mode_rejects_overlapping_colour_windows_without_a_device():
