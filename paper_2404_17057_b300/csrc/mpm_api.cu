@@ -895,17 +895,6 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
     if (s->np + n > (int64_t)0x7FFFFFFF) return fail(s, MPM_EINVAL, "too many particles");
     const Geom& G = s->G;
     const int d = G.dim;
-    for (int64_t k = 0; k < n; ++k) {
-        if (!(mass[k] > 0.0) || !(rho[k] > 0.0) || !std::isfinite(e[k]) || !std::isfinite(mass[k]) ||
-            !std::isfinite(rho[k]))
-            return fail(s, MPM_EINVAL, "mass and rho must be > 0, e finite");
-        for (int a = 0; a < d; ++a) {
-            double xa = x[a * n + k];
-            if (!(xa >= G.lo[a]) || !(xa <= G.hi[a]) || !std::isfinite(v[a * n + k]))
-                return fail(s, MPM_EINVAL, "particle outside the domain or non-finite velocity");
-            if (G.per[a] && !(xa < G.hi[a])) return fail(s, MPM_EINVAL, "periodic axis: x must be < hi");
-        }
-    }
     const int64_t np = s->np + n;
     Buffers nb[2];
     mpm_status st = alloc_particles(s, np, nb);
@@ -926,23 +915,53 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
         CK(cudaMemcpyAsync(nb[0].id, ob.id, s->np * 4, cudaMemcpyDeviceToDevice, S), "copy");
         CK(cudaMemcpyAsync(nb[0].gen, ob.gen, s->np * 4, cudaMemcpyDeviceToDevice, S), "copy");
     }
-    // stage the new doubles on the device and convert to the storage precision
+    // stage the new doubles on the device, check them there and convert them
+    // to the storage precision; stream order keeps the staging buffer safe to
+    // reuse (each copy into it follows the previous array's kernels)
     double* stage = (double*)dalloc(s, (size_t)n * sizeof(double));
-    if (!stage) { free_particles(s, nb); return fail(s, MPM_ENOMEM, "device allocation failed"); }
-    auto up = [&](const double* src, void* dst) -> cudaError_t {
+    unsigned* bad = (unsigned*)dalloc(s, sizeof(unsigned));
+    if (!stage || !bad) {
+        dfree(s, stage);
+        dfree(s, bad);
+        free_particles(s, nb);
+        return fail(s, MPM_ENOMEM, "device allocation failed");
+    }
+    enum { kBadState = 1, kBadPlace = 2, kBadSeam = 4 };
+    // axis >= 0: a position component (inside the domain, below hi on a
+    // periodic axis); otherwise a value checked by `mode` that sets `bit`
+    auto up = [&](const double* src, void* dst, int mode, unsigned bit, int axis) -> cudaError_t {
         cudaError_t r = cudaMemcpyAsync(stage, src, n * sizeof(double), cudaMemcpyHostToDevice, S);
         if (r != cudaSuccess) return r;
+        if (axis < 0) {
+            k_check_values<<<nblk(n), kThreads, 0, S>>>(stage, n, mode, 0.0, 0.0, bit, bad);
+        } else {
+            k_check_values<<<nblk(n), kThreads, 0, S>>>(stage, n, 2, G.lo[axis], G.hi[axis], kBadPlace, bad);
+            if (G.per[axis])
+                k_check_values<<<nblk(n), kThreads, 0, S>>>(stage, n, 3, G.lo[axis], G.hi[axis], kBadSeam, bad);
+        }
         s->vt->from_double(stage, (char*)dst + s->np * rs, n, S);
-        return cudaStreamSynchronize(S);   // the staging buffer is reused
+        return cudaGetLastError();
     };
-    for (int a = 0; a < d; ++a) {
-        CK(up(x + a * n, nb[0].x[a]), "upload x");
-        CK(up(v + a * n, nb[0].v[a]), "upload v");
+    cudaError_t ue = cudaMemsetAsync(bad, 0, sizeof(unsigned), S);
+    for (int a = 0; a < d && ue == cudaSuccess; ++a) {
+        ue = up(x + a * n, nb[0].x[a], 2, kBadPlace, a);
+        if (ue == cudaSuccess) ue = up(v + a * n, nb[0].v[a], 0, kBadPlace, -1);
     }
-    CK(up(mass, nb[0].M), "upload mass");
-    CK(up(rho, nb[0].rho), "upload rho");
-    CK(up(e, nb[0].E), "upload e");
+    if (ue == cudaSuccess) ue = up(mass, nb[0].M, 1, kBadState, -1);
+    if (ue == cudaSuccess) ue = up(rho, nb[0].rho, 1, kBadState, -1);
+    if (ue == cudaSuccess) ue = up(e, nb[0].E, 0, kBadState, -1);
+    unsigned hbad = 0;
+    if (ue == cudaSuccess) ue = cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, S);
+    if (ue == cudaSuccess) ue = cudaStreamSynchronize(S);
     dfree(s, stage);
+    dfree(s, bad);
+    if (ue != cudaSuccess) { free_particles(s, nb); return cuda_fail(s, ue, "upload"); }
+    if (hbad) {
+        free_particles(s, nb);
+        if (hbad & kBadState) return fail(s, MPM_EINVAL, "mass and rho must be > 0, e finite");
+        if (hbad & kBadPlace) return fail(s, MPM_EINVAL, "particle outside the domain or non-finite velocity");
+        return fail(s, MPM_EINVAL, "periodic axis: x must be < hi");
+    }
     CK(cudaMemsetAsync((char*)nb[0].Q + s->np * rs, 0, n * rs, S), "zero q");
     CK(cudaMemsetAsync(nb[0].gen + s->np, 0, n * 4, S), "zero gen");
     k_iota<<<nblk(n), kThreads, 0, S>>>(nb[0].id + s->np, n, (uint32_t)s->np);
@@ -1186,6 +1205,22 @@ static mpm_status read_real(mpm_sim* s, const void* src, int64_t n, double* out)
     if (s->rsize == 8) {
         CK(cudaMemcpyAsync(out, src, n * 8, cudaMemcpyDeviceToHost, s->stream), "read");
         CK(cudaStreamSynchronize(s->stream), "synchronize");
+        return MPM_OK;
+    }
+    // widen on the device and copy straight into the caller's array, in
+    // chunks (stream order protects the staging buffer)
+    const int64_t chunk = std::min<int64_t>(n, (int64_t)1 << 25);
+    double* stage = (double*)dalloc(s, (size_t)chunk * 8);
+    if (stage) {
+        cudaError_t e = cudaSuccess;
+        for (int64_t off = 0; off < n && e == cudaSuccess; off += chunk) {
+            const int64_t m = std::min(chunk, n - off);
+            k_to_double<float><<<nblk(m), kThreads, 0, s->stream>>>((const float*)src + off, stage, m);
+            e = cudaMemcpyAsync(out + off, stage, m * 8, cudaMemcpyDeviceToHost, s->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        dfree(s, stage);
+        CK(e, "read");
         return MPM_OK;
     }
     std::vector<float> t(n);

@@ -1038,6 +1038,31 @@ __global__ void k_from_double(const double* in, R* out, int64_t n)
     if (i < n) out[i] = (R)in[i];
 }
 
+template <class R>
+__global__ void k_to_double(const R* in, double* out, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)in[i];
+}
+
+// Checks of uploaded particle values; sets `bit` in *bad when one fails.
+// mode 0: finite; 1: finite and > 0; 2: lo <= v <= hi; 3: lo <= v < hi.
+__global__ void k_check_values(const double* in, int64_t n, int mode, double lo, double hi, unsigned bit,
+                               unsigned* bad)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = in[i];
+    bool ok;
+    switch (mode) {
+    case 0: ok = isfinite(v); break;
+    case 1: ok = isfinite(v) && v > 0.0; break;
+    case 2: ok = v >= lo && v <= hi; break;
+    default: ok = v >= lo && v < hi; break;
+    }
+    if (!ok) atomicOr(bad, bit);
+}
+
 __global__ void k_iota(uint32_t* out, int64_t n, uint32_t base)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -236,10 +236,14 @@ def mpm_field_size(h, field) -> int:
     return int(load().mpm_field_size(h, f))
 
 
-def mpm_read_state(h, field, dim: int | None = None) -> np.ndarray:
+def mpm_read_state(h, field, dim: int | None = None, out: np.ndarray | None = None) -> np.ndarray:
     f = FIELDS[field] if isinstance(field, str) else int(field)
     n = mpm_field_size(h, f)
-    out = np.empty(max(n, 0), dtype=np.float64)
+    if out is None:
+        out = np.empty(max(n, 0), dtype=np.float64)
+    elif out.dtype != np.float64 or not out.flags.c_contiguous or out.size < n:
+        raise ValueError("out must be a contiguous float64 array of the field's size")
+    out = out.reshape(-1)[:max(n, 0)]
     _check(load().mpm_read_state(h, f, _ptr(out), n), h)
     if dim and field in ("X", "V", "GRID_MV", "GRID_F", "GRID_MV2"):
         out = out.reshape(dim, -1)
@@ -414,8 +418,10 @@ class Simulation:
     def sync(self):
         mpm_sync(self._h)
 
-    def read(self, field: str) -> np.ndarray:
-        return mpm_read_state(self._h, field, self.dim)
+    def read(self, field: str, out: np.ndarray | None = None) -> np.ndarray:
+        """Field values as float64; `out` (optional) receives them, e.g. a
+        page-locked array for a faster device-to-host copy."""
+        return mpm_read_state(self._h, field, self.dim, out)
 
     def read_fixed(self, field: str) -> np.ndarray:
         return mpm_read_grid_fixed(self._h, field, self.dim)

@@ -410,6 +410,27 @@ def test_errors_are_status_codes():
     g.close()
 
 
+def test_add_particles_checks_every_value_on_the_device():
+    p = I.shock_tube(ncell=32, ny=4, precision="fp32")   # periodic in y: y < 4h
+    g = M.Simulation(p.cfg)
+    hy = 4 * p.cfg["h"]
+    ok = dict(x=np.array([[0.3, 0.6], [0.01, 0.02]]), v=np.zeros((2, 2)), m=np.ones(2), r=np.ones(2), e=np.ones(2))
+    cases = [("x", (0, 1), 1.5, "outside the domain"), ("v", (1, 0), np.nan, "non-finite velocity"),
+             ("m", (1,), 0.0, "mass and rho"), ("r", (0,), -1.0, "mass and rho"), ("e", (1,), np.inf, "e finite"),
+             ("x", (1, 1), hy, "periodic axis")]
+    for key, idx, val, msg in cases:
+        arr = {k: a.copy() for k, a in ok.items()}
+        arr[key][idx] = val
+        with pytest.raises(M.MPMError) as e:
+            g.add_particles(arr["x"], arr["v"], arr["m"], arr["r"], arr["e"])
+        assert e.value.status == "MPM_EINVAL" and msg in str(e.value), (key, str(e.value))
+    # rejected calls leave the simulation as it was
+    g.add_particles(ok["x"], ok["v"], ok["m"], ok["r"], ok["e"])
+    assert g.sizes()["particles"] == 2
+    assert np.array_equal(np.sort(g.read("X")[0]), np.float32(ok["x"][0]).astype(np.float64))
+    g.close()
+
+
 def test_short_output_buffer_rejected():
     import ctypes
     p = I.shock_tube(ncell=16, ny=4)
