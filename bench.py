@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--config", default="blast", choices=["blast", "cylinder"])
     ap.add_argument("--n", type=int, default=0, help="override the grid size (cells per axis / x cells)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_coloured", "fp32_fixed64", "fp64"])
+    ap.add_argument("--degree", type=int, default=2, choices=[1, 2], help="basis: 1 = Q1, 2 = quadratic B-spline")
+    ap.add_argument("--ppa", type=int, default=2, help="particles per cell along each axis")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", type=int, default=0,
                     help="also run the serving stream with this many requests (batched vs one at a time)")
@@ -60,20 +62,33 @@ def parse():
     return ap.parse_args()
 
 
-def problem(args):
-    from paper_2404_17057_b300 import inputs as I
+def workload(args):
+    """The workload's description, from the arguments alone (both arms)."""
+    basis = "quadratic B-spline" if args.degree == 2 else "Q1"
     if args.config == "blast":
         n = args.n or 256
-        p = I.blast(n=n, precision=args.precision)
-        wl = f"3D blast wave {n}^3 cells, 8 ppc, quadratic B-spline, {args.precision}"
-        cfg = {"workload": wl, "cells": [n, n, n], "particles": p.n_particles, "degree": 2,
-               "precision": args.precision, "l2": "inputs larger than L2 (no flush)"}
+        ppc = args.ppa ** 3
+        return {"workload": f"3D blast wave {n}^3 cells, {ppc} ppc, {basis}, {args.precision}",
+                "cells": [n, n, n], "ppc": ppc, "degree": args.degree, "precision": args.precision}
+    nx = args.n or 1024
+    ppc = args.ppa ** 2
+    return {"workload": f"2D Mach-3 cylinder {nx}x{nx // 2} cells, {ppc} ppc, {basis}, {args.precision}",
+            "cells": [nx, nx // 2], "ppc": ppc, "degree": args.degree, "precision": args.precision}
+
+
+def problem(args):
+    from paper_2404_17057_b300 import inputs as I
+    cfg = workload(args)
+    if args.config == "blast":
+        n = cfg["cells"][0]
+        p = I.blast(n=n, ppa=args.ppa, degree=args.degree, precision=args.precision)
+        cfg["l2"] = "inputs larger than L2 (no flush)"
     else:
-        nx = args.n or 1024
-        p = I.cylinder(nx=nx, ny=nx // 2, precision=args.precision)
-        wl = f"2D Mach-3 cylinder {nx}x{nx // 2} cells, 4 ppc, quadratic B-spline, {args.precision}"
-        cfg = {"workload": wl, "cells": [nx, nx // 2], "particles": p.n_particles, "degree": 2,
-               "precision": args.precision, "l2": "particle state partly L2-resident"}
+        nx, ny = cfg["cells"]
+        p = I.cylinder(nx=nx, ny=ny, ppa=args.ppa, degree=args.degree, precision=args.precision)
+        cfg["l2"] = ("inputs larger than L2 (no flush)" if p.n_particles * 40 > 126e6
+                     else "particle state partly L2-resident")
+    cfg["particles"] = p.n_particles
     return p, cfg
 
 
@@ -159,7 +174,7 @@ class ClockSampler:
 # moves 8x those bytes.  Valid only for the kernel sources with this digest.
 MEASURED_TRAFFIC = {
     "sources": "98971463225b80c0",
-    "config": ("blast", 3, 2, "fp32"),
+    "config": ("blast", 3, 2, "fp32", 2),
     "bytes_per_particle": {"p2g": 49.53, "grid_g2p": 44.89, "g2pd": 55.05, "reorder": 92.91},
 }
 
@@ -173,11 +188,11 @@ def sources_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str, config: str, dim: int, degree: int, precision: str, n_p: int):
+def measured_traffic(kernel: str, config: str, dim: int, degree: int, precision: str, ppa: int, n_p: int):
     """DRAM bytes of one launch of `kernel`, or None when the counters were
     taken on other kernel sources or another kind of workload."""
     t = MEASURED_TRAFFIC
-    if t["config"] != (config, dim, degree, precision) or sources_digest() != t["sources"]:
+    if t["config"] != (config, dim, degree, precision, ppa) or sources_digest() != t["sources"]:
         return None
     return t["bytes_per_particle"][kernel] * n_p
 
@@ -197,12 +212,14 @@ def cpu_baseline(args, cfg_meta, seconds_budget=20.0):
     from paper_2404_17057_b300 import inputs as I
     if args.config == "blast":
         n = 32
-        p = I.blast(n=n, precision="fp64")
-        sample = f"blast {n}^3 cells (8 ppc, {p.n_particles} particles), same ppc/basis, FP64 oracle"
+        p = I.blast(n=n, ppa=args.ppa, degree=args.degree, precision="fp64")
+        sample = (f"blast {n}^3 cells ({args.ppa ** 3} ppc, {p.n_particles} particles), same ppc/basis, "
+                  f"FP64 oracle")
     else:
         n = 128
-        p = I.cylinder(nx=n, ny=n // 2, precision="fp64")
-        sample = f"cylinder {n}x{n // 2} cells ({p.n_particles} particles), FP64 oracle"
+        p = I.cylinder(nx=n, ny=n // 2, ppa=args.ppa, degree=args.degree, precision="fp64")
+        sample = (f"cylinder {n}x{n // 2} cells ({args.ppa ** 2} ppc, {p.n_particles} particles), same "
+                  f"ppc/basis, FP64 oracle")
     s = O.OracleSim(p.cfg)
     s.add_particles(p.x, p.v, p.mass, p.rho, p.e)
     if p.mask is not None:
@@ -224,7 +241,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    _, meta = problem_meta_only(args)
+    meta = workload(args)
     cb = cpu_baseline(args, meta, seconds_budget=max(5.0, min(60.0, 3.0 * (args.steps + args.warmup))))
     line = {"impl": "reference", "metric": "particle-steps/s", "value": cb["value"], "unit": "particle-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
@@ -233,16 +250,6 @@ def run_reference(args):
             "e2e": {"value": cb["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def problem_meta_only(args):
-    if args.config == "blast":
-        n = args.n or 256
-        return None, {"workload": f"3D blast wave {n}^3 cells, 8 ppc, quadratic B-spline, {args.precision}",
-                      "cells": [n, n, n], "particles": 8 * n ** 3}
-    nx = args.n or 1024
-    return None, {"workload": f"2D Mach-3 cylinder {nx}x{nx // 2} cells, 4 ppc, quadratic B-spline",
-                  "cells": [nx, nx // 2]}
 
 
 def serving(args):
@@ -363,6 +370,7 @@ def main():
     sim = M.Simulation.from_problem(p)
     st = torch.cuda.ExternalStream(sim.stream)
     sim.step(args.warmup)
+    t_sim0 = float(sim.read("CLOCK")[0])
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
@@ -379,6 +387,7 @@ def main():
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    t_sim1 = float(sim.read("CLOCK")[0])
     if dist:
         dist.barrier()
     # per-phase device times: the same steps again with events between phases
@@ -421,7 +430,8 @@ def main():
         "data": "synthetic", "config": meta,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
                      "frac": ach / hbm, "peak_source": which,
-                     "traffic": measured_traffic(dom, args.config, dim, int(p.cfg["degree"]), args.precision, n_p),
+                     "traffic": measured_traffic(dom, args.config, dim, int(p.cfg["degree"]), args.precision,
+                                                 args.ppa, n_p),
                      "k1_k2_k3_gbs": k123_gbs, "k1_k2_k3_frac": k123_gbs / hbm,
                      "k1_k2_k3_frac_nominal_7.7TB": k123_gbs / NOMINAL_HBM},
         "phase_ms_per_step": {"p2g": per_launch_ms["p2g"], "grid_g2p": per_launch_ms["grid_g2p"],
@@ -430,6 +440,10 @@ def main():
         "algorithmic_bytes": alg,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": ck,
+        # physical time the timed steps advanced (CFL steps), and the device
+        # time per simulated second (the paper's wall-time figure, Sec. 4.3)
+        "sim_time": {"simulated_s": t_sim1 - t_sim0,
+                     "device_s_per_simulated_s": (ms / 1e3) / (t_sim1 - t_sim0) if t_sim1 > t_sim0 else None},
         "e2e": e2e,
         "cpu_baseline": cb,
     }
