@@ -224,9 +224,14 @@ struct Impl {
     // G2PD reads the grid once into its window, so the fixed-point mode runs
     // the single-precision kernel too (the int64 sums are converted there)
     static constexpr bool kFast3 = std::is_same<R, float>::value;
-    // 2D fixed point: P2G and grid + G2P + P2G by the span-per-lane int64 kernels
-    static constexpr bool kFixed1 = D == 2 && std::is_same<R, float>::value && std::is_same<A, long long>::value;
-    static_assert(!(kFixed1 && kFast), "one P2G kernel per mode");
+    // 2D fixed point and FP64: P2G and grid + G2P + P2G by the span-per-lane
+    // kernels with 64-bit register sums
+    static constexpr bool kSpan2d = D == 2 && ((std::is_same<R, float>::value && std::is_same<A, long long>::value) ||
+                                               (std::is_same<R, double>::value && std::is_same<A, double>::value));
+    static_assert(!(kSpan2d && kFast), "one P2G kernel per mode");
+    // ... on grids of at least two tiles per SM; smaller grids keep the
+    // particle-parallel generic kernels, whose 256 threads finish a tile sooner
+    static bool span2d(const Geom& G) { return G.ntiles >= 2 * 148; }
     static size_t smem(const Geom& G, int kernel)
     {
         const size_t W = (size_t)G.Wvol;
@@ -268,9 +273,9 @@ struct Impl {
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
             return cudaSuccess;
         } else {
-            if constexpr (kFixed1) {
-                if ((e = allow((const void*)k_p2g_fixed<P>, smem(G, 0))) != cudaSuccess) return e;
-                return allow((const void*)k_grid_g2p_fixed<P>, smem(G, 1));
+            if constexpr (kSpan2d) {
+                if ((e = allow((const void*)k_p2g_span2d<P, R, A>, smem(G, 0))) != cudaSuccess) return e;
+                if ((e = allow((const void*)k_grid_g2p_span2d<P, R, A>, smem(G, 1))) != cudaSuccess) return e;
             }
             if ((e = allow((const void*)k_p2g<D, P, R, A>, smem(G, 0))) != cudaSuccess) return e;
             return allow((const void*)k_grid_g2p<D, P, R, A>, smem(G, 1));
@@ -298,8 +303,8 @@ struct Impl {
                     else k_p2g_span<D, P, false><<<nb, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk, tl);
                 }
                 s->launches += ncolours(s) - 1;
-            } else if constexpr (kFixed1) {
-                k_p2g_fixed<P><<<G.ntiles, kP2GFixedThreads, smem(G, 0), st>>>(G, pt, gr, cs, s->clk);
+            } else if (kSpan2d && span2d(G)) {
+                k_p2g_span2d<P, R, A><<<G.ntiles, kP2GSpan2dThreads, smem(G, 0), st>>>(G, pt, gr, cs, s->clk);
             } else {
                 k_p2g<D, P, R, A><<<G.ntiles, kThreads, smem(G, 0), st>>>(G, pt, gr, cs, s->clk);
             }
@@ -321,8 +326,8 @@ struct Impl {
                                                                                                  s->clk, tl);
                 }
                 s->launches += ncolours(s) - 1;
-            } else if constexpr (kFixed1) {
-                k_grid_g2p_fixed<P><<<G.ntiles, kG2PFixedThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
+            } else if (kSpan2d && span2d(G)) {
+                k_grid_g2p_span2d<P, R, A><<<G.ntiles, kG2PSpan2dThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
             } else {
                 k_grid_g2p<D, P, R, A><<<G.ntiles, kThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
             }
@@ -402,9 +407,9 @@ struct Impl {
                 if (per) kb_grid_g2p_span<D, P, true><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
                 else kb_grid_g2p_span<D, P, false><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
             }
-        } else if constexpr (kFixed1) {
-            if (stage == 0) kb_p2g_fixed<P><<<ntl, kP2GFixedThreads, sm, st>>>(d, tl);
-            else kb_grid_g2p_fixed<P><<<ntl, kG2PFixedThreads, sm, st>>>(d, tl);
+        } else if constexpr (kSpan2d) {
+            if (stage == 0) kb_p2g_span2d<P, R, A><<<ntl, kP2GSpan2dThreads, sm, st>>>(d, tl);
+            else kb_grid_g2p_span2d<P, R, A><<<ntl, kG2PSpan2dThreads, sm, st>>>(d, tl);
         } else {
             if (stage == 0) kb_p2g<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
             else kb_grid_g2p<D, P, R, A><<<ntl, kThreads, sm, st>>>(d, tl);
@@ -440,9 +445,9 @@ struct Impl {
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
             return cudaSuccess;
         } else {
-            if constexpr (kFixed1) {
-                if ((e = allow((const void*)kb_p2g_fixed<P>, sm[0])) != cudaSuccess) return e;
-                return allow((const void*)kb_grid_g2p_fixed<P>, sm[1]);
+            if constexpr (kSpan2d) {
+                if ((e = allow((const void*)kb_p2g_span2d<P, R, A>, sm[0])) != cudaSuccess) return e;
+                return allow((const void*)kb_grid_g2p_span2d<P, R, A>, sm[1]);
             }
             if ((e = allow((const void*)kb_p2g<D, P, R, A>, sm[0])) != cudaSuccess) return e;
             return allow((const void*)kb_grid_g2p<D, P, R, A>, sm[1]);

@@ -157,20 +157,20 @@ __global__ void __launch_bounds__(kP2GThreads, 6) kb_p2g_span(const BatchProb<fl
     p2g_span_tile<D, P, PER>(p.G, p.pt[par], p.p2g_out, p.cs[par], p.clk, r.tile);
 }
 
-template <int P>
-__global__ void __launch_bounds__(kP2GFixedThreads, 6) kb_p2g_fixed(const BatchProb<float, long long>* __restrict__ bp,
-                                                                    const TileRef* __restrict__ tl)
+template <int P, class R, class A>
+__global__ void __launch_bounds__(kP2GSpan2dThreads, 6) kb_p2g_span2d(const BatchProb<R, A>* __restrict__ bp,
+                                                                      const TileRef* __restrict__ tl)
 {
-    MPM_BATCH_PROLOGUE(float, long long)
-    p2g_fixed_tile<P>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, r.tile);
+    MPM_BATCH_PROLOGUE(R, A)
+    p2g_span2d_tile<P, R, A>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, r.tile);
 }
 
-template <int P>
-__global__ void __launch_bounds__(kG2PFixedThreads, 4)
-    kb_grid_g2p_fixed(const BatchProb<float, long long>* __restrict__ bp, const TileRef* __restrict__ tl)
+template <int P, class R, class A>
+__global__ void __launch_bounds__(kG2PSpan2dThreads, 4)
+    kb_grid_g2p_span2d(const BatchProb<R, A>* __restrict__ bp, const TileRef* __restrict__ tl)
 {
-    MPM_BATCH_PROLOGUE(float, long long)
-    grid_g2p_fixed_tile<P>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, r.tile);
+    MPM_BATCH_PROLOGUE(R, A)
+    grid_g2p_span2d_tile<P, R, A>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, r.tile);
 }
 
 template <int D, int P, bool PER>

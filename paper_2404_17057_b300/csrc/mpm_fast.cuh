@@ -79,6 +79,12 @@ __device__ __forceinline__ void sh_add(float* p, float v)
     else *p += v;
 }
 template <bool ATOMIC>
+__device__ __forceinline__ void sh_add(double* p, double v)
+{
+    if constexpr (ATOMIC) atomicAdd(p, v);
+    else *p += v;
+}
+template <bool ATOMIC>
 __device__ __forceinline__ void sh_add(long long* p, long long v)
 {
     if constexpr (ATOMIC) atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
@@ -387,58 +393,60 @@ __global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, Particles<f
     p2g_span_tile<D, P, PER>(G, pt, out, cs, clk, tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x);
 }
 
-// -------------------------------------------- K1, fixed point (2D)
+// ------------------------------- 2D span-per-lane kernels, 64-bit sums
 //
-// The P2G of the fixed-point mode with the span-per-lane layout of K1: each
-// contribution is formed exactly as in the generic kernel (same weights,
-// same binary32 order, quantised with the same rounding), so the int64 sums
-// -- exact and order independent -- are bit-identical to it.  A lane sums
-// its span's quanta in registers; warp 0 owns {m, M V_x, M V_y}, warp 1
-// {f_x, f_y}; each completed row goes into an int64 window (x-neighbours
-// summed by shuffles first), which is added to the grid once per node.
+// P2G and grid + G2P + P2G of the 2D fixed-point and FP64 modes in the
+// span-per-lane layout of K1: a lane takes the particles of its span one by
+// one and sums their contributions to the span's (p+1)^2 support nodes in
+// registers (int64 quanta, or binary64); each completed row of 32 spans goes
+// into a shared window (x-neighbours summed by shuffles first), which is added
+// to the grid once per node.  Every contribution is formed exactly as in the
+// generic kernels (same weights, same operation order); fixed-point sums are
+// exact and order independent, so they are bit-identical to the generic
+// kernel's.  Registers bound this layout to two dimensions (3D needs
+// 4 x 27 64-bit sums per lane); 3D keeps the generic kernels.
 //
-// Rounding to int64 costs about as much as the rest of the kernel, so a
-// particle whose every quantised contribution is bounded by 2^31 in
-// magnitude (checked from its largest weight, with a factor 2 margin for the
-// roundings) takes the 32-bit conversion, which is exact there; the others
-// take the 64-bit one.
+// Fixed point: rounding to int64 costs about as much as the rest of the
+// kernel, so a particle whose every quantised contribution is bounded by 2^31
+// in magnitude (checked from its largest weight, with a factor 2 margin for
+// the roundings) takes the 32-bit conversion, which is exact there; the
+// others take the 64-bit one.
 
-// One particle's quanta into the lane sums: group 0 {M w, M V_x w, M V_y w}
-// (a = {M, M V_x, M V_y}), group 1 {F g_x, F g_y} (a[0] = F).
-template <int P, int GROUP, bool SMALL>
-__device__ __forceinline__ void fixed_contribs(const Geom& G, const AxisSup<float>* sx, const float* a,
-                                               long long (&q)[GROUP == 0 ? 3 : 2][(P + 1) * (P + 1)])
+// One particle's contributions into the lane sums: group 0 {M w, M V_x w,
+// M V_y w} (a = {M, M V_x, M V_y}), group 1 {F g_x, F g_y} (a[0] = F).
+template <int P, int GROUP, bool SMALL, class R, class A>
+__device__ __forceinline__ void span2d_contribs(const Geom& G, const AxisSup<R>* sx, const R* a,
+                                                A (&q)[GROUP == 0 ? 3 : 2][(P + 1) * (P + 1)])
 {
-    typedef Op<float> O;
+    typedef Op<R> O;
     constexpr int NS = P + 1;
 #pragma unroll
     for (int ky = 0; ky < NS; ++ky)
 #pragma unroll
         for (int kx = 0; kx < NS; ++kx) {
-            float w, g[3];
-            node_weights<float, 2>(sx, kx, ky, 0, w, g);
+            R w, g[3];
+            node_weights<R, 2>(sx, kx, ky, 0, w, g);
             const int i = ky * NS + kx;
             if constexpr (GROUP == 0) {
-                q[0][i] += Acc<long long>::from_t<SMALL>(O::mul(a[0], w), G.qscale[0]);
-                q[1][i] += Acc<long long>::from_t<SMALL>(O::mul(a[1], w), G.qscale[1]);
-                q[2][i] += Acc<long long>::from_t<SMALL>(O::mul(a[2], w), G.qscale[1]);
+                q[0][i] += Acc<A>::template from_t<SMALL>(O::mul(a[0], w), G.qscale[0]);
+                q[1][i] += Acc<A>::template from_t<SMALL>(O::mul(a[1], w), G.qscale[1]);
+                q[2][i] += Acc<A>::template from_t<SMALL>(O::mul(a[2], w), G.qscale[1]);
             } else {
-                q[0][i] += Acc<long long>::from_t<SMALL>(O::mul(a[0], g[0]), G.qscale[2]);
-                q[1][i] += Acc<long long>::from_t<SMALL>(O::mul(a[0], g[1]), G.qscale[2]);
+                q[0][i] += Acc<A>::template from_t<SMALL>(O::mul(a[0], g[0]), G.qscale[2]);
+                q[1][i] += Acc<A>::template from_t<SMALL>(O::mul(a[0], g[1]), G.qscale[2]);
             }
         }
 }
 
-template <int P, int GROUP>
-__device__ __forceinline__ int p2g_fixed_group(const Geom& G, const Particles<float>& pt,
-                                               const uint32_t* __restrict__ cs, int64_t kb, const int so[3],
-                                               long long* win)
+template <int P, int GROUP, class R, class A>
+__device__ __forceinline__ int p2g_span2d_group(const Geom& G, const Particles<R>& pt,
+                                                const uint32_t* __restrict__ cs, int64_t kb, const int so[3], A* win)
 {
-    typedef Op<float> O;
+    typedef Op<R> O;
     constexpr int NS = P + 1, NN = NS * NS, NQ = GROUP == 0 ? 3 : 2;
     const int W = G.Wvol, W0 = G.W[0];
     const int lane = threadIdx.x & 31;
-    const float gm1 = (float)(G.gamma - 1.0), ih = (float)G.inv_h;
+    const R gm1 = (R)(G.gamma - 1.0), ih = (R)G.inv_h;
     const int nrows = G.Tvol >> 5;
     const int tseg = G.T[0] < 32 ? G.T[0] : 32;
     const int lxw = lane & (tseg - 1);
@@ -449,139 +457,139 @@ __device__ __forceinline__ int p2g_fixed_group(const Geom& G, const Particles<fl
         const int lx = s & (G.T[0] - 1);
         const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
         if (__all_sync(0xffffffffu, b == e)) continue;
-        long long q[NQ][NN];
+        A q[NQ][NN];
 #pragma unroll
         for (int f = 0; f < NQ; ++f)
 #pragma unroll
-            for (int i = 0; i < NN; ++i) q[f][i] = 0;
+            for (int i = 0; i < NN; ++i) q[f][i] = A(0);
         for (uint32_t k = b; k < e; ++k) {
-            AxisSup<float> sx[3];
-            axis_support<float, P>(G, 0, pt.x[0][k], so[0], sx[0]);
-            axis_support<float, P>(G, 1, pt.x[1][k], so[1], sx[1]);
+            AxisSup<R> sx[3];
+            axis_support<R, P>(G, 0, pt.x[0][k], so[0], sx[0]);
+            axis_support<R, P>(G, 1, pt.x[1][k], so[1], sx[1]);
             if (sx[0].l != lx || sx[1].l != ly) { err = 1; continue; }
             sx[2].l = 0;
-            sx[2].w[0] = 1.f;
-            sx[2].dw[0] = 0.f;
-            float wm0, dm0, wm1, dm1;
-            axis_bounds<NS>(sx[0], wm0, dm0);
-            axis_bounds<NS>(sx[1], wm1, dm1);
-            const float M = pt.M[k];
-            float a[3];
-            bool small;
+            sx[2].w[0] = (R)1;
+            sx[2].dw[0] = (R)0;
+            const R M = pt.M[k];
+            R a[3];
             if constexpr (GROUP == 0) {
                 a[0] = M;
                 a[1] = O::mul(M, pt.v[0][k]);
                 a[2] = O::mul(M, pt.v[1][k]);
-                // NaN or infinity fails every comparison: full rounding
-                const float wb = wm0 * wm1;
-                small = (M * G.qscale[0] * wb < kSmallQuanta) & (fabsf(a[1]) * G.qscale[1] * wb < kSmallQuanta) &
-                        (fabsf(a[2]) * G.qscale[1] * wb < kSmallQuanta);
             } else {
-                const float rho = pt.rho[k];
-                const float Pk = O::mul(O::mul(gm1, rho), pt.E[k]);
-                const float vol = O::dvd(M, rho);
+                const R rho = pt.rho[k];
+                const R Pk = O::mul(O::mul(gm1, rho), pt.E[k]);
+                const R vol = O::dvd(M, rho);
                 a[0] = O::mul(O::mul(O::add(Pk, pt.Q[k]), vol), ih);
-                a[1] = a[2] = 0.f;
-                const float gb = fmaxf(dm0 * wm1, wm0 * dm1);
-                small = fabsf(a[0]) * G.qscale[2] * gb < kSmallQuanta;
+                a[1] = a[2] = (R)0;
             }
-            if (small) fixed_contribs<P, GROUP, true>(G, sx, a, q);
-            else fixed_contribs<P, GROUP, false>(G, sx, a, q);
+            bool small = false;
+            if constexpr (Acc<A>::kFixed) {
+                R wm0, dm0, wm1, dm1;
+                axis_bounds<NS>(sx[0], wm0, dm0);
+                axis_bounds<NS>(sx[1], wm1, dm1);
+                // NaN or infinity fails every comparison: full rounding
+                if constexpr (GROUP == 0) {
+                    const R wb = wm0 * wm1;
+                    small = (M * G.qscale[0] * wb < kSmallQuanta) &
+                            (fabs(a[1]) * G.qscale[1] * wb < kSmallQuanta) &
+                            (fabs(a[2]) * G.qscale[1] * wb < kSmallQuanta);
+                } else {
+                    small = fabs(a[0]) * G.qscale[2] * fmax(dm0 * wm1, wm0 * dm1) < kSmallQuanta;
+                }
+            }
+            if (small) span2d_contribs<P, GROUP, true>(G, sx, a, q);
+            else span2d_contribs<P, GROUP, false>(G, sx, a, q);
         }
         const int base = ly * W0 + lx - lxw;
 #pragma unroll
         for (int ky = 0; ky < NS; ++ky) {
 #pragma unroll
             for (int f = 0; f < NQ; ++f) {
-                long long v[NS];
+                A v[NS];
 #pragma unroll
                 for (int c = 0; c < NS; ++c) v[c] = q[f][ky * NS + c];
                 // window fields: 0 m, 1 M V_x, 2 M V_y, 3 f_x, 4 f_y
-                xrow_rmw<NS, long long>(win + ((GROUP == 0 ? 0 : 3) + f) * W + base + ky * W0, v, lxw, tseg);
+                xrow_rmw<NS, A>(win + ((GROUP == 0 ? 0 : 3) + f) * W + base + ky * W0, v, lxw, tseg);
             }
         }
     }
     return err;
 }
 
-template <int P>
-__device__ __forceinline__ void p2g_fixed_tile(const Geom& G, const Particles<float>& pt,
-                                               const Grid<long long, float>& gr, const uint32_t* __restrict__ cs,
-                                               Clock* clk, const int tile)
+template <int P, class R, class A>
+__device__ __forceinline__ void p2g_span2d_tile(const Geom& G, const Particles<R>& pt, const Grid<A, R>& gr,
+                                                const uint32_t* __restrict__ cs, Clock* clk, const int tile)
 {
     if (!clk->active) return;
     const int64_t kb = (int64_t)tile * G.Tvol;
     if (cs[kb] == cs[kb + G.Tvol]) return;
-    extern __shared__ __align__(16) long long swin[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    A* swin = reinterpret_cast<A*>(smem_raw);
     constexpr int NF = 5;
     const int W = G.Wvol;
-    for (int i = threadIdx.x; i < NF * W; i += blockDim.x) swin[i] = 0;
+    for (int i = threadIdx.x; i < NF * W; i += blockDim.x) swin[i] = A(0);
     __syncthreads();
     int so[3];
     tile_origin(G, tile, so);
     // each warp is the only writer of its fields of the window
-    const int err = (threadIdx.x >> 5) == 0 ? p2g_fixed_group<P, 0>(G, pt, cs, kb, so, swin)
-                                            : p2g_fixed_group<P, 1>(G, pt, cs, kb, so, swin);
+    const int err = (threadIdx.x >> 5) == 0 ? p2g_span2d_group<P, 0>(G, pt, cs, kb, so, swin)
+                                            : p2g_span2d_group<P, 1>(G, pt, cs, kb, so, swin);
     if (err) atomicOr(&clk->err, ERR_TILE);
     __syncthreads();
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         int idx[3];
         const int64_t node = slot_node<P>(G, so, i, idx);
         if (node < 0) continue;
-        long long* dst[NF] = {gr.m, gr.mv[0], gr.mv[1], gr.f[0], gr.f[1]};
+        A* dst[NF] = {gr.m, gr.mv[0], gr.mv[1], gr.f[0], gr.f[1]};
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            const long long v = swin[f * W + i];
-            if (v != 0) Acc<long long>::add(dst[f] + node, v);
+            const A v = swin[f * W + i];
+            if (v != A(0)) Acc<A>::add(dst[f] + node, v);
         }
     }
 }
 
-constexpr int kP2GFixedThreads = 64;
+constexpr int kP2GSpan2dThreads = 64;
 
-template <int P>
-__global__ void __launch_bounds__(kP2GFixedThreads, 8) k_p2g_fixed(Geom G, Particles<float> pt,
-                                                                   Grid<long long, float> gr,
-                                                                   const uint32_t* __restrict__ cs, Clock* clk)
+template <int P, class R, class A>
+__global__ void __launch_bounds__(kP2GSpan2dThreads, 8) k_p2g_span2d(Geom G, Particles<R> pt, Grid<A, R> gr,
+                                                                     const uint32_t* __restrict__ cs, Clock* clk)
 {
-    p2g_fixed_tile<P>(G, pt, gr, cs, clk, blockIdx.x);
+    p2g_span2d_tile<P, R, A>(G, pt, gr, cs, clk, blockIdx.x);
 }
 
-// -------------------------------- K2, fixed point (2D): grid + G2P + P2G
-//
-// The generic kernel's arithmetic in the span-per-lane layout: the tile's
-// acceleration window is built as there; a lane then takes the particles of
-// its span one by one -- G2P sum in the same node order, V' written back,
-// M V' quantised into int64 register sums for the span's support nodes --
-// and each warp adds its completed rows into the shared int64 window (with
-// shared atomics: the rows of different warps overlap in y), which is added
-// to the grid once per node.
-constexpr int kG2PFixedThreads = 128;
+// Grid update + G2P + P2G: the acceleration window is built as in the
+// generic kernel; a lane then takes the particles of its span one by one --
+// G2P sum in the generic node order, V' written back, M V' into 64-bit
+// register sums for the span's support nodes -- and each warp adds its
+// completed rows into the shared window with shared atomics (the rows of
+// different warps overlap in y).
+constexpr int kG2PSpan2dThreads = 128;
 
-template <int P>
-__device__ __forceinline__ void grid_g2p_fixed_tile(const Geom& G, const Particles<float>& pt,
-                                                    const Grid<long long, float>& gr,
-                                                    const uint32_t* __restrict__ cs, Clock* clk, const int tile)
+template <int P, class R, class A>
+__device__ __forceinline__ void grid_g2p_span2d_tile(const Geom& G, const Particles<R>& pt, const Grid<A, R>& gr,
+                                                     const uint32_t* __restrict__ cs, Clock* clk, const int tile)
 {
-    typedef Op<float> O;
+    typedef Op<R> O;
     if (!clk->active) return;
     const int64_t kb = (int64_t)tile * G.Tvol;
     if (cs[kb] == cs[kb + G.Tvol]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int W = G.Wvol, W0 = G.W[0];
-    float* sA = reinterpret_cast<float*>(smem_raw);
-    long long* s2 = reinterpret_cast<long long*>(smem_raw + ((sizeof(float) * 2 * W + 15) & ~size_t(15)));
+    R* sA = reinterpret_cast<R*>(smem_raw);
+    A* s2 = reinterpret_cast<A*>(smem_raw + ((sizeof(R) * 2 * W + 15) & ~size_t(15)));
     int so[3];
     tile_origin(G, tile, so);
-    accel_window<2, P, float, long long>(G, gr, so, sA, s2);
+    accel_window<2, P, R, A>(G, gr, so, sA, s2);
     __syncthreads();
     constexpr int NS = P + 1, NN = NS * NS;
-    const float dt = (float)clk->dt_cur;
+    const R dt = (R)clk->dt_cur;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int nrows = G.Tvol >> 5;
     const int tseg = G.T[0] < 32 ? G.T[0] : 32;
     const int lxw = lane & (tseg - 1);
-    float vmax = 0.f;
+    R vmax = (R)0;
     int err = 0;
     for (int r = warp; r < nrows; r += nwarps) {
         const int s = (r << 5) + lane;
@@ -589,57 +597,60 @@ __device__ __forceinline__ void grid_g2p_fixed_tile(const Geom& G, const Particl
         const int lx = s & (G.T[0] - 1);
         const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
         if (__all_sync(0xffffffffu, b == e)) continue;
-        long long q[2][NN];
+        A q[2][NN];
 #pragma unroll
         for (int f = 0; f < 2; ++f)
 #pragma unroll
-            for (int i = 0; i < NN; ++i) q[f][i] = 0;
+            for (int i = 0; i < NN; ++i) q[f][i] = A(0);
         for (uint32_t k = b; k < e; ++k) {
-            AxisSup<float> sx[3];
-            axis_support<float, P>(G, 0, pt.x[0][k], so[0], sx[0]);
-            axis_support<float, P>(G, 1, pt.x[1][k], so[1], sx[1]);
+            AxisSup<R> sx[3];
+            axis_support<R, P>(G, 0, pt.x[0][k], so[0], sx[0]);
+            axis_support<R, P>(G, 1, pt.x[1][k], so[1], sx[1]);
             if (sx[0].l != lx || sx[1].l != ly) { err = 1; continue; }
             sx[2].l = 0;
-            sx[2].w[0] = 1.f;
-            sx[2].dw[0] = 0.f;
-            float acc[2] = {0.f, 0.f};
+            sx[2].w[0] = (R)1;
+            sx[2].dw[0] = (R)0;
+            R acc[2] = {(R)0, (R)0};
 #pragma unroll
             for (int ky = 0; ky < NS; ++ky)
 #pragma unroll
                 for (int kx = 0; kx < NS; ++kx) {
-                    float w, g[3];
-                    node_weights<float, 2>(sx, kx, ky, 0, w, g);
+                    R w, g[3];
+                    node_weights<R, 2>(sx, kx, ky, 0, w, g);
                     const int slot = (ly + ky) * W0 + lx + kx;
                     acc[0] = O::add(acc[0], O::mul(w, sA[slot]));
                     acc[1] = O::add(acc[1], O::mul(w, sA[W + slot]));
                 }
-            const float M = pt.M[k];
-            float MV[2], v2 = 0.f;
+            const R M = pt.M[k];
+            R MV[2], v2 = (R)0;
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
-                const float vn = O::add(pt.v[a][k], O::mul(dt, acc[a]));
+                const R vn = O::add(pt.v[a][k], O::mul(dt, acc[a]));
                 pt.v[a][k] = vn;
                 MV[a] = O::mul(M, vn);
                 v2 = O::add(v2, O::mul(vn, vn));
             }
-            vmax = fmaxf(vmax, O::sqr(v2));
-            float wm0, dm0, wm1, dm1;
-            axis_bounds<NS>(sx[0], wm0, dm0);
-            axis_bounds<NS>(sx[1], wm1, dm1);
-            const float bnd = fmaxf(fabsf(MV[0]), fabsf(MV[1])) * G.qscale[1] * (wm0 * wm1);
-            auto scatter = [&](auto small) {
-                constexpr bool SM = decltype(small)::value;
+            vmax = fmax(vmax, O::sqr(v2));
+            bool small = false;
+            if constexpr (Acc<A>::kFixed) {
+                R wm0, dm0, wm1, dm1;
+                axis_bounds<NS>(sx[0], wm0, dm0);
+                axis_bounds<NS>(sx[1], wm1, dm1);
+                small = fmax(fabs(MV[0]), fabs(MV[1])) * G.qscale[1] * (wm0 * wm1) < kSmallQuanta;
+            }
+            auto scatter = [&](auto sm) {
+                constexpr bool SM = decltype(sm)::value;
 #pragma unroll
                 for (int ky = 0; ky < NS; ++ky)
 #pragma unroll
                     for (int kx = 0; kx < NS; ++kx) {
-                        float w, g[3];
-                        node_weights<float, 2>(sx, kx, ky, 0, w, g);
-                        q[0][ky * NS + kx] += Acc<long long>::from_t<SM>(O::mul(MV[0], w), G.qscale[1]);
-                        q[1][ky * NS + kx] += Acc<long long>::from_t<SM>(O::mul(MV[1], w), G.qscale[1]);
+                        R w, g[3];
+                        node_weights<R, 2>(sx, kx, ky, 0, w, g);
+                        q[0][ky * NS + kx] += Acc<A>::template from_t<SM>(O::mul(MV[0], w), G.qscale[1]);
+                        q[1][ky * NS + kx] += Acc<A>::template from_t<SM>(O::mul(MV[1], w), G.qscale[1]);
                     }
             };
-            if (bnd < kSmallQuanta) scatter(std::true_type{});
+            if (small) scatter(std::true_type{});
             else scatter(std::false_type{});
         }
         const int base = ly * W0 + lx - lxw;
@@ -647,10 +658,10 @@ __device__ __forceinline__ void grid_g2p_fixed_tile(const Geom& G, const Particl
         for (int ky = 0; ky < NS; ++ky)
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
-                long long v[NS];
+                A v[NS];
 #pragma unroll
                 for (int c = 0; c < NS; ++c) v[c] = q[f][ky * NS + c];
-                xrow_rmw<NS, long long, true>(s2 + f * W + base + ky * W0, v, lxw, tseg);
+                xrow_rmw<NS, A, true>(s2 + f * W + base + ky * W0, v, lxw, tseg);
             }
     }
     vmax = warp_max(vmax);
@@ -663,18 +674,17 @@ __device__ __forceinline__ void grid_g2p_fixed_tile(const Geom& G, const Particl
         if (node < 0) continue;
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-            const long long v = s2[a * W + i];
-            if (v != 0) Acc<long long>::add(gr.mv2[a] + node, v);
+            const A v = s2[a * W + i];
+            if (v != A(0)) Acc<A>::add(gr.mv2[a] + node, v);
         }
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(kG2PFixedThreads, 4) k_grid_g2p_fixed(Geom G, Particles<float> pt,
-                                                                        Grid<long long, float> gr,
-                                                                        const uint32_t* __restrict__ cs, Clock* clk)
+template <int P, class R, class A>
+__global__ void __launch_bounds__(kG2PSpan2dThreads, 4) k_grid_g2p_span2d(Geom G, Particles<R> pt, Grid<A, R> gr,
+                                                                          const uint32_t* __restrict__ cs, Clock* clk)
 {
-    grid_g2p_fixed_tile<P>(G, pt, gr, cs, clk, blockIdx.x);
+    grid_g2p_span2d_tile<P, R, A>(G, pt, gr, cs, clk, blockIdx.x);
 }
 
 // ----------------------------------------- K2: grid update + G2P + P2G

@@ -128,17 +128,21 @@ def test_sort_after_steps_is_a_valid_stable_key_order():
 
 # ------------------------------------------------------------------- P2G
 
+# the last two grids have more than two tiles per SM: the 2D fixed-point and
+# FP64 modes then run the span-per-lane kernels (smaller grids the generic ones)
 P2G_CASES = [
-    (2, 2, [40, 29], ["wall"] * 4),
-    (2, 1, [33, 20], ["periodic"] * 2 + ["inflow", "outflow"]),
-    (3, 2, [13, 11, 9], ["wall", "wall", "periodic", "periodic", "wall", "wall"]),
-    (3, 1, [10, 9, 11], ["wall"] * 6),
+    (2, 2, [40, 29], ["wall"] * 4, (0, 0, 0)),
+    (2, 1, [33, 20], ["periodic"] * 2 + ["inflow", "outflow"], (0, 0, 0)),
+    (3, 2, [13, 11, 9], ["wall", "wall", "periodic", "periodic", "wall", "wall"], (0, 0, 0)),
+    (3, 1, [10, 9, 11], ["wall"] * 6, (0, 0, 0)),
+    (2, 2, [160, 60], ["wall"] * 4, (32, 1, 0)),
+    (2, 1, [160, 64], ["periodic"] * 2 + ["inflow", "outflow"], (32, 1, 0)),
 ]
 
 
-@pytest.mark.parametrize("dim,degree,n,bc", P2G_CASES)
-def test_fixed_point_p2g_bit_exact(dim, degree, n, bc):
-    p = random_problem(dim, degree, n, bc, 15013, 11, "fp32_fixed64")
+@pytest.mark.parametrize("dim,degree,n,bc,tile", P2G_CASES)
+def test_fixed_point_p2g_bit_exact(dim, degree, n, bc, tile):
+    p = random_problem(dim, degree, n, bc, 15013, 11, "fp32_fixed64", tile)
     sim = gpu_sim(p)
     sim.step(1, dt=1e-6)
     gm, gmv, gf = O.p2g_fixed32(p.cfg, p.x, p.v, p.mass, p.rho, p.e)
@@ -148,11 +152,11 @@ def test_fixed_point_p2g_bit_exact(dim, degree, n, bc):
     sim.close()
 
 
-@pytest.mark.parametrize("dim,degree,n,bc", P2G_CASES)
-def test_fixed_point_p2g_bit_exact_with_large_quanta(dim, degree, n, bc):
+@pytest.mark.parametrize("dim,degree,n,bc,tile", P2G_CASES)
+def test_fixed_point_p2g_bit_exact_with_large_quanta(dim, degree, n, bc, tile):
     # units near the typical contribution: quantised values straddle 2^31,
     # so particles take both the 32-bit and the full int64 rounding
-    p = random_problem(dim, degree, n, bc, 15013, 13, "fp32_fixed64")
+    p = random_problem(dim, degree, n, bc, 15013, 13, "fp32_fixed64", tile)
     h = p.cfg["h"]
     p.cfg["fixed_unit"] = [h ** dim, 0.1 * h ** dim, 0.8 * h ** (dim - 1)]
     sim = gpu_sim(p)
@@ -224,10 +228,10 @@ def test_coloured_simulation_cannot_join_a_batch():
     sim.close()
 
 
-@pytest.mark.parametrize("dim,degree,n,bc", P2G_CASES)
+@pytest.mark.parametrize("dim,degree,n,bc,tile", P2G_CASES)
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_float_p2g_matches_oracle(dim, degree, n, bc, precision):
-    p = random_problem(dim, degree, n, bc, 15013, 12, precision)
+def test_float_p2g_matches_oracle(dim, degree, n, bc, tile, precision):
+    p = random_problem(dim, degree, n, bc, 15013, 12, precision, tile)
     sim = gpu_sim(p)
     sim.step(1, dt=1e-6)
     gm, gmv, gf = O.p2g(p.cfg, p.x, p.v, p.mass, p.rho, p.e)
@@ -310,6 +314,21 @@ def test_fp32_fixed_cylinder_100_steps_within_target():
     g.step(100)
     o.step(100)
     r = compare_fields(g, o, 1e-4, 2, exclude_far=0.25)
+    assert r["excluded"] == 0
+    g.close()
+
+
+@pytest.mark.parametrize("precision,steps,tol", [("fp32_fixed64", 100, 1e-4), ("fp64", 40, 1e-9)])
+def test_span_kernel_cylinder_matches_oracle(precision, steps, tol):
+    # 160 x 80 cells in 32 x 1 tiles: enough tiles for the 2D span-per-lane
+    # kernels of the fixed-point and FP64 modes
+    p = I.cylinder(nx=160, ny=80, seed=5, precision=precision, tile=[32, 1, 0])
+    if precision != "fp64":
+        p = f32(p)
+    g, o = gpu_sim(p), oracle_sim(p)
+    g.step(steps)
+    o.step(steps)
+    r = compare_fields(g, o, tol, 2, exclude_far=0.25)
     assert r["excluded"] == 0
     g.close()
 
