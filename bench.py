@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--config", default="blast", choices=["blast", "cylinder"])
+    ap.add_argument("--config", default="blast", choices=["blast", "cylinder", "cylinder_paper"],
+                    help="cylinder: the 1024x512 C2 set-up; cylinder_paper: the paper's own cylinder geometry "
+                         "([0,4]x[0,2], r = 0.25 at (0.6, 1), CFL 1/2; --n x cells)")
     ap.add_argument("--n", type=int, default=0, help="override the grid size (cells per axis / x cells)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_coloured", "fp32_fixed64", "fp64"])
     ap.add_argument("--degree", type=int, default=2, choices=[1, 2], help="basis: 1 = Q1, 2 = quadratic B-spline")
@@ -70,9 +72,10 @@ def workload(args):
         ppc = args.ppa ** 3
         return {"workload": f"3D blast wave {n}^3 cells, {ppc} ppc, {basis}, {args.precision}",
                 "cells": [n, n, n], "ppc": ppc, "degree": args.degree, "precision": args.precision}
-    nx = args.n or 1024
+    nx = args.n or (1024 if args.config == "cylinder" else 1414)
     ppc = args.ppa ** 2
-    return {"workload": f"2D Mach-3 cylinder {nx}x{nx // 2} cells, {ppc} ppc, {basis}, {args.precision}",
+    where = "" if args.config == "cylinder" else " on [0,4]x[0,2], r = 0.25, CFL 1/2"
+    return {"workload": f"2D Mach-3 cylinder {nx}x{nx // 2} cells{where}, {ppc} ppc, {basis}, {args.precision}",
             "cells": [nx, nx // 2], "ppc": ppc, "degree": args.degree, "precision": args.precision}
 
 
@@ -85,7 +88,8 @@ def problem(args):
         cfg["l2"] = "inputs larger than L2 (no flush)"
     else:
         nx, ny = cfg["cells"]
-        p = I.cylinder(nx=nx, ny=ny, ppa=args.ppa, degree=args.degree, precision=args.precision)
+        geo = {} if args.config == "cylinder" else {"lx": 4.0, "center": (0.6, 1.0), "radius": 0.25, "cfl": 0.5}
+        p = I.cylinder(nx=nx, ny=ny, ppa=args.ppa, degree=args.degree, precision=args.precision, **geo)
         cfg["l2"] = ("inputs larger than L2 (no flush)" if p.n_particles * 40 > 126e6
                      else "particle state partly L2-resident")
     cfg["particles"] = p.n_particles
@@ -217,7 +221,8 @@ def cpu_baseline(args, cfg_meta, seconds_budget=20.0):
                   f"FP64 oracle")
     else:
         n = 128
-        p = I.cylinder(nx=n, ny=n // 2, ppa=args.ppa, degree=args.degree, precision="fp64")
+        geo = {} if args.config == "cylinder" else {"lx": 4.0, "center": (0.6, 1.0), "radius": 0.25, "cfl": 0.5}
+        p = I.cylinder(nx=n, ny=n // 2, ppa=args.ppa, degree=args.degree, precision="fp64", **geo)
         sample = (f"cylinder {n}x{n // 2} cells ({args.ppa ** 2} ppc, {p.n_particles} particles), same "
                   f"ppc/basis, FP64 oracle")
     s = O.OracleSim(p.cfg)
