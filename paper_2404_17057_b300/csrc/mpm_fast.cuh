@@ -17,6 +17,10 @@
 // chunks of particles in shared memory with bulk copies and runs both kinds
 // of work on them: the gather per particle, then the momentum scatter per
 // span.
+//
+// The file also holds the 2D span-per-lane P2G and grid + G2P + P2G kernels
+// of the fixed-point and FP64 modes (64-bit register sums), and the G2PD
+// kernel that the fixed-point mode shares with FP32.
 #pragma once
 #include "mpm_kernels.cuh"
 #include "mpm_tma.cuh"
