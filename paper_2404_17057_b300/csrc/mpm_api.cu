@@ -218,8 +218,9 @@ unsigned colour_blocks(const mpm_sim* s, int c)
 
 template <int D, int P, class R, class A>
 struct Impl {
-    // The single-precision float-atomic path runs the span-per-thread kernels
-    // of mpm_fast.cuh; the fixed-point and FP64 paths the generic ones.
+    // The single-precision float-atomic path (and its colour passes) runs the
+    // span-per-thread kernels of mpm_fast.cuh; the fixed-point and FP64 paths
+    // run the 2D span kernels below, or the generic ones (3D, small grids).
     static constexpr bool kFast = std::is_same<R, float>::value && std::is_same<A, float>::value;
     // G2PD reads the grid once into its window, so the fixed-point mode runs
     // the single-precision kernel too (the int64 sums are converted there)
