@@ -64,7 +64,7 @@ typedef enum {
     MPM_ESTATE = 4,        /* call not allowed in the current state / poisoned */
     MPM_ENONFINITE = 5,    /* non-finite state or 1 + dt div(v) <= 0 */
     MPM_ETIMEOUT = 6,      /* a bounded device wait expired */
-    MPM_EUNSUPPORTED = 7,  /* valid request this build does not provide */
+    MPM_EUNSUPPORTED = 7,  /* valid request the library does not support */
     MPM_ECFL = 8           /* a particle crossed more than one span in a step */
 } mpm_status;
 
