@@ -742,8 +742,10 @@ static int one_step(oracle_sim* s, double dt)
         if (div[k] < 0.0) {
             double c2 = gam * Pnew / rnew;
             double cs = sqrt(c2 > 0.0 ? c2 : 0.0);
-            double t1 = rnew * G->h * div[k];
-            qnew = c->c0 * t1 * t1 - c->c1 * G->h * cs * div[k];
+            /* eq. muart read as the von Neumann-Richtmyer and Landshoff
+             * terms it names, both proportional to the density */
+            double t1 = G->h * div[k];
+            qnew = rnew * (c->c0 * t1 * t1 - c->c1 * G->h * cs * div[k]);
         }
         s->E[k] = Enew; s->rho[k] = rnew; s->Q[k] = qnew;
         if (!isfinite(Enew) || !isfinite(rnew) || !isfinite(qnew)) return OR_ENONFINITE;

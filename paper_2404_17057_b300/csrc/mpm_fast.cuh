@@ -1111,8 +1111,10 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
         const float cs = sqrtf(c2 > 0.f ? c2 : 0.f);
         float Qn = 0.f;
         if (dv < 0.f) {
-            const float t1 = rn * hh * dv;
-            Qn = c0 * t1 * t1 - c1 * hh * cs * dv;
+            // eq. muart: von Neumann-Richtmyer and Landshoff terms, both
+            // proportional to the density
+            const float t1 = hh * dv;
+            Qn = rn * (c0 * t1 * t1 - c1 * hh * cs * dv);
         }
         (void)Pn;
         // step ix: move with Vbar; step x: wrap / hold / recycle; new key

@@ -766,8 +766,10 @@ __device__ __forceinline__ void g2pd_tile(const Geom& G, const Particles<R>& pt,
         const R cs = O::sqr(c2 > (R)0 ? c2 : (R)0);
         R Qn = (R)0;
         if (dv < (R)0) {
-            R t1 = O::mul(O::mul(rn, hh), dv);
-            Qn = O::sub(O::mul(O::mul(c0, t1), t1), O::mul(O::mul(O::mul(c1, hh), cs), dv));
+            // eq. muart: von Neumann-Richtmyer and Landshoff terms, both
+            // proportional to the density
+            const R t1 = O::mul(hh, dv);
+            Qn = O::mul(rn, O::sub(O::mul(O::mul(c0, t1), t1), O::mul(O::mul(O::mul(c1, hh), cs), dv)));
         }
         // step ix: move with Vbar; step x: connectivity (wrap, hold, recycle)
         R xn[3];

@@ -276,16 +276,16 @@ def uniform_flow(dim=2, n=(16, 16, 16), ppa=2, vel=(0.3, -0.2, 0.1), rho0=1.0, p
     return Problem("uniform_flow", cfg, x, v, mass, rho, e)
 
 
-def linear_velocity(dim=2, n=16, ppa=2, a=0.05, degree=2, precision="fp64", e0=0.0, **kw) -> Problem:
-    """Gas of uniform density and internal energy e0 with V = a X on a lattice,
-    free (outflow) faces: interior particles see div V = d a."""
+def linear_velocity(dim=2, n=16, ppa=2, a=0.05, degree=2, precision="fp64", e0=0.0, rho0=1.0, **kw) -> Problem:
+    """Gas of uniform density rho0 and internal energy e0 with V = a X on a
+    lattice, free (outflow) faces: interior particles see div V = d a."""
     h = 1.0 / n
     cfg = base_config(dim, [n] * dim, h, ["outflow"] * (2 * dim), degree=degree, precision=precision, **kw)
     x = _lattice([n] * dim, h, ppa, dim)
     N = x.shape[1]
     v = a * x
-    rho = np.ones(N)
-    mass = np.full(N, h ** dim / ppa ** dim)
+    rho = np.full(N, float(rho0))
+    mass = np.full(N, rho0 * h ** dim / ppa ** dim)
     e = np.full(N, float(e0))
     return Problem("linear_velocity", cfg, x, v, mass, rho, e, meta={"a": a})
 

@@ -434,10 +434,19 @@ def test_homogeneous_compression_update(dim):
     r1 = 1.0 / (1 + dt * div)
     P1 = (gam - 1) * r1 * E1
     h = 1.0 / n
-    Q1 = (r1 * h * div) ** 2 - h * np.sqrt(gam * P1 / r1) * div
+    Q1 = r1 * ((h * div) ** 2 - h * np.sqrt(gam * P1 / r1) * div)
     assert np.abs(_by_id(s, "E")[interior] - E1).max() < 1e-13
     assert np.abs(_by_id(s, "RHO")[interior] - r1).max() < 1e-13
     assert np.abs(_by_id(s, "Q")[interior] - Q1).max() < 1e-13
+    # the viscous pressure is proportional to the density: the same flow at
+    # four times the density (same e, so the same sound speed) has four
+    # times the Q and the same E
+    p4 = I.linear_velocity(dim=dim, n=n, a=a, e0=e0, rho0=4.0)
+    s4 = _sim(p4)
+    s4.step(1, dt=dt)
+    ratio = _by_id(s4, "Q")[interior] / _by_id(s, "Q")[interior]
+    assert np.abs(ratio - 4.0).max() < 1e-12
+    assert np.abs(_by_id(s4, "E")[interior] - E1).max() < 1e-13
     # expansion switches the viscosity off
     p = I.linear_velocity(dim=dim, n=n, a=-a, e0=e0)
     s = _sim(p)
