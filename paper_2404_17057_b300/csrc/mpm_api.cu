@@ -230,9 +230,10 @@ struct Impl {
     static constexpr bool kSpan2d = D == 2 && ((std::is_same<R, float>::value && std::is_same<A, long long>::value) ||
                                                (std::is_same<R, double>::value && std::is_same<A, double>::value));
     static_assert(!(kSpan2d && kFast), "one P2G kernel per mode");
-    // ... on grids of at least two tiles per SM; smaller grids keep the
-    // particle-parallel generic kernels, whose 256 threads finish a tile sooner
-    static bool span2d(const Geom& G) { return G.ntiles >= 2 * 148; }
+    // ... always in fixed point; in FP64 on grids of at least two tiles per
+    // SM (smaller FP64 grids keep the particle-parallel generic kernels, whose
+    // 256 threads finish a tile sooner; fixed point gains at every size)
+    static bool span2d(const Geom& G) { return std::is_same<A, long long>::value || G.ntiles >= 2 * 148; }
     static size_t smem(const Geom& G, int kernel)
     {
         const size_t W = (size_t)G.Wvol;
