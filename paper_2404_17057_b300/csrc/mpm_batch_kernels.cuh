@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 3)
 }
 
 template <int D, int P, class A>
-__global__ void __launch_bounds__(kG2PDThreads) kb_g2pd_fast(const BatchProb<float, A>* __restrict__ bp,
+__global__ void __launch_bounds__(kG2PDThreads, kG2PDBlocks) kb_g2pd_fast(const BatchProb<float, A>* __restrict__ bp,
                                                              const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(float, A)

@@ -957,6 +957,9 @@ __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 4) k_grid_g2p_span(Geom G,
 // ------------------------------- K3: G2PD + particle update + move + key
 
 constexpr int kG2PDThreads = 128;
+// five resident blocks: 96 registers a thread (128 without the bound; the
+// extra warps hide more latency than the few spilled bytes cost)
+constexpr int kG2PDBlocks = 5;
 
 // A: grid accumulator type (float, or int64 fixed point read back as float).
 template <int D, int P, class A>
@@ -1207,7 +1210,7 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
 }
 
 template <int D, int P, class A>
-__global__ void __launch_bounds__(kG2PDThreads) k_g2pd_fast(Geom G, Particles<float> pt, Grid<A, float> gr,
+__global__ void __launch_bounds__(kG2PDThreads, kG2PDBlocks) k_g2pd_fast(Geom G, Particles<float> pt, Grid<A, float> gr,
                                                             const uint32_t* __restrict__ cs, Clock* clk, Reorder ro)
 {
     g2pd_fast_tile<D, P, A>(G, pt, gr, cs, clk, ro, blockIdx.x);
