@@ -450,6 +450,38 @@ def test_add_particles_checks_every_value_on_the_device():
     g.close()
 
 
+def test_particles_added_in_parts_equal_one_call():
+    # two calls append (ids run on) and the initial order is the same stable
+    # key order as one call with all particles
+    p = random_problem(2, 2, [40, 29], ["wall"] * 4, 5000, 21, "fp32")
+    one = gpu_sim(p)
+    two = M.Simulation(p.cfg)
+    k = 1777
+    two.add_particles(p.x[:, :k], p.v[:, :k], p.mass[:k], p.rho[:k], p.e[:k])
+    two.add_particles(p.x[:, k:], p.v[:, k:], p.mass[k:], p.rho[k:], p.e[k:])
+    for f in ("ID", "X", "V", "RHO", "KEY", "CELLSTART"):
+        assert np.array_equal(one.read(f), two.read(f)), f
+    one.step(5)
+    two.step(5)
+    assert np.allclose(one.read("RHO"), two.read("RHO"), rtol=1e-5, atol=0)
+    one.close()
+    two.close()
+
+
+def test_read_into_a_caller_array():
+    p = I.shock_tube(ncell=32, ny=4, precision="fp32")
+    g = gpu_sim(p)
+    g.step(3)
+    ref = g.read("V")
+    buf = np.full(2 * p.n_particles + 7, -1.0)
+    got = g.read("V", out=buf)
+    assert np.array_equal(got, ref) and np.array_equal(buf[:2 * p.n_particles], ref.reshape(-1))
+    assert np.all(buf[2 * p.n_particles:] == -1.0)
+    with pytest.raises(ValueError):
+        g.read("V", out=np.empty(3))
+    g.close()
+
+
 def test_short_output_buffer_rejected():
     import ctypes
     p = I.shock_tube(ncell=16, ny=4)
