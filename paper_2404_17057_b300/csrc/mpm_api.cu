@@ -56,6 +56,7 @@ struct mpm_sim {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
+    int sms = 148;                 // streaming multiprocessors of the device
     int64_t np = 0;
     int cur = 0;
     Buffers buf[2];
@@ -233,7 +234,7 @@ struct Impl {
     // ... always in fixed point; in FP64 on grids of at least two tiles per
     // SM (smaller FP64 grids keep the particle-parallel generic kernels, whose
     // 256 threads finish a tile sooner; fixed point gains at every size)
-    static bool span2d(const Geom& G) { return std::is_same<A, long long>::value || G.ntiles >= 2 * 148; }
+    static bool span2d(const mpm_sim* s) { return std::is_same<A, long long>::value || s->G.ntiles >= 2 * s->sms; }
     static size_t smem(const Geom& G, int kernel)
     {
         const size_t W = (size_t)G.Wvol;
@@ -292,7 +293,7 @@ struct Impl {
         const uint32_t* cs = s->cs[s->cur];
         const Reorder ro = {s->count, s->far, s->far_cap, s->mwords, s->ring};
         if (which & 1) {
-            k_zero<<<std::min<int64_t>(nblk(s->grid_bytes / 16), 148 * 8), kThreads, 0, st>>>(
+            k_zero<<<std::min<int64_t>(nblk(s->grid_bytes / 16), s->sms * 8), kThreads, 0, st>>>(
                 (uint4*)s->grid, (int64_t)(s->grid_bytes / 16), &s->clk->active);
             if constexpr (kFast) {
                 const FieldPtrs o = p2g_fields(gr);
@@ -305,7 +306,7 @@ struct Impl {
                     else k_p2g_span<D, P, false><<<nb, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk, tl);
                 }
                 s->launches += ncolours(s) - 1;
-            } else if (kSpan2d && span2d(G)) {
+            } else if (kSpan2d && span2d(s)) {
                 k_p2g_span2d<P, R, A><<<G.ntiles, kP2GSpan2dThreads, smem(G, 0), st>>>(G, pt, gr, cs, s->clk);
             } else {
                 k_p2g<D, P, R, A><<<G.ntiles, kThreads, smem(G, 0), st>>>(G, pt, gr, cs, s->clk);
@@ -328,7 +329,7 @@ struct Impl {
                                                                                                  s->clk, tl);
                 }
                 s->launches += ncolours(s) - 1;
-            } else if (kSpan2d && span2d(G)) {
+            } else if (kSpan2d && span2d(s)) {
                 k_grid_g2p_span2d<P, R, A><<<G.ntiles, kG2PSpan2dThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
             } else {
                 k_grid_g2p<D, P, R, A><<<G.ntiles, kThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
@@ -471,7 +472,7 @@ struct Impl {
     }
     static void cfl_init(mpm_sim* s, cudaStream_t st)
     {
-        unsigned nb = std::max(1u, std::min(nblk(s->np), 148u * 8u));
+        unsigned nb = std::max(1u, std::min(nblk(s->np), (unsigned)s->sms * 8u));
         k_cfl_init<D, R><<<nb, kThreads, 0, st>>>(s->G, parts<R>(s->buf[s->cur]), s->np, s->clk);
         k_cfl_init_finish<<<1, 1, 0, st>>>(s->clk, s->G.cfl * s->G.h);
         s->launches += 2;
@@ -689,7 +690,7 @@ void launch_reorder(mpm_sim* s, cudaStream_t st)
     uint32_t* cs_new = s->cs[1 - s->cur];
     scan_exclusive(s->count, cs_new, s->G.nkey, s->cscan_part, 1, st, &s->launches);
     if (s->far_cap) {
-        k_far_place<<<148 * 2, 256, 0, st>>>(s->far, s->far_cap, s->count, cs_new, s->perm, s->clk);
+        k_far_place<<<s->sms * 2, 256, 0, st>>>(s->far, s->far_cap, s->count, cs_new, s->perm, s->clk);
         s->launches += 1;
     }
     s->vt->reorder(s, st);
@@ -820,6 +821,10 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
         cudaGetLastError();
         delete s;
         return fail(nullptr, MPM_ECUDA, "no CUDA device");
+    }
+    if (cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess || s->sms < 1) {
+        cudaGetLastError();
+        s->sms = 148;
     }
     if (cfg->stream) {
         s->stream = (cudaStream_t)cfg->stream;
@@ -1286,7 +1291,7 @@ mpm_status mpm_read_state(mpm_sim* s, int field, double* out, int64_t count)
         if (np == 0) return MPM_OK;
         uint32_t* tk = (uint32_t*)dalloc(s, (size_t)np * 4);
         if (!tk) return fail(s, MPM_ENOMEM, "device allocation failed");
-        k_keys_from_start<<<std::min<int64_t>(nblk(s->G.nkey), 148 * 16), kThreads, 0, s->stream>>>(
+        k_keys_from_start<<<std::min<int64_t>(nblk(s->G.nkey), s->sms * 16), kThreads, 0, s->stream>>>(
             s->cs[s->cur], s->G.nkey, tk);
         st = read_u32(s, tk, np, out);
         dfree(s, tk);

@@ -45,9 +45,15 @@ extern "C" mpm_status mpm_check_fixed_rounding(uint64_t* mismatches, uint32_t* f
         return fail(nullptr, MPM_ENOMEM, "mpm_check_fixed_rounding: cudaMalloc failed");
     }
     Out h = {0ull, 0xffffffffu};
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 148;
+    }
     e = cudaMemcpy(d, &h, sizeof h, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        k_check_f2ll<<<148 * 8, kCheckThreads>>>(&d->bad, &d->first);
+        k_check_f2ll<<<sms * 8, kCheckThreads>>>(&d->bad, &d->first);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
