@@ -91,3 +91,23 @@ def test_flow_past_a_profile_matches_the_oracle(precision, steps, tol):
     o.step(steps)
     _compare(g, o, 2, tol)
     g.close()
+
+
+def test_aerofoil_flow_is_faster_over_the_upper_surface():
+    """The aerofoil case (Sec. 4.1): at 25 degrees the flow speeds up
+    approaching the profile, more over the upper surface than under it.  Mean
+    particle speed in bands along 10-90% of the chord, up to 0.11 chords from
+    the chord line, after t = 0.3 (about two chord passages)."""
+    p = I.aerofoil(nx=300, ny=203, ppa=2)
+    le, chord, ang = np.array([0.1, 0.15]), 0.1, np.deg2rad(25.0)
+    tdir = np.array([np.cos(-ang), np.sin(-ang)])
+    ndir = np.array([-tdir[1], tdir[0]])
+    with M.Simulation.from_problem(p) as s:
+        s.step(1000000, t_end=0.3)
+        x, v = s.read("X"), s.read("V")
+    rel = x - le[:, None]
+    along, up = rel.T @ tdir, rel.T @ ndir
+    speed = np.sqrt((v ** 2).sum(axis=0))
+    band = (along > 0.1 * chord) & (along < 0.9 * chord) & (np.abs(up) < 0.11 * chord)
+    above, below = speed[band & (up > 0)].mean(), speed[band & (up < 0)].mean()
+    assert above > 1.2 * below and below > 0.73, (above, below)
