@@ -481,7 +481,7 @@ struct Impl {
     {
         const int nb = 1024;
         k_cons_partial<D, R><<<nb, 256, 0, st>>>(parts<R>(s->buf[s->cur]), s->np, s->cons_part);
-        k_cons_final<<<1, 32, 0, st>>>(s->cons_part, nb, s->cons_out);
+        k_cons_final<<<1, kConsThreads, 0, st>>>(s->cons_part, nb, s->cons_out);
         s->launches += 2;
     }
     static void from_double(const double* in, void* out, int64_t n, cudaStream_t st)

@@ -994,8 +994,8 @@ __global__ void k_gather(Particles<R> in, Particles<R> out, const uint32_t* perm
     (void)sorted_keys;   // the sorted keys stay in the re-order's own buffer
 }
 
-// FP64 sums for the conservation diagnostics: one partial per block,
-// summed by k_cons_final in block order (deterministic).
+// FP64 sums for the conservation diagnostics: one partial per block, summed
+// by k_cons_final in a fixed order (deterministic).
 template <int D, class R>
 __global__ void __launch_bounds__(256) k_cons_partial(Particles<R> pt, int64_t n, double* partial)
 {
@@ -1023,13 +1023,26 @@ __global__ void __launch_bounds__(256) k_cons_partial(Particles<R> pt, int64_t n
         for (int i = 0; i < 5; ++i) partial[blockIdx.x * 5 + i] = sh[i][0];
 }
 
-__global__ void k_cons_final(const double* partial, int nb, double* out)
+// One block of kConsThreads: thread t adds partials t, t + kConsThreads, ...,
+// then a fixed tree over the threads (a serial chain of dependent FP64 adds
+// over all partials took longer than the partials themselves).
+constexpr int kConsThreads = 256;
+
+__global__ void __launch_bounds__(kConsThreads) k_cons_final(const double* partial, int nb, double* out)
 {
-    if (threadIdx.x != 0) return;
+    __shared__ double sh[5][kConsThreads];
     double s[5] = {0, 0, 0, 0, 0};
-    for (int b = 0; b < nb; ++b)
+    for (int b = threadIdx.x; b < nb; b += kConsThreads)
         for (int i = 0; i < 5; ++i) s[i] += partial[b * 5 + i];
-    for (int i = 0; i < 5; ++i) out[i] = s[i];
+    for (int i = 0; i < 5; ++i) sh[i][threadIdx.x] = s[i];
+    __syncthreads();
+    for (int o = kConsThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int i = 0; i < 5; ++i) sh[i][threadIdx.x] += sh[i][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 5; ++i) out[i] = sh[i][0];
 }
 
 // Convert host-side doubles to the storage precision.

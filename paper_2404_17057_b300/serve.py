@@ -98,7 +98,8 @@ class Server:
     def run(self, requests: list[dict], realtime: bool = True) -> tuple[list[Result], dict]:
         import torch
         reqs = sorted(requests, key=lambda r: r["arrival"])
-        waiting: list[tuple[dict, object, int]] = []
+        pending: list[dict] = []                       # arrived, problem not built yet
+        waiting: list[tuple[dict, object, int]] = []   # built, not admitted yet
         active: list[dict] = []
         results: list[Result] = []
         used = 0.0
@@ -107,17 +108,19 @@ class Server:
         ev = None
         t0 = time.perf_counter()
         try:
-            while nxt < len(reqs) or waiting or active:
+            while nxt < len(reqs) or pending or waiting or active:
                 now = time.perf_counter() - t0
                 # arrivals (all at once when not in real time)
                 while nxt < len(reqs) and (not realtime or reqs[nxt]["arrival"] <= now):
-                    r = reqs[nxt]
-                    prob = I.request_problem(r)
-                    if self.tuner is not None:
-                        prob.cfg["tile"] = self.tuner.tile_for(prob)
-                    waiting.append((r, prob, footprint_bytes(prob)))
+                    pending.append(reqs[nxt])
                     nxt += 1
-                if ev is not None and not ev.query():
+                busy = ev is not None and not ev.query()
+                # build the arrived problems on the host while the device runs
+                # a chunk, or when there is nothing to admit or run
+                if pending and len(waiting) < self.max_active and (busy or (not active and not waiting)):
+                    waiting.append(self._build(pending.pop(0)))
+                    continue
+                if busy:
                     time.sleep(0.0002)
                     continue
                 if ev is not None:
@@ -167,6 +170,12 @@ class Server:
         t1 = time.perf_counter()
         return results, _summary(results, t0, t1)
 
+    def _build(self, r):
+        prob = I.request_problem(r)
+        if self.tuner is not None:
+            prob.cfg["tile"] = self.tuner.tile_for(prob)
+        return r, prob, footprint_bytes(prob)
+
     @staticmethod
     def _drop_failed(batch, active, results):
         """A member raised an error (its state is then poisoned): take every
@@ -191,11 +200,14 @@ class Server:
 
 
 def run_sequential(requests: list[dict], realtime: bool = True, tuner=None) -> tuple[list[Result], dict]:
-    """One request at a time in arrival order with the same kernels."""
+    """One request at a time in arrival order with the same kernels; the next
+    arrived request's problem is built on the host while the current one
+    runs, as the batched server does."""
     reqs = sorted(requests, key=lambda r: r["arrival"])
     results = []
     t0 = time.perf_counter()
-    for r in reqs:
+
+    def build(r):
         if realtime:
             wait = r["arrival"] - (time.perf_counter() - t0)
             if wait > 0:
@@ -203,14 +215,32 @@ def run_sequential(requests: list[dict], realtime: bool = True, tuner=None) -> t
         prob = I.request_problem(r)
         if tuner is not None:
             prob.cfg["tile"] = tuner.tile_for(prob)
+        return prob
+
+    nxt = build(reqs[0]) if reqs else None
+    for i, r in enumerate(reqs):
+        prob = nxt
         admitted = time.perf_counter()
         sim = M.Simulation.from_problem(prob)
         arrival = t0 + (r["arrival"] if realtime else 0.0)
+        err = None
         try:
-            sim.step(prob.steps)
-            results.append(_finish(sim, r, arrival, admitted, prob.n_particles, prob.steps))
+            sim.step_async(prob.steps)
         except M.MPMError as e:
-            results.append(_failed(r, arrival, admitted, prob.n_particles, prob.steps, e.status))
+            err = e
+        arrived = i + 1 < len(reqs) and (not realtime or reqs[i + 1]["arrival"] <= time.perf_counter() - t0)
+        nxt = build(reqs[i + 1]) if arrived else None
+        if err is None:
+            try:
+                sim.sync()
+            except M.MPMError as e:
+                err = e
+        if err is None:
+            results.append(_finish(sim, r, arrival, admitted, prob.n_particles, prob.steps))
+        else:
+            results.append(_failed(r, arrival, admitted, prob.n_particles, prob.steps, err.status))
         sim.close()
+        if nxt is None and i + 1 < len(reqs):
+            nxt = build(reqs[i + 1])
     t1 = time.perf_counter()
     return results, _summary(results, t0, t1)
