@@ -606,48 +606,60 @@ int oracle_stable_sort(int64_t n, const uint32_t* keys, int64_t nkeys, int64_t* 
     return OR_OK;
 }
 
+/* Sec. 3 step xii: the per-cell lists rebuilt from the cells the particles
+ * are now in.  Walk the particles in their current order and append each to
+ * the list of its key; a particle re-created at the inflow during the step
+ * (Sec. 4.1) is new in its cell and goes after the cell's other particles,
+ * several of them by id.  perm[j] = current index of the particle placed at
+ * j; start[K] = first position of key K (nkeys + 1 entries). */
+int oracle_reorder(int64_t n, const uint32_t* keys, const uint8_t* recycled, const int64_t* ids,
+                   int64_t nkeys, int64_t* perm, int64_t* start)
+{
+    if (n < 0 || nkeys < 1 || !perm || !start || (n > 0 && (!keys || !recycled || !ids))) return OR_EINVAL;
+    for (int64_t i = 0; i <= nkeys; ++i) start[i] = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        if ((int64_t)keys[k] >= nkeys) return OR_EINVAL;
+        start[keys[k] + 1]++;
+    }
+    for (int64_t i = 0; i < nkeys; ++i) start[i + 1] += start[i];
+    int64_t* cur = (int64_t*)malloc((size_t)nkeys * sizeof(int64_t) + 8);
+    if (!cur) return OR_ENOMEM;
+    memcpy(cur, start, (size_t)nkeys * sizeof(int64_t));
+    /* the cell's stayers in current order */
+    for (int64_t k = 0; k < n; ++k)
+        if (!recycled[k]) perm[cur[keys[k]]++] = k;
+    /* then its re-created particles: each goes after those of its cell with a
+     * smaller id (insertion into the cell's tail, which is short) */
+    for (int64_t k = 0; k < n; ++k) {
+        if (!recycled[k]) continue;
+        const uint32_t K = keys[k];
+        int64_t j = cur[K]++;
+        while (j > start[K] && recycled[perm[j - 1]] && ids[perm[j - 1]] > ids[k]) {
+            perm[j] = perm[j - 1];
+            --j;
+        }
+        perm[j] = k;
+    }
+    free(cur);
+    return OR_OK;
+}
+
 static void permute_d(double* a, const int64_t* perm, int64_t n, double* tmp)
 {
     for (int64_t j = 0; j < n; ++j) tmp[j] = a[perm[j]];
     memcpy(a, tmp, (size_t)n * sizeof(double));
 }
 
-/* Recycled particles of one key, ordered by id (qsort comparator). */
-static const uint32_t* g_rk;
-static const int64_t* g_rid;
-static int cmp_recycled(const void* a, const void* b)
-{
-    int64_t i = *(const int64_t*)a, j = *(const int64_t*)b;
-    if (g_rk[i] != g_rk[j]) return g_rk[i] < g_rk[j] ? -1 : 1;
-    return g_rid[i] < g_rid[j] ? -1 : (g_rid[i] > g_rid[j] ? 1 : 0);
-}
-
-/* Sec. 3 step xii: rebuild each cell's list from the particles now in it, in
- * their current order; particles re-created at the inflow during this step
- * (Sec. 4.1) are new in their cell and are appended after the others, by id. */
+/* Re-order the particle state by the lists of oracle_reorder. */
 static int sort_particles(oracle_sim* s)
 {
     keys_of_particles(s);
     int64_t n = s->np;
     int64_t* perm = (int64_t*)malloc((size_t)n * sizeof(int64_t) + 8);
     double* tmp = (double*)malloc((size_t)n * sizeof(double) + 8);
-    int64_t* cur = (int64_t*)malloc((size_t)s->G.nkey * sizeof(int64_t) + 8);
-    int64_t* rl = (int64_t*)malloc((size_t)n * sizeof(int64_t) + 8);
-    if (!perm || !tmp || !cur || !rl) { free(perm); free(tmp); free(cur); free(rl); return OR_ENOMEM; }
-    int64_t* start = s->cellstart;
-    for (int64_t i = 0; i <= s->G.nkey; ++i) start[i] = 0;
-    for (int64_t k = 0; k < n; ++k) start[s->key[k] + 1]++;
-    for (int64_t i = 0; i < s->G.nkey; ++i) start[i + 1] += start[i];
-    memcpy(cur, start, (size_t)s->G.nkey * sizeof(int64_t));
-    int64_t nr = 0;
-    for (int64_t k = 0; k < n; ++k) {
-        if (s->recyc[k]) rl[nr++] = k;
-        else perm[cur[s->key[k]]++] = k;
-    }
-    g_rk = s->key; g_rid = s->id;
-    qsort(rl, (size_t)nr, sizeof(int64_t), cmp_recycled);
-    for (int64_t i = 0; i < nr; ++i) perm[cur[s->key[rl[i]]]++] = rl[i];
-    free(cur); free(rl);
+    if (!perm || !tmp) { free(perm); free(tmp); return OR_ENOMEM; }
+    int st = oracle_reorder(n, s->key, s->recyc, s->id, s->G.nkey, perm, s->cellstart);
+    if (st) { free(perm); free(tmp); return st; }
     for (int a = 0; a < 3; ++a) { permute_d(s->x[a], perm, n, tmp); permute_d(s->v[a], perm, n, tmp);
                                   permute_d(s->vbar[a], perm, n, tmp); }
     permute_d(s->M, perm, n, tmp); permute_d(s->rho, perm, n, tmp);
@@ -827,7 +839,8 @@ int64_t oracle_field_size(oracle_sim* s, int field)
     int d = s->G.dim;
     switch (field) {
     case OR_F_X: case OR_F_V: case OR_F_VBAR: return d * s->np;
-    case OR_F_M: case OR_F_RHO: case OR_F_E: case OR_F_P: case OR_F_Q: case OR_F_ID: case OR_F_KEY: return s->np;
+    case OR_F_M: case OR_F_RHO: case OR_F_E: case OR_F_P: case OR_F_Q: case OR_F_ID: case OR_F_KEY:
+    case OR_F_GEN: return s->np;
     case OR_F_CELLSTART: return s->G.nkey + 1;
     case OR_F_GRID_M: return s->G.nnode;
     case OR_F_GRID_MV: case OR_F_GRID_F: case OR_F_GRID_MV2: return d * s->G.nnode;
@@ -853,6 +866,7 @@ int oracle_read(oracle_sim* s, int field, double* out, int64_t count)
     case OR_F_Q: memcpy(out, s->Q, np * sizeof(double)); break;
     case OR_F_ID: for (int64_t k = 0; k < np; ++k) out[k] = (double)s->id[k]; break;
     case OR_F_KEY: for (int64_t k = 0; k < np; ++k) out[k] = (double)s->key[k]; break;
+    case OR_F_GEN: for (int64_t k = 0; k < np; ++k) out[k] = (double)s->gen[k]; break;
     case OR_F_CELLSTART: for (int64_t i = 0; i <= s->G.nkey; ++i) out[i] = (double)s->cellstart[i]; break;
     case OR_F_GRID_M: memcpy(out, s->gm, nn * sizeof(double)); break;
     case OR_F_GRID_MV: for (int a = 0; a < d; ++a) memcpy(out + a * nn, s->gmv[a], nn * sizeof(double)); break;

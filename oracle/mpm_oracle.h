@@ -28,11 +28,13 @@ enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2, OR_ESTATE = 4,
        OR_ENONFINITE = 5, OR_ECFL = 8 };
 enum { OR_BC_WALL = 0, OR_BC_PERIODIC = 1, OR_BC_INFLOW = 2, OR_BC_OUTFLOW = 3 };
 
-/* Field ids for oracle_read (same numbering as the product's read call). */
+/* Field ids for oracle_read (the product's read call uses the same numbers
+ * for the fields both have; VBAR is the oracle's alone).  GEN = how many times
+ * each particle has been re-created at the inflow. */
 enum { OR_F_X = 0, OR_F_V = 1, OR_F_M = 2, OR_F_RHO = 3, OR_F_E = 4, OR_F_P = 5,
        OR_F_Q = 6, OR_F_ID = 7, OR_F_KEY = 8, OR_F_CELLSTART = 9,
        OR_F_GRID_M = 10, OR_F_GRID_MV = 11, OR_F_GRID_F = 12, OR_F_GRID_MV2 = 13,
-       OR_F_CLOCK = 14, OR_F_VBAR = 15 };
+       OR_F_CLOCK = 14, OR_F_VBAR = 15, OR_F_GEN = 16 };
 
 typedef struct {
     int dim;              /* 2 or 3 */
@@ -47,7 +49,7 @@ typedef struct {
     int sort_interval;    /* re-order every k steps (0 = never) */
     uint64_t seed;        /* recycling generator key */
     int tile[3];          /* span-tile edge per axis for the key numbering
-                             (0: 32 x 4 x 4 in 3D, 32 x 8 in 2D) */
+                             (0: 16 x 8 x 4 in 3D, 32 x 8 in 2D) */
 } oracle_config;
 
 typedef struct oracle_sim oracle_sim;
@@ -81,6 +83,12 @@ double oracle_bspline_dense(int degree, double r, double* dN);
 int oracle_keys(const oracle_config* cfg, int64_t n, const double* x, int prec32, uint32_t* keys);
 /* Stable sort by key: perm[j] = old index placed at j; start[K+1]. */
 int oracle_stable_sort(int64_t n, const uint32_t* keys, int64_t nkeys, int64_t* perm, int64_t* start);
+/* The per-step re-order (Sec. 3 step xii): particles in their current order
+ * go to the list of their key; those re-created at the inflow during the step
+ * (recycled[k] != 0, Sec. 4.1) follow the other particles of their key, by
+ * id.  perm[j] = current index placed at j; start[K] (nkeys + 1 entries). */
+int oracle_reorder(int64_t n, const uint32_t* keys, const uint8_t* recycled, const int64_t* ids,
+                   int64_t nkeys, int64_t* perm, int64_t* start);
 
 /* P2G of m, M V, (P+Q) M/rho grad(phi) for a particle set (FP64, plain loop). */
 int oracle_p2g(const oracle_config* cfg, int64_t n, const double* x, const double* v,

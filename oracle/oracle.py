@@ -20,7 +20,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 BC = {"wall": 0, "periodic": 1, "inflow": 2, "outflow": 3}
 FIELDS = {"X": 0, "V": 1, "M": 2, "RHO": 3, "E": 4, "P": 5, "Q": 6, "ID": 7, "KEY": 8,
           "CELLSTART": 9, "GRID_M": 10, "GRID_MV": 11, "GRID_F": 12, "GRID_MV2": 13,
-          "CLOCK": 14, "VBAR": 15}
+          "CLOCK": 14, "VBAR": 15, "GEN": 16}
 ERRORS = {1: "EINVAL", 2: "ENOMEM", 4: "ESTATE", 5: "ENONFINITE", 8: "ECFL"}
 
 
@@ -77,6 +77,7 @@ def lib():
         L.oracle_bspline_dense.restype = d
         L.oracle_keys.argtypes = [P(_Config), i64, vp, C.c_int, vp]
         L.oracle_stable_sort.argtypes = [i64, vp, i64, vp, vp]
+        L.oracle_reorder.argtypes = [i64, vp, vp, vp, i64, vp, vp]
         L.oracle_p2g.argtypes = [P(_Config), i64] + [vp] * 9
         L.oracle_p2g_dense.argtypes = [P(_Config), i64] + [vp] * 9
         L.oracle_p2g_fixed32.argtypes = [P(_Config), i64] + [vp] * 10
@@ -216,6 +217,21 @@ def stable_sort(k: np.ndarray, nkeys: int):
     perm = np.empty(k.shape[0], dtype=np.int64)
     start = np.empty(nkeys + 1, dtype=np.int64)
     _check(lib().oracle_stable_sort(k.shape[0], _ptr(k), int(nkeys), _ptr(perm), _ptr(start)), "stable_sort")
+    return perm, start
+
+
+def reorder(k: np.ndarray, recycled: np.ndarray, ids: np.ndarray, nkeys: int):
+    """The per-step re-order (Sec. 3 step xii) of particles in their current
+    order: perm[j] = current index placed at j, start = first position of
+    each key.  Particles with recycled != 0 (re-created at the inflow in the
+    step) follow the others of their key, by id."""
+    k = np.ascontiguousarray(k, dtype=np.uint32)
+    r = np.ascontiguousarray(recycled, dtype=np.uint8)
+    i = np.ascontiguousarray(ids, dtype=np.int64)
+    perm = np.empty(k.shape[0], dtype=np.int64)
+    start = np.empty(nkeys + 1, dtype=np.int64)
+    _check(lib().oracle_reorder(k.shape[0], _ptr(k), _ptr(r), _ptr(i), int(nkeys), _ptr(perm), _ptr(start)),
+           "reorder")
     return perm, start
 
 

@@ -216,6 +216,59 @@ def test_stable_sort_equals_library_and_histogram():
     assert np.array_equal(np.diff(start), np.bincount(k, minlength=50))
 
 
+def test_reorder_equals_library_lexsort():
+    """Sec. 3 step xii with the recycling reading: by key; within a key the
+    particles that stayed, in their current order, then the re-created ones by
+    id.  numpy's stable lexsort on (tie-break, recycled flag, key) is the
+    library statement of the same order."""
+    rng = np.random.default_rng(11)
+    n, nk = 6000, 97
+    k = rng.integers(0, nk, n).astype(np.uint32)
+    rec = (rng.random(n) < 0.2).astype(np.uint8)
+    ids = rng.permutation(10 * n)[:n].astype(np.int64)
+    perm, start = O.reorder(k, rec, ids, nk)
+    tie = np.where(rec != 0, ids, np.arange(n))
+    assert np.array_equal(perm, np.lexsort((tie, rec, k)))
+    assert np.array_equal(np.diff(start), np.bincount(k, minlength=nk))
+    # no recycled particle: the plain stable sort
+    perm0, start0 = O.reorder(k, np.zeros(n, np.uint8), ids, nk)
+    assert np.array_equal(perm0, np.argsort(k, kind="stable"))
+    assert np.array_equal(start0, start)
+
+
+@pytest.mark.parametrize("case", ["cylinder", "periodic"])
+def test_reorder_inside_a_step_follows_the_rule(case):
+    """The oracle's own step re-orders by reorder(): from the same start, one
+    step with re-ordering equals one step without it followed by the rule
+    applied to that state (the first step's arithmetic is the same in both)."""
+    if case == "cylinder":   # Mach 3: particles leave at +x and are re-created at -x in step 1
+        p = I.cylinder(nx=32, ny=16, center=(0.4, 0.5), radius=0.1, mach=3.0, seed=3)
+    else:
+        p = I.uniform_flow(dim=3, n=(8, 6, 5), vel=(2.0, -1.5, 1.0), degree=2, shift=0.2)
+    a = _sim(p)
+    b = O.OracleSim(dict(p.cfg, sort_interval=0))
+    b.add_particles(p.x, p.v, p.mass, p.rho, p.e)
+    if p.mask is not None:
+        b.set_obstacle_mask(p.mask, p.normals)
+    assert np.array_equal(a.read("ID"), b.read("ID"))
+    gen0 = b.read("GEN")
+    a.step(1)
+    b.step(1)
+    ids = b.read("ID").astype(np.int64)
+    rec = (b.read("GEN") != gen0).astype(np.uint8)
+    keys = b.read("KEY").astype(np.uint32)
+    perm, start = O.reorder(keys, rec, ids, a.sizes()["keys"])
+    if case == "cylinder":
+        assert rec.sum() > 0
+    assert not np.array_equal(perm, np.arange(len(perm)))
+    assert np.array_equal(a.read("ID").astype(np.int64), ids[perm])
+    assert np.array_equal(a.read("CELLSTART").astype(np.int64), start)
+    assert np.array_equal(a.read("KEY").astype(np.uint32), keys[perm])
+    assert np.array_equal(a.read("X"), b.read("X")[:, perm])
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("degree", [1, 2])
 @pytest.mark.parametrize("dim", [2, 3])
 def test_keys_locate_particle_in_its_span(dim, degree):
