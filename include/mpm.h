@@ -89,7 +89,7 @@ enum {
     MPM_FIELD_X = 0, MPM_FIELD_V = 1, MPM_FIELD_M = 2, MPM_FIELD_RHO = 3, MPM_FIELD_E = 4,
     MPM_FIELD_P = 5, MPM_FIELD_Q = 6, MPM_FIELD_ID = 7, MPM_FIELD_KEY = 8,
     MPM_FIELD_CELLSTART = 9, MPM_FIELD_GRID_M = 10, MPM_FIELD_GRID_MV = 11,
-    MPM_FIELD_GRID_F = 12, MPM_FIELD_GRID_MV2 = 13, MPM_FIELD_CLOCK = 14
+    MPM_FIELD_GRID_F = 12, MPM_FIELD_GRID_MV2 = 13, MPM_FIELD_CLOCK = 14, MPM_FIELD_GEN = 16
 };
 
 typedef struct {
@@ -111,7 +111,9 @@ typedef struct {
                                 leaving through an outflow face for the g-th time draws
                                 from counter (g, 0, id, 0) */
     int tile[3];             /* spans per tile per axis, powers of two <= 64; 0 selects
-                                32 x 4 x 4 (3D) / 32 x 8 (2D) */
+                                16 x 8 x 4 (3D) / 32 x 8 (2D).  The tiles define the
+                                key numbering, so they fix the KEY and CELLSTART
+                                outputs (see "Span and key" above) */
     void* stream;            /* cudaStream_t to run on; NULL: the library's own stream */
     /* Optional device allocator (e.g. a framework's caching allocator):
        alloc(bytes, ctx) returns device memory or NULL; free(ptr, ctx).
@@ -184,19 +186,41 @@ mpm_status mpm_step_async(mpm_sim* sim, int64_t nsteps, double dt, double t_end)
 /* Wait for queued work; report device errors. */
 mpm_status mpm_sync(mpm_sim* sim);
 
-/* Copy a field to the host buffer out (count doubles, at least
- * mpm_field_size(sim, field), else MPM_EINVAL).  Particle fields are in the
- * current (key) order; ID gives the input numbering.  GRID_* are the raw
- * P2G sums of the last step before boundary conditions (GRID_MV2 the second
- * momentum P2G).  CLOCK = {t, dt_next, steps}. */
+/* Copy a field to the host buffer out: the outputs of the time loop (the
+ * device-to-host copies of Sec. 3 step xi and of the final output after
+ * Algorithm 1; KEY and CELLSTART are the connectivity of step x in the
+ * order of the re-order of step xii).  out holds count doubles, at least
+ * mpm_field_size(sim, field), else MPM_EINVAL.
+ *   X, V           dim x n, structure of arrays
+ *   M, RHO, E, Q   mass, density, specific internal energy, artificial
+ *                  viscosity (eq. muart) of each particle
+ *   P              pressure of the ideal-gas law (eq. pressures),
+ *                  (gamma - 1) rho e, evaluated on the device in the storage
+ *                  precision exactly as the step kernels evaluate it, then
+ *                  widened to double
+ *   ID             the input numbering (running count of mpm_add_particles)
+ *   KEY            span key of each particle (tile-major, see above)
+ *   CELLSTART      keys + 1 entries: first position of each key
+ *   GEN            times each particle has been re-created at the inflow
+ *                  (Sec. 4.1); the counter g of its next Philox draw
+ *   GRID_*         the raw P2G sums of the last step before boundary
+ *                  conditions (GRID_MV2 the second momentum P2G)
+ *   CLOCK          {t, dt_next, steps}
+ * Particle fields are in the current (key) order.  Synchronous.  Errors:
+ * MPM_EINVAL (unknown field, short buffer, NULL out), MPM_ESTATE (poisoned
+ * or in a batch), MPM_ENOMEM, MPM_ECUDA, or the device error the call
+ * observes. */
 mpm_status mpm_read_state(mpm_sim* sim, int field, double* out, int64_t count);
 /* Raw int64 grid sums of the fixed-point mode (GRID_M/MV/F/MV2 only). */
 mpm_status mpm_read_grid_fixed(mpm_sim* sim, int field, int64_t* out, int64_t count);
 /* Number of doubles a field needs, or -1. */
 int64_t mpm_field_size(const mpm_sim* sim, int field);
 
-/* FP64 sums over particles: {sum M, sum M (e + |V|^2/2), sum M V_x, _y, _z},
- * reduced on the device in a fixed order. */
+/* Conservation diagnostics of the state (mass, total energy and momentum,
+ * the quantities whose balance Sec. 2.1's equations state): FP64 sums over
+ * particles {sum M, sum M (e + |V|^2/2), sum M V_x, _y, _z}, reduced on the
+ * device in a fixed order, so repeated calls on the same state agree bit for
+ * bit.  Synchronous.  Errors as for mpm_read_state. */
 mpm_status mpm_conservation(mpm_sim* sim, double out[5]);
 /* {particles, nodes, keys, steps done}. */
 mpm_status mpm_sizes(const mpm_sim* sim, int64_t out[4]);
@@ -211,23 +235,30 @@ mpm_status mpm_profile_read(mpm_sim* sim, double out[8], int64_t counts[8], int 
 
 /* Stable sort of caller-supplied span keys that allocates no device memory.
  * The paper has no counterpart: this is the library's re-order step (a1)
- * offered to callers that must not call cudaMalloc -- code recording into a
- * CUDA graph, components confined to another framework's memory pool, or
- * loops where an allocation could synchronise the device.  Its scratch lives
- * in fixed device arrays inside the library (3.1 MiB per GPU that loads the
- * library, held until the process exits), so the input size is capped.
+ * offered to callers that must not call cudaMalloc -- components confined to
+ * another framework's memory pool, which must not grow the device footprint
+ * behind its back, or latency-critical loops where an allocation could
+ * synchronise the device.  Its scratch lives in fixed device arrays inside
+ * the library (3.1 MiB per GPU that loads the library, held until the
+ * process exits), so the input size is capped.
  *   keys        device pointer, n keys, each < nkeys (not modified)
  *   n           0 <= n <= MPM_SORT_STATIC_MAX_KEYS, else MPM_EINVAL
  *   nkeys       1 <= nkeys <= MPM_SORT_STATIC_MAX_SPANS, else MPM_EINVAL
  *   perm        device pointer, n entries: perm[j] = index of the key placed
  *               at position j (equal keys keep their input order)
- *   cell_start  device pointer, nkeys + 1 entries: first position of each key
+ *   cell_start  device pointer, nkeys + 1 entries: first position of each
+ *               key; cell_start[nkeys] = n.  If some key is >= nkeys the
+ *               call writes 0xffffffff to cell_start[nkeys] instead (the
+ *               check runs on the device); perm and the other cell starts
+ *               are then unspecified
  *   stream      cudaStream_t the work is queued on (NULL: the default stream)
  * The call only queues kernels and returns; the outputs are valid once the
  * stream reaches them.  The first call on a device looks up the scratch
- * addresses, so make it before any stream capture.  All calls on a device
- * share the scratch: calls whose work overlaps on the GPU (other streams,
- * other threads) race and must be serialised by the caller. */
+ * addresses and keeps them for the life of the process, so the call must not
+ * be used after cudaDeviceReset.  All calls on a device share the scratch,
+ * which keeps the last call's contents: calls whose work overlaps on the GPU
+ * (other streams, other threads) race and must be serialised by the
+ * caller. */
 #define MPM_SORT_STATIC_MAX_KEYS 262144
 #define MPM_SORT_STATIC_MAX_SPANS 16777216
 mpm_status mpm_sort_keys_static(const uint32_t* keys, int64_t n, int64_t nkeys, uint32_t* perm,

@@ -1202,7 +1202,7 @@ int64_t mpm_field_size(const mpm_sim* s, int field)
     switch (field) {
     case MPM_FIELD_X: case MPM_FIELD_V: return d * s->np;
     case MPM_FIELD_M: case MPM_FIELD_RHO: case MPM_FIELD_E: case MPM_FIELD_P: case MPM_FIELD_Q:
-    case MPM_FIELD_ID: case MPM_FIELD_KEY: return s->np;
+    case MPM_FIELD_ID: case MPM_FIELD_KEY: case MPM_FIELD_GEN: return s->np;
     case MPM_FIELD_CELLSTART: return s->G.nkey + 1;
     case MPM_FIELD_GRID_M: return s->G.nnode;
     case MPM_FIELD_GRID_MV: case MPM_FIELD_GRID_F: case MPM_FIELD_GRID_MV2: return d * s->G.nnode;
@@ -1279,13 +1279,30 @@ mpm_status mpm_read_state(mpm_sim* s, int field, double* out, int64_t count)
     case MPM_FIELD_E: return read_real(s, b.E, np, out);
     case MPM_FIELD_Q: return read_real(s, b.Q, np, out);
     case MPM_FIELD_P: {
-        std::vector<double> r(np);
-        if ((st = read_real(s, b.rho, np, r.data()))) return st;
-        if ((st = read_real(s, b.E, np, out))) return st;
-        for (int64_t k = 0; k < np; ++k) out[k] = (s->G.gamma - 1.0) * r[k] * out[k];
-        return MPM_OK;
+        // evaluated on the device from the stored density and energy, as
+        // the step kernels evaluate it
+        if (np == 0) return MPM_OK;
+        void* tp = dalloc(s, (size_t)np * s->rsize);
+        if (!tp) return fail(s, MPM_ENOMEM, "device allocation failed");
+        if (s->rsize == 8)
+            k_pressure<double><<<nblk(np), kThreads, 0, s->stream>>>((const double*)b.rho, (const double*)b.E,
+                                                                    s->G.gamma - 1.0, (double*)tp, np);
+        else
+            k_pressure<float><<<nblk(np), kThreads, 0, s->stream>>>((const float*)b.rho, (const float*)b.E,
+                                                                   (float)(s->G.gamma - 1.0), (float*)tp, np);
+        st = read_real(s, tp, np, out);
+        dfree(s, tp);
+        return st;
     }
     case MPM_FIELD_ID: return read_u32(s, b.id, np, out);
+    case MPM_FIELD_GEN:
+        // the recycle counts move with the particles only where recycling
+        // exists (an inflow face); elsewhere they are all 0
+        if (s->G.inflow_face < 0) {
+            for (int64_t k = 0; k < np; ++k) out[k] = 0.0;
+            return MPM_OK;
+        }
+        return read_u32(s, b.gen, np, out);
     case MPM_FIELD_KEY: {
         // keys of the current order, expanded from its cell starts
         if (np == 0) return MPM_OK;

@@ -1060,6 +1060,15 @@ __global__ void k_to_double(const R* in, double* out, int64_t n)
     if (i < n) out[i] = (double)in[i];
 }
 
+// Pressure of the ideal-gas law (eq. pressures), P = (gamma - 1) rho e, in the
+// storage precision with the operation order of the step kernels.
+template <class R>
+__global__ void k_pressure(const R* rho, const R* E, R gm1, R* out, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = Op<R>::mul(Op<R>::mul(gm1, rho[i]), E[i]);
+}
+
 // Checks of uploaded particle values; sets `bit` in *bad when one fails.
 // mode 0: finite; 1: finite and > 0; 2: lo <= v <= hi; 3: lo <= v < hi.
 __global__ void k_check_values(const double* in, int64_t n, int mode, double lo, double hi, unsigned bit,

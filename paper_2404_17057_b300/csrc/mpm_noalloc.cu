@@ -1,14 +1,12 @@
 // mpm_noalloc.cu -- mpm_sort_keys_static: the stable key re-order for callers
 // that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc (or cannot afford to): code that runs
-// while a CUDA stream is being captured into a graph, where allocating is
-// not allowed; components that live inside another framework's memory pool
-// and must not grow the device footprint behind its back; and latency-
-// critical loops where an allocation can synchronise the device.  For them
-// this entry point keeps all of its scratch space in fixed arrays that are
-// part of the library image itself.  Every GPU that loads the library holds
-// these arrays (3.1 MiB) until the process exits.
+// Some callers cannot call cudaMalloc: components that live inside another
+// framework's memory pool and must not grow the device footprint behind its
+// back, and latency-critical loops where an allocation can synchronise the
+// device.  For them this entry point keeps all of its scratch space in fixed
+// arrays that are part of the library image itself.  Every GPU that loads
+// the library holds these arrays (3.1 MiB) until the process exits.
 //
 // This file is compiled into the same translation unit as mpm_api.cu (it is
 // included at its end) and reuses the radix-sort kernels of mpm_sort.cuh.
@@ -26,12 +24,15 @@ static __device__ __align__(256) uint32_t g_sort_keys[2][kStaticSortMaxKeys];
 static __device__ __align__(256) uint32_t g_sort_idx[kStaticSortMaxKeys];
 static __device__ __align__(256) uint32_t g_sort_hist[kStaticSortHist];
 static __device__ __align__(256) uint32_t g_sort_part[kScanTile];
+// set by a call that meets a key >= nkeys, cleared by the same call
+static __device__ __align__(256) uint32_t g_sort_bad[4];
 
 struct StaticSortScratch {
     uint32_t* keys[2];
     uint32_t* idx;
     uint32_t* hist;
     uint32_t* part;
+    uint32_t* bad;
     bool ready;
 };
 
@@ -58,10 +59,30 @@ static cudaError_t static_sort_scratch(int dev, StaticSortScratch* out)
         s.hist = static_cast<uint32_t*>(p);
         if ((e = cudaGetSymbolAddress(&p, g_sort_part)) != cudaSuccess) return e;
         s.part = static_cast<uint32_t*>(p);
+        if ((e = cudaGetSymbolAddress(&p, g_sort_bad)) != cudaSuccess) return e;
+        s.bad = static_cast<uint32_t*>(p);
         s.ready = true;
     }
     *out = s;
     return cudaSuccess;
+}
+
+// Any key >= nkeys marks the call as invalid.
+__global__ void k_static_sort_verify(const uint32_t* __restrict__ keys, int64_t n, int64_t nkeys, uint32_t* bad)
+{
+    bool b = false;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        b = b || (int64_t)keys[j] >= nkeys;
+    if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
+// After the cell starts are written: an invalid call replaces
+// cell_start[nkeys] (n otherwise) by 0xffffffff; the flag is cleared for the
+// next call.
+__global__ void k_static_sort_finish(uint32_t* bad, uint32_t* cell_start, int64_t nkeys)
+{
+    if (*bad) cell_start[nkeys] = 0xffffffffu;
+    *bad = 0u;
 }
 
 }  // namespace mpm
@@ -96,8 +117,10 @@ extern "C" mpm_status mpm_sort_keys_static(const uint32_t* keys, int64_t n, int6
     const unsigned nb = (unsigned)std::max<int64_t>(1, (n + kSortTile - 1) / kSortTile);
     const int64_t nhist = (int64_t)(1 << dbits) * nb;
     if (n > 0) {
-        // the digit histograms are fully rewritten by every pass; nothing
-        // in the scratch has to start at zero
+        // the digit histograms are fully rewritten by every pass; only the
+        // invalid-key flag must start at zero (every call clears it at its end)
+        k_static_sort_verify<<<(unsigned)std::min<int64_t>(256, (n + 255) / 256), 256, 0, st>>>(keys, n, nkeys,
+                                                                                              sc.bad);
         const uint32_t* kin = keys;
         const uint32_t* iin = nullptr;
         for (int pass = 0; pass < passes; ++pass) {
@@ -117,6 +140,7 @@ extern "C" mpm_status mpm_sort_keys_static(const uint32_t* keys, int64_t n, int6
     } else {
         k_cell_start<<<1, 256, 0, st>>>(keys, 0, nkeys, cell_start, nullptr);
     }
+    k_static_sort_finish<<<1, 1, 0, st>>>(sc.bad, cell_start, nkeys);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, MPM_ECUDA, std::string("mpm_sort_keys_static: ") + cudaGetErrorString(e));
     return MPM_OK;

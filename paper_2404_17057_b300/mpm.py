@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_PKG, "libmpm.so")
 BC = {"wall": 0, "periodic": 1, "inflow": 2, "outflow": 3}
 PRECISION = {"fp32": 0, "fp32_fixed64": 1, "fp64": 2, "fp32_coloured": 3}
 FIELDS = {"X": 0, "V": 1, "M": 2, "RHO": 3, "E": 4, "P": 5, "Q": 6, "ID": 7, "KEY": 8,
-          "CELLSTART": 9, "GRID_M": 10, "GRID_MV": 11, "GRID_F": 12, "GRID_MV2": 13, "CLOCK": 14}
+          "CELLSTART": 9, "GRID_M": 10, "GRID_MV": 11, "GRID_F": 12, "GRID_MV2": 13, "CLOCK": 14,
+          "GEN": 16}
 STATUS = {0: "MPM_OK", 1: "MPM_EINVAL", 2: "MPM_ENOMEM", 3: "MPM_ECUDA", 4: "MPM_ESTATE",
           5: "MPM_ENONFINITE", 6: "MPM_ETIMEOUT", 7: "MPM_EUNSUPPORTED", 8: "MPM_ECFL"}
 
