@@ -49,9 +49,9 @@ __device__ __forceinline__ void weights1d(float fx, float* w, float* dw)
 
 // Offset and weights of a particle along one axis when its span is known
 // (the thread's span, first support node cb): no float<->int conversion on
-// the critical path.  The span of the particle was computed with the same
-// rounding when it was sorted; the range test catches an inconsistent order
-// (fx may sit one ulp outside the nominal interval at a span edge).
+// the critical path.  Returns whether fx lies in the span's nominal interval
+// (it may sit one ulp outside at a span edge); the P2G kernel ignores it: the
+// G2PD step checks every particle's span against its tile.
 template <int P, bool PER>
 __device__ __forceinline__ bool axis_known(float x, float lo, float ih, float cb, float n, float* w, float* dw)
 {
@@ -218,7 +218,6 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int group = warp & 1;
     const int nrows = G.Tvol >> 5;
-    int err = 0;
     for (int r = 0; r < nrows; ++r) {
         const int s = (r << 5) + lane;
         // empty spans take part in the warp-wide row adds with zeros
@@ -260,10 +259,9 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
                     nM = pt.M[k + 1];
                 }
                 float w[3][3], dw[3][3];
-                bool ok = axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
-                ok &= axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
-                if (D == 3) ok &= axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
-                if (!ok) { err = 1; continue; }
+                axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
+                axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+                if (D == 3) axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
                 float2 c0[NS], c1[NS];
                 float c3[NS];
                 const float mv0 = M * v[0], mv1 = M * v[1], mv2 = D == 3 ? M * v[2] : 0.f;
@@ -331,10 +329,9 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
                     nM = pt.M[k + 1]; nr = pt.rho[k + 1]; nE = pt.E[k + 1]; nQ = pt.Q[k + 1];
                 }
                 float w[3][3], dw[3][3];
-                bool ok = axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
-                ok &= axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
-                if (D == 3) ok &= axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
-                if (!ok) { err = 1; continue; }
+                axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
+                axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+                if (D == 3) axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
                 const float F = fmaf(gm1 * rho, E, Q) * __fdividef(M, rho) * ih;
                 if (D == 3) {
                     float Fx[NS], Fd[NS];
@@ -382,7 +379,6 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
             }
         }
     }
-    if (err) atomicOr(&clk->err, ERR_TILE);
     __syncthreads();
     flush_window<D, P>(G, so, sm, NF, out);
 }
