@@ -308,17 +308,38 @@ def test_fp32_cylinder_100_steps_within_target(precision):
     g.close()
 
 
+FIXED_TOL = 2e-5   # the fixed-point path's bound: five times below the FP32 target
+
+
 def test_fp32_fixed_cylinder_100_steps_within_target():
-    p = f32(I.cylinder(nx=128, ny=64, seed=1, precision="fp32_fixed64"))
-    g, o = gpu_sim(p), oracle_sim(p)
-    g.step(100)
+    """The fixed-point path's tolerance, tightened: after 100 steps the
+    relative L1 error of rho, P and each velocity component against the FP64
+    oracle is at most 2e-5 (the FP32 target is 1e-4), with the literal unit
+    (1) and with units normalised to the problem.  The float-atomic path runs
+    beside it: both evaluate every contribution in binary32, so their errors
+    are of the same size (the integer sums only remove the dependence on the
+    order of the additions, which makes the result bit-reproducible)."""
+    base = f32(I.cylinder(nx=128, ny=64, seed=1, precision="fp32"))
+    o = oracle_sim(base)
     o.step(100)
-    r = compare_fields(g, o, 1e-4, 2, exclude_far=0.25)
-    assert r["excluded"] == 0
-    g.close()
+    errs = {}
+    for name, prec, unit in (("float", "fp32", None), ("fixed_unit1", "fp32_fixed64", None),
+                             ("fixed_normalised", "fp32_fixed64", I.normalised_fixed_units(base))):
+        p = f32(I.cylinder(nx=128, ny=64, seed=1, precision=prec))
+        if unit is not None:
+            p.cfg["fixed_unit"] = list(unit)
+        g = gpu_sim(p)
+        g.step(100)
+        errs[name] = compare_fields(g, o, 1e-4, 2, exclude_far=0.25)
+        assert errs[name]["excluded"] == 0
+        g.close()
+    for name in ("fixed_unit1", "fixed_normalised"):
+        for k in ("RHO", "P", "V0", "V1"):
+            assert errs[name][k] <= FIXED_TOL, (name, k, errs)
+    print({n: {k: float(v) for k, v in e.items()} for n, e in errs.items()})
 
 
-@pytest.mark.parametrize("precision,steps,tol", [("fp32_fixed64", 100, 1e-4), ("fp64", 40, 1e-9)])
+@pytest.mark.parametrize("precision,steps,tol", [("fp32_fixed64", 100, FIXED_TOL), ("fp64", 40, 1e-9)])
 def test_span_kernel_cylinder_matches_oracle(precision, steps, tol):
     # 160 x 80 cells in 32 x 1 tiles: enough tiles for the 2D span-per-lane
     # kernels of the fixed-point and FP64 modes
