@@ -94,7 +94,7 @@ def test_flow_past_a_profile_matches_the_oracle(precision, steps, tol):
 
 
 def test_aerofoil_flow_is_faster_over_the_upper_surface():
-    """The aerofoil case (Sec. 4.1): at 25 degrees the flow speeds up
+    """The aerofoil case (Sec. 4.1, Fig. oat15a): at 25 degrees the flow speeds up
     approaching the profile, more over the upper surface than under it.  Mean
     particle speed in bands along 10-90% of the chord, up to 0.11 chords from
     the chord line, after t = 0.3 (about two chord passages)."""
