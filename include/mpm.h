@@ -205,7 +205,9 @@ mpm_status mpm_sync(mpm_sim* sim);
  *                  (Sec. 4.1); the counter g of its next Philox draw
  *   GRID_*         the raw P2G sums of the last step before boundary
  *                  conditions (GRID_MV2 the second momentum P2G)
- *   CLOCK          {t, dt_next, steps}
+ *   CLOCK          {t, dt_next, steps, relayouts}: relayouts counts the steps
+ *                  whose re-order gave every tile a new region (a tile had
+ *                  outgrown its own)
  * Particle fields are in the current (key) order.  Synchronous.  Errors:
  * MPM_EINVAL (unknown field, short buffer, NULL out), MPM_ESTATE (poisoned
  * or in a batch), MPM_ENOMEM, MPM_ECUDA, or the device error the call

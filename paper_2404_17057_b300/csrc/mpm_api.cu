@@ -65,12 +65,18 @@ struct mpm_sim {
     uint8_t* mask = nullptr;
     void* nrm = nullptr;           // d x nodes of type R
     Clock* clk = nullptr;
-    uint32_t* cs[2] = {nullptr, nullptr};   // cell starts of particle buffer b
+    uint32_t* cs[2] = {nullptr, nullptr};   // per-tile cell starts of the tiles in buffer b
+    uint8_t* tpar[2] = {nullptr, nullptr};  // buffer of each tile before step parity 0 / 1
+    uint32_t* tbase = nullptr;              // tile regions (ntiles + 1 slots)
+    uint32_t* tbase_next = nullptr;         // regions of a relayout
+    uint32_t* tcount = nullptr;             // particles of each tile after a step
+    uint32_t* dirty = nullptr;              // tiles whose span lists change in a step
+    uint32_t* toff = nullptr;               // particles before each tile (reads; ntiles + 1)
+    int64_t nslots = 0;                     // slots of each particle buffer
     uint32_t* col_tiles = nullptr;          // colour passes: tiles grouped by colour
     std::vector<int> col_off;               // colour c: col_tiles[col_off[c] .. col_off[c+1])
     uint32_t* count = nullptr;              // particles per new span (step re-order)
-    uint32_t* cscan_part = nullptr;         // scan partials over the spans
-    uint32_t* perm = nullptr;               // old index of each re-ordered particle
+    uint32_t* cscan_part = nullptr;         // scan partials over the tiles
     uint2* far = nullptr;                   // recycled particles of a step
     uint32_t far_cap = 0;
     unsigned long long* ring = nullptr;     // per tile: ring parts entered in a step
@@ -160,6 +166,11 @@ struct Vtbl {
                    cudaStream_t st);
     void (*cfl_init)(mpm_sim* s, cudaStream_t st);
     void (*cons)(mpm_sim* s, cudaStream_t st);
+    // the particle field `f` (0 x, 1 v, 2 M, 3 rho, 4 E, 5 Q, 6 id, 7 gen;
+    // component a) in key order into out (device); needs s->toff
+    void (*compact)(mpm_sim* s, int f, int a, void* out, cudaStream_t st);
+    void (*tile_counts)(mpm_sim* s, uint32_t* counts, cudaStream_t st);
+    void (*spread)(mpm_sim* s, const uint32_t* cc, cudaStream_t st);
     void (*from_double)(const double* in, void* out, int64_t n, cudaStream_t st);
     cudaError_t (*set_smem)(const Geom& G);
     size_t (*smem)(const Geom& G, int kernel);
@@ -207,6 +218,21 @@ Grid<A, R> grid_view(const mpm_sim* s)
     }
     g.mask = s->mask;
     return g;
+}
+
+void order_offsets(mpm_sim* s, cudaStream_t st);
+
+// The particle state with the tile-buffer table of step parity b.
+template <class R>
+TileState<R> tstate(const mpm_sim* s, int b)
+{
+    TileState<R> ts;
+    ts.pt[0] = parts<R>(s->buf[0]);
+    ts.pt[1] = parts<R>(s->buf[1]);
+    ts.cs[0] = s->cs[0];
+    ts.cs[1] = s->cs[1];
+    ts.tpar = s->tpar[b];
+    return ts;
 }
 
 // Colour passes of a coloured simulation (one pass over all tiles otherwise).
@@ -288,10 +314,9 @@ struct Impl {
     static void step_kernels(mpm_sim* s, int which, cudaStream_t st)
     {
         const Geom& G = s->G;
-        Particles<R> pt = parts<R>(s->buf[s->cur]);
+        const TileState<R> ts = tstate<R>(s, s->cur);
         Grid<A, R> gr = grid_view<A, R>(s);
-        const uint32_t* cs = s->cs[s->cur];
-        const Reorder ro = {s->count, s->far, s->far_cap, s->mwords, s->ring};
+        const Reorder ro = {s->count, s->far, s->far_cap, s->mwords, s->ring, s->dirty};
         if (which & 1) {
             k_zero<<<std::min<int64_t>(nblk(s->grid_bytes / 16), s->sms * 8), kThreads, 0, st>>>(
                 (uint4*)s->grid, (int64_t)(s->grid_bytes / 16), &s->clk->active);
@@ -302,14 +327,14 @@ struct Impl {
                     const uint32_t* tl = colour_tiles(s, c);
                     const unsigned nb = colour_blocks(s, c);
                     if (nb == 0) continue;
-                    if (per) k_p2g_span<D, P, true><<<nb, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk, tl);
-                    else k_p2g_span<D, P, false><<<nb, kP2GThreads, smem(G, 0), st>>>(G, pt, o, cs, s->clk, tl);
+                    if (per) k_p2g_span<D, P, true><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
+                    else k_p2g_span<D, P, false><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
                 }
                 s->launches += ncolours(s) - 1;
             } else if (kSpan2d && span2d(s)) {
-                k_p2g_span2d<P, R, A><<<G.ntiles, kP2GSpan2dThreads, smem(G, 0), st>>>(G, pt, gr, cs, s->clk);
+                k_p2g_span2d<P, R, A><<<G.ntiles, kP2GSpan2dThreads, smem(G, 0), st>>>(G, ts, gr, s->clk);
             } else {
-                k_p2g<D, P, R, A><<<G.ntiles, kThreads, smem(G, 0), st>>>(G, pt, gr, cs, s->clk);
+                k_p2g<D, P, R, A><<<G.ntiles, kThreads, smem(G, 0), st>>>(G, ts, gr, s->clk);
             }
             s->launches += 2;
         }
@@ -322,35 +347,57 @@ struct Impl {
                     const unsigned nb = colour_blocks(s, c);
                     if (nb == 0) continue;
                     if (per)
-                        k_grid_g2p_span<D, P, true><<<nb, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, pt, gr, o, cs,
-                                                                                                s->clk, tl);
+                        k_grid_g2p_span<D, P, true><<<nb, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, ts, gr, o, s->clk,
+                                                                                                tl);
                     else
-                        k_grid_g2p_span<D, P, false><<<nb, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, pt, gr, o, cs,
-                                                                                                 s->clk, tl);
+                        k_grid_g2p_span<D, P, false><<<nb, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, ts, gr, o, s->clk,
+                                                                                                 tl);
                 }
                 s->launches += ncolours(s) - 1;
             } else if (kSpan2d && span2d(s)) {
-                k_grid_g2p_span2d<P, R, A><<<G.ntiles, kG2PSpan2dThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
+                k_grid_g2p_span2d<P, R, A><<<G.ntiles, kG2PSpan2dThreads, smem(G, 1), st>>>(G, ts, gr, s->clk);
             } else {
-                k_grid_g2p<D, P, R, A><<<G.ntiles, kThreads, smem(G, 1), st>>>(G, pt, gr, cs, s->clk);
+                k_grid_g2p<D, P, R, A><<<G.ntiles, kThreads, smem(G, 1), st>>>(G, ts, gr, s->clk);
             }
             s->launches += 1;
         }
         if (which & 4) {
             if constexpr (kFast3)
-                k_g2pd_fast<D, P, A><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, pt, gr, cs, s->clk, ro);
+                k_g2pd_fast<D, P, A><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
             else
-                k_g2pd<D, P, R, A><<<G.ntiles, kThreads, smem(G, 2), st>>>(G, pt, gr, cs, s->clk, ro);
+                k_g2pd<D, P, R, A><<<G.ntiles, kThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
             s->launches += 1;
         }
     }
+    static ReorderArgs<R> rargs(const mpm_sim* s, int b)
+    {
+        ReorderArgs<R> a;
+        a.pt[0] = parts<R>(s->buf[0]);
+        a.pt[1] = parts<R>(s->buf[1]);
+        a.cs[0] = s->cs[0];
+        a.cs[1] = s->cs[1];
+        a.tpar_old = s->tpar[b];
+        a.tpar_new = s->tpar[1 - b];
+        a.tbase = s->tbase;
+        a.tbase_next = s->tbase_next;
+        a.tcount = s->tcount;
+        a.ro = {s->count, s->far, s->far_cap, s->mwords, s->ring, s->dirty};
+        a.clk = s->clk;
+        return a;
+    }
+    // Pass 0 over the changed tiles; the relayout kernels return at once
+    // unless a tile overflowed its region.
     static void reorder(mpm_sim* s, cudaStream_t st)
     {
-        const int b = s->cur;
-        k_reorder<D, R><<<s->G.ntiles, kReorderThreads, reorder_smem(s->G), st>>>(
-            s->G, parts<R>(s->buf[b]), parts<R>(s->buf[1 - b]), s->cs[b], s->cs[1 - b], s->count, s->perm, s->np,
-            s->ring, s->mwords, s->clk);
-        s->launches += 1;
+        const Geom& G = s->G;
+        const ReorderArgs<R> a = rargs(s, s->cur);
+        const unsigned nb = (unsigned)std::min<int64_t>(G.ntiles, (int64_t)s->sms * 3);
+        k_reorder<D, R><<<nb, kReorderThreads, reorder_smem(G), st>>>(G, a, 0);
+        k_consolidate<D, R><<<nb, kReorderThreads, 0, st>>>(G, a);
+        k_relayout_bases<<<1, 1024, 0, st>>>(s->tcount, G.ntiles, s->tbase_next, s->clk);
+        k_reorder<D, R><<<nb, kReorderThreads, reorder_smem(G), st>>>(G, a, 1);
+        k_reorder_done<<<nblk(G.ntiles), kThreads, 0, st>>>(G, a.ro, s->clk, s->tbase, s->tbase_next);
+        s->launches += 5;
     }
     static FieldPtrs p2g_fields(const Grid<A, R>& gr)
     {
@@ -382,19 +429,28 @@ struct Impl {
         }
         d.cs[0] = s->cs[0];
         d.cs[1] = s->cs[1];
-        d.ro = {s->count, s->far, s->far_cap, s->mwords, s->ring};
-        d.perm = s->perm;
+        d.tpar[0] = s->tpar[0];
+        d.tpar[1] = s->tpar[1];
+        d.tbase = s->tbase;
+        d.tbase_next = s->tbase_next;
+        d.tcount = s->tcount;
+        d.ro = {s->count, s->far, s->far_cap, s->mwords, s->ring, s->dirty};
         d.np = s->np;
         d.clk = s->clk;
         memcpy(out, &d, sizeof d);
     }
-    // stage 0: P2G, 1: grid + G2P + P2G, 2: G2PD + update, 3: re-order
+    // stage 0: P2G, 1: grid + G2P + P2G, 2: G2PD + update, 3: re-order of
+    // the changed tiles, 4 and 5: relayout (consolidation, rebuild)
     static void blaunch(int stage, const void* dv, const TileRef* tl, int ntl, size_t sm, int per, cudaStream_t st)
     {
         const BatchProb<R, A>* d = static_cast<const BatchProb<R, A>*>(dv);
         if (ntl <= 0) return;
-        if (stage == 3) {
-            kb_reorder<D, R, A><<<ntl, kReorderThreads, sm, st>>>(d, tl);
+        if (stage == 3 || stage == 5) {
+            kb_reorder<D, R, A><<<ntl, kReorderThreads, sm, st>>>(d, tl, stage == 5 ? 1 : 0);
+            return;
+        }
+        if (stage == 4) {
+            kb_consolidate<D, R, A><<<ntl, kReorderThreads, 0, st>>>(d, tl);
             return;
         }
         if (stage == 2) {
@@ -473,14 +529,16 @@ struct Impl {
     static void cfl_init(mpm_sim* s, cudaStream_t st)
     {
         unsigned nb = std::max(1u, std::min(nblk(s->np), (unsigned)s->sms * 8u));
-        k_cfl_init<D, R><<<nb, kThreads, 0, st>>>(s->G, parts<R>(s->buf[s->cur]), s->np, s->clk);
+        order_offsets(s, st);
+        k_cfl_init<D, R><<<nb, kThreads, 0, st>>>(s->G, tstate<R>(s, s->cur), s->toff, s->np, s->clk);
         k_cfl_init_finish<<<1, 1, 0, st>>>(s->clk, s->G.cfl * s->G.h);
         s->launches += 2;
     }
     static void cons(mpm_sim* s, cudaStream_t st)
     {
         const int nb = 1024;
-        k_cons_partial<D, R><<<nb, 256, 0, st>>>(parts<R>(s->buf[s->cur]), s->np, s->cons_part);
+        order_offsets(s, st);
+        k_cons_partial<D, R><<<nb, 256, 0, st>>>(s->G, tstate<R>(s, s->cur), s->toff, s->np, s->cons_part);
         k_cons_final<<<1, kConsThreads, 0, st>>>(s->cons_part, nb, s->cons_out);
         s->launches += 2;
     }
@@ -488,14 +546,47 @@ struct Impl {
     {
         if (n > 0) k_from_double<R><<<nblk(n), kThreads, 0, st>>>(in, (R*)out, n);
     }
+    static void compact(mpm_sim* s, int f, int a, void* out, cudaStream_t st)
+    {
+        const TileState<R> ts = tstate<R>(s, s->cur);
+        const unsigned nb = std::max(1u, std::min(nblk(s->np), (unsigned)s->sms * 16u));
+        const Particles<R>& p0 = ts.pt[0];
+        const Particles<R>& p1 = ts.pt[1];
+        if (f <= 5) {
+            const R* a0 = f == 0 ? p0.x[a] : f == 1 ? p0.v[a] : f == 2 ? p0.M : f == 3 ? p0.rho : f == 4 ? p0.E : p0.Q;
+            const R* a1 = f == 0 ? p1.x[a] : f == 1 ? p1.v[a] : f == 2 ? p1.M : f == 3 ? p1.rho : f == 4 ? p1.E : p1.Q;
+            k_compact<R, R><<<nb, kThreads, 0, st>>>(s->G, ts, s->toff, a0, a1, (R*)out, s->np);
+        } else {
+            const uint32_t* a0 = f == 6 ? p0.id : p0.gen;
+            const uint32_t* a1 = f == 6 ? p1.id : p1.gen;
+            k_compact<uint32_t, R><<<nb, kThreads, 0, st>>>(s->G, ts, s->toff, a0, a1, (uint32_t*)out, s->np);
+        }
+        s->launches += 1;
+    }
+    static void tile_counts(mpm_sim* s, uint32_t* counts, cudaStream_t st)
+    {
+        k_tile_counts<R><<<nblk(s->G.ntiles), kThreads, 0, st>>>(s->G, tstate<R>(s, s->cur), counts);
+        s->launches += 1;
+    }
+    // the compact sorted state of buffer 1 (cell starts cc) into the regions
+    // of buffer 0; every tile in buffer 0
+    static void spread(mpm_sim* s, const uint32_t* cc, cudaStream_t st)
+    {
+        const unsigned nb = (unsigned)std::min<int64_t>(s->G.ntiles, (int64_t)s->sms * 8);
+        k_spread<D, R><<<nb, kThreads, 0, st>>>(s->G, parts<R>(s->buf[1]), parts<R>(s->buf[0]), cc, s->tbase,
+                                                s->cs[0]);
+        s->launches += 1;
+    }
 };
 
 template <int D, int P, class R, class A>
 const Vtbl* vtbl_of()
 {
     typedef Impl<D, P, R, A> I;
-    static const Vtbl v = {I::step_kernels, I::keys, I::gather, I::cfl_init, I::cons, I::from_double, I::set_smem,
-                           I::smem, I::reorder, sizeof(BatchProb<R, A>), I::bdesc_fill, I::blaunch, I::bset_smem};
+    static const Vtbl v = {I::step_kernels, I::keys,    I::gather,          I::cfl_init,
+                           I::cons,         I::compact, I::tile_counts,     I::spread,
+                           I::from_double,  I::set_smem, I::smem,           I::reorder,
+                           sizeof(BatchProb<R, A>), I::bdesc_fill, I::blaunch, I::bset_smem};
     return &v;
 }
 
@@ -651,48 +742,65 @@ struct RadixScratch {
     int passes = 0, bits = 0;
 };
 
-// Initial re-order of particles in any order: LSD radix passes over
-// (key, index), gather into the other buffer, cell starts of that buffer.
-// Swaps s->cur.
-void launch_sort(mpm_sim* s, const RadixScratch& rs, cudaStream_t st)
+// Particles before each tile in key order (s->toff, ntiles + 1 entries).
+void order_offsets(mpm_sim* s, cudaStream_t st)
+{
+    s->vt->tile_counts(s, s->toff, st);
+    scan_exclusive(s->toff, s->toff, s->G.ntiles, s->cscan_part, 1, st, &s->launches);
+}
+
+// Regions for the tile counts in s->tcount: region_slots each, in tile order.
+__global__ void k_region_bases(const uint32_t* tcount, int ntiles, uint32_t* tbase)
+{
+    relayout_bases_block(tcount, ntiles, tbase);
+}
+
+// Initial order of the particles of buffer 0 (any order, slots [0, n)): LSD
+// radix passes over (key, index), a gather into buffer 1 (compact key order)
+// and its cell starts cc (nkey + 1 entries), then every tile spread into its
+// region of buffer 0.
+void launch_sort(mpm_sim* s, const RadixScratch& rs, uint32_t* cc, cudaStream_t st)
 {
     const int64_t n = s->np;
-    if (n == 0) return;
-    const unsigned nb = (unsigned)((n + kSortTile - 1) / kSortTile);
-    const uint32_t* kin = s->buf[s->cur].key;
-    const uint32_t* iin = nullptr;
-    int o = 0;
-    for (int pass = 0; pass < rs.passes; ++pass) {
-        const int shift = pass * rs.bits;
-        k_radix_hist<<<nb, kSortThreads, 0, st>>>(kin, n, shift, rs.bits, rs.hist, nullptr);
-        scan_exclusive(rs.hist, rs.hist, (int64_t)(1 << rs.bits) * nb, rs.part, 0, st, &s->launches);
-        k_radix_scatter<<<nb, kSortThreads, 0, st>>>(kin, iin, rs.skeys[o], rs.sidx[o], n, shift, rs.bits, rs.hist,
-                                                      nullptr, pass == 0);
-        s->launches += 2;
-        kin = rs.skeys[o];
-        iin = rs.sidx[o];
-        o ^= 1;
+    const Geom& G = s->G;
+    if (n > 0) {
+        const unsigned nb = (unsigned)((n + kSortTile - 1) / kSortTile);
+        const uint32_t* kin = s->buf[0].key;
+        const uint32_t* iin = nullptr;
+        int o = 0;
+        for (int pass = 0; pass < rs.passes; ++pass) {
+            const int shift = pass * rs.bits;
+            k_radix_hist<<<nb, kSortThreads, 0, st>>>(kin, n, shift, rs.bits, rs.hist, nullptr);
+            scan_exclusive(rs.hist, rs.hist, (int64_t)(1 << rs.bits) * nb, rs.part, 0, st, &s->launches);
+            k_radix_scatter<<<nb, kSortThreads, 0, st>>>(kin, iin, rs.skeys[o], rs.sidx[o], n, shift, rs.bits, rs.hist,
+                                                          nullptr, pass == 0);
+            s->launches += 2;
+            kin = rs.skeys[o];
+            iin = rs.sidx[o];
+            o ^= 1;
+        }
+        s->vt->gather(s, 0, iin, nullptr, nullptr, st);
+        k_cell_start<<<nblk(n + 1), kThreads, 0, st>>>(kin, n, G.nkey, cc, nullptr);
+    } else {
+        k_cell_start<<<1, kThreads, 0, st>>>(nullptr, 0, G.nkey, cc, nullptr);
     }
-    s->vt->gather(s, s->cur, iin, nullptr, nullptr, st);
-    k_cell_start<<<nblk(n + 1), kThreads, 0, st>>>(kin, n, s->G.nkey, s->cs[1 - s->cur], nullptr);
-    s->launches += 1;
-    s->cur ^= 1;
+    k_tile_counts_compact<<<nblk(G.ntiles), kThreads, 0, st>>>(cc, G.ntiles, G.Tvol, s->tcount);
+    k_region_bases<<<1, 1024, 0, st>>>(s->tcount, G.ntiles, s->tbase);
+    s->vt->spread(s, cc, st);
+    cudaMemsetAsync(s->tpar[0], 0, (size_t)G.ntiles, st);
+    cudaMemsetAsync(s->tpar[1], 0, (size_t)G.ntiles, st);
+    s->launches += 3;
+    s->cur = 0;
 }
 
 // Per-step re-order (Sec. 3 step xii): the G2PD step has written each
-// particle's new key and counted the particles of every new span; scan the
-// counts into the other buffer's cell starts, give recycled particles their
-// slots, then move every tile's particles into the other buffer.  Swaps
-// s->cur.
+// particle's new key, counted the particles of every new span and marked the
+// changed tiles; every changed tile moves into its other buffer (or the
+// whole state is laid out again if one outgrew its region).  Swaps s->cur
+// (the tile-buffer table in use).
 void launch_reorder(mpm_sim* s, cudaStream_t st)
 {
     if (s->np == 0) return;
-    uint32_t* cs_new = s->cs[1 - s->cur];
-    scan_exclusive(s->count, cs_new, s->G.nkey, s->cscan_part, 1, st, &s->launches);
-    if (s->far_cap) {
-        k_far_place<<<s->sms * 2, 256, 0, st>>>(s->far, s->far_cap, s->count, cs_new, s->perm, s->clk);
-        s->launches += 1;
-    }
     s->vt->reorder(s, st);
     s->cur ^= 1;
 }
@@ -856,18 +964,28 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
     s->grid_bytes = align16((size_t)(1 + 3 * d) * (size_t)s->G.nnode_p * s->asize);
     s->grid = dalloc(s, s->grid_bytes);
     s->clk = (Clock*)dalloc(s, sizeof(Clock));
-    const size_t csb = (size_t)(s->G.nkey + 1) * 4;
+    const int64_t nt = s->G.ntiles;
+    const size_t csb = (size_t)(tile_cs0(s->G, nt) + 1) * 4;
+    const size_t ntb = (size_t)(nt + 1) * 4;
     s->cs[0] = (uint32_t*)dalloc(s, csb);
     s->cs[1] = (uint32_t*)dalloc(s, csb);
-    s->count = (uint32_t*)dalloc(s, csb);
-    s->cscan_part = (uint32_t*)dalloc(s, (size_t)scan_blocks(s->G.nkey) * 4);
+    s->count = (uint32_t*)dalloc(s, (size_t)(s->G.nkey + 1) * 4);
+    s->cscan_part = (uint32_t*)dalloc(s, (size_t)scan_blocks(nt + 1) * 4);
+    s->tpar[0] = (uint8_t*)dalloc(s, (size_t)nt);
+    s->tpar[1] = (uint8_t*)dalloc(s, (size_t)nt);
+    s->tbase = (uint32_t*)dalloc(s, ntb);
+    s->tbase_next = (uint32_t*)dalloc(s, ntb);
+    s->tcount = (uint32_t*)dalloc(s, ntb);
+    s->dirty = (uint32_t*)dalloc(s, ntb);
+    s->toff = (uint32_t*)dalloc(s, ntb);
     s->mwords = (reorder_ranges(s->G) + 63) / 64;
     const size_t ringb = (size_t)s->G.ntiles * s->mwords * 8;
     s->ring = (unsigned long long*)dalloc(s, ringb);
     s->cons_part = (double*)dalloc(s, 1024 * 5 * sizeof(double));
     s->cons_out = (double*)dalloc(s, 8 * sizeof(double));
     if (!s->grid || !s->clk || !s->cs[0] || !s->cs[1] || !s->count || !s->cscan_part || !s->ring ||
-        !s->cons_part || !s->cons_out) {
+        !s->cons_part || !s->cons_out || !s->tpar[0] || !s->tpar[1] || !s->tbase || !s->tbase_next || !s->tcount ||
+        !s->dirty || !s->toff) {
         mpm_destroy(s);
         return fail(nullptr, MPM_ENOMEM, "device allocation failed");
     }
@@ -875,7 +993,12 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
         cudaMemsetAsync(s->clk, 0, sizeof(Clock), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->cs[0], 0, csb, s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->cs[1], 0, csb, s->stream) != cudaSuccess ||
-        cudaMemsetAsync(s->count, 0, csb, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->count, 0, (size_t)(s->G.nkey + 1) * 4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->tpar[0], 0, (size_t)nt, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->tpar[1], 0, (size_t)nt, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->tbase, 0, ntb, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->tcount, 0, ntb, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->dirty, 0, ntb, s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->ring, 0, ringb, s->stream) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -908,24 +1031,29 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
     const Geom& G = s->G;
     const int d = G.dim;
     const int64_t np = s->np + n;
+    // every tile's region holds region_slots(its count) <= 2 count + 95
+    // slots, now and after any relayout: buffers of 2 np + 95 ntiles slots
+    const int64_t nslots = 2 * np + 95 * (int64_t)G.ntiles;
+    if (nslots > (int64_t)0x7FFFFFFF) return fail(s, MPM_EINVAL, "too many particles");
     Buffers nb[2];
-    mpm_status st = alloc_particles(s, np, nb);
+    mpm_status st = alloc_particles(s, nslots, nb);
     if (st != MPM_OK) { free_particles(s, nb); return fail(s, st, "device allocation failed"); }
     const size_t rs = s->rsize;
     cudaStream_t S = s->stream;
-    // keep the particles already there (current buffer) at the front
+    // keep the particles already there at the front, in key order
     if (s->np > 0) {
-        const Buffers& ob = s->buf[s->cur];
+        order_offsets(s, S);
         for (int a = 0; a < d; ++a) {
-            CK(cudaMemcpyAsync(nb[0].x[a], ob.x[a], s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
-            CK(cudaMemcpyAsync(nb[0].v[a], ob.v[a], s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
+            s->vt->compact(s, 0, a, nb[0].x[a], S);
+            s->vt->compact(s, 1, a, nb[0].v[a], S);
         }
-        CK(cudaMemcpyAsync(nb[0].M, ob.M, s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
-        CK(cudaMemcpyAsync(nb[0].rho, ob.rho, s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
-        CK(cudaMemcpyAsync(nb[0].E, ob.E, s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
-        CK(cudaMemcpyAsync(nb[0].Q, ob.Q, s->np * rs, cudaMemcpyDeviceToDevice, S), "copy");
-        CK(cudaMemcpyAsync(nb[0].id, ob.id, s->np * 4, cudaMemcpyDeviceToDevice, S), "copy");
-        CK(cudaMemcpyAsync(nb[0].gen, ob.gen, s->np * 4, cudaMemcpyDeviceToDevice, S), "copy");
+        s->vt->compact(s, 2, 0, nb[0].M, S);
+        s->vt->compact(s, 3, 0, nb[0].rho, S);
+        s->vt->compact(s, 4, 0, nb[0].E, S);
+        s->vt->compact(s, 5, 0, nb[0].Q, S);
+        s->vt->compact(s, 6, 0, nb[0].id, S);
+        s->vt->compact(s, 7, 0, nb[0].gen, S);
+        CK(cudaGetLastError(), "compact");
     }
     // stage the new doubles on the device, check them there and convert them
     // to the storage precision; stream order keeps the staging buffer safe to
@@ -983,15 +1111,13 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
     s->buf[1] = nb[1];
     s->cur = 0;
     s->np = np;
-    dfree(s, s->perm);
+    s->nslots = nslots;
     dfree(s, s->far);
-    s->perm = nullptr;
     s->far = nullptr;
     s->far_cap = G.inflow_face >= 0 ? (uint32_t)np : 0u;
     if (s->far_cap) {
-        s->perm = (uint32_t*)dalloc(s, (size_t)np * 4);
         s->far = (uint2*)dalloc(s, (size_t)np * sizeof(uint2));
-        if (!s->perm || !s->far) return fail(s, MPM_ENOMEM, "device allocation failed");
+        if (!s->far) return fail(s, MPM_ENOMEM, "device allocation failed");
     }
     // radix scratch for the initial order only
     RadixScratch sc;
@@ -1007,20 +1133,23 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
     }
     sc.hist = (uint32_t*)dalloc(s, (size_t)nhist * 4);
     sc.part = (uint32_t*)dalloc(s, (size_t)std::max<int64_t>(scan_blocks(nhist), 1) * 4);
+    uint32_t* cc = (uint32_t*)dalloc(s, (size_t)(G.nkey + 1) * 4);
     auto free_sc = [&]() {
         for (int b = 0; b < 2; ++b) { dfree(s, sc.skeys[b]); dfree(s, sc.sidx[b]); }
         dfree(s, sc.hist);
         dfree(s, sc.part);
+        dfree(s, cc);
     };
-    if (!sc.skeys[0] || !sc.skeys[1] || !sc.sidx[0] || !sc.sidx[1] || !sc.hist || !sc.part) {
+    if (!sc.skeys[0] || !sc.skeys[1] || !sc.sidx[0] || !sc.sidx[1] || !sc.hist || !sc.part || !cc) {
         free_sc();
         return fail(s, MPM_ENOMEM, "device allocation failed");
     }
     drop_graphs(s);
     s->cfl_done = false;
-    // initial order: keys from the positions, then the stable re-order
-    s->vt->keys(s, s->cur, S);
-    launch_sort(s, sc, S);
+    // initial order: keys from the positions, then the stable re-order into
+    // the tile regions
+    s->vt->keys(s, 0, S);
+    launch_sort(s, sc, cc, S);
     cudaError_t le = cudaGetLastError();
     cudaError_t se = cudaStreamSynchronize(S);
     free_sc();
@@ -1137,11 +1266,12 @@ static mpm_status capture_graph(mpm_sim* s, int b)
 
 static int64_t step_launch_count(const mpm_sim* s)
 {
-    // prepare, zero, 3 step kernels, finalize; re-order: 3 scan kernels,
-    // recycled placement (inflow only), tile moves
+    // prepare, zero, 3 step kernels, finalize; re-order: changed tiles,
+    // consolidation, region bases, relayout pass, marks (the last three return
+    // at once unless a tile outgrew its region)
     // a coloured simulation launches the two scattering kernels once per colour
     const int extra = s->col_off.empty() ? 0 : 2 * ((int)s->col_off.size() - 2);
-    return 6 + 4 + (s->far_cap ? 1 : 0) + extra;
+    return 6 + 5 + extra;
 }
 
 mpm_status mpm_step_async(mpm_sim* s, int64_t nsteps, double dt, double t_end)
@@ -1206,7 +1336,7 @@ int64_t mpm_field_size(const mpm_sim* s, int field)
     case MPM_FIELD_CELLSTART: return s->G.nkey + 1;
     case MPM_FIELD_GRID_M: return s->G.nnode;
     case MPM_FIELD_GRID_MV: case MPM_FIELD_GRID_F: case MPM_FIELD_GRID_MV2: return d * s->G.nnode;
-    case MPM_FIELD_CLOCK: return 3;
+    case MPM_FIELD_CLOCK: return 4;
     }
     return -1;
 }
@@ -1264,37 +1394,65 @@ mpm_status mpm_read_state(mpm_sim* s, int field, double* out, int64_t count)
     if (count < need) return fail(s, MPM_EINVAL, "output buffer too short");
     mpm_status st = check_device_errors(s);
     if (st != MPM_OK) return st;
-    const Buffers& b = s->buf[s->cur];
     const int d = s->G.dim;
     const int64_t np = s->np, nn = s->G.nnode;
+    const bool particle_field = field <= MPM_FIELD_CELLSTART || field == MPM_FIELD_GEN;
+    if (particle_field && np > 0) order_offsets(s, s->stream);
+    // a particle field gathered into key order on the device, then read
+    auto real_field = [&](int f, int a, double* dst) -> mpm_status {
+        void* tmp = dalloc(s, (size_t)np * s->rsize);
+        if (!tmp) return fail(s, MPM_ENOMEM, "device allocation failed");
+        s->vt->compact(s, f, a, tmp, s->stream);
+        const mpm_status r = read_real(s, tmp, np, dst);
+        dfree(s, tmp);
+        return r;
+    };
+    auto u32_field = [&](int f, double* dst) -> mpm_status {
+        uint32_t* tmp = (uint32_t*)dalloc(s, (size_t)np * 4);
+        if (!tmp) return fail(s, MPM_ENOMEM, "device allocation failed");
+        s->vt->compact(s, f, 0, tmp, s->stream);
+        const mpm_status r = read_u32(s, tmp, np, dst);
+        dfree(s, tmp);
+        return r;
+    };
+    // the cell starts of the key order without the regions' gaps
+    auto compact_starts = [&](uint32_t* dst) {
+        k_compact_starts<<<std::min<int64_t>(nblk(s->G.nkey + 1), s->sms * 16), kThreads, 0, s->stream>>>(
+            s->G, s->cs[0], s->cs[1], s->tpar[s->cur], s->toff, dst);
+    };
+    if (np == 0 && particle_field && field != MPM_FIELD_CELLSTART) return MPM_OK;
     switch (field) {
     case MPM_FIELD_X:
-        for (int a = 0; a < d; ++a) if ((st = read_real(s, b.x[a], np, out + a * np))) return st;
+        for (int a = 0; a < d; ++a) if ((st = real_field(0, a, out + a * np))) return st;
         return MPM_OK;
     case MPM_FIELD_V:
-        for (int a = 0; a < d; ++a) if ((st = read_real(s, b.v[a], np, out + a * np))) return st;
+        for (int a = 0; a < d; ++a) if ((st = real_field(1, a, out + a * np))) return st;
         return MPM_OK;
-    case MPM_FIELD_M: return read_real(s, b.M, np, out);
-    case MPM_FIELD_RHO: return read_real(s, b.rho, np, out);
-    case MPM_FIELD_E: return read_real(s, b.E, np, out);
-    case MPM_FIELD_Q: return read_real(s, b.Q, np, out);
+    case MPM_FIELD_M: return real_field(2, 0, out);
+    case MPM_FIELD_RHO: return real_field(3, 0, out);
+    case MPM_FIELD_E: return real_field(4, 0, out);
+    case MPM_FIELD_Q: return real_field(5, 0, out);
     case MPM_FIELD_P: {
         // evaluated on the device from the stored density and energy, as
         // the step kernels evaluate it
-        if (np == 0) return MPM_OK;
-        void* tp = dalloc(s, (size_t)np * s->rsize);
-        if (!tp) return fail(s, MPM_ENOMEM, "device allocation failed");
+        char* tmp = (char*)dalloc(s, (size_t)np * s->rsize * 3);
+        if (!tmp) return fail(s, MPM_ENOMEM, "device allocation failed");
+        void* tr = tmp;
+        void* te = tmp + np * s->rsize;
+        void* tp = tmp + 2 * np * s->rsize;
+        s->vt->compact(s, 3, 0, tr, s->stream);
+        s->vt->compact(s, 4, 0, te, s->stream);
         if (s->rsize == 8)
-            k_pressure<double><<<nblk(np), kThreads, 0, s->stream>>>((const double*)b.rho, (const double*)b.E,
+            k_pressure<double><<<nblk(np), kThreads, 0, s->stream>>>((const double*)tr, (const double*)te,
                                                                     s->G.gamma - 1.0, (double*)tp, np);
         else
-            k_pressure<float><<<nblk(np), kThreads, 0, s->stream>>>((const float*)b.rho, (const float*)b.E,
+            k_pressure<float><<<nblk(np), kThreads, 0, s->stream>>>((const float*)tr, (const float*)te,
                                                                    (float)(s->G.gamma - 1.0), (float*)tp, np);
         st = read_real(s, tp, np, out);
-        dfree(s, tp);
+        dfree(s, tmp);
         return st;
     }
-    case MPM_FIELD_ID: return read_u32(s, b.id, np, out);
+    case MPM_FIELD_ID: return u32_field(6, out);
     case MPM_FIELD_GEN:
         // the recycle counts move with the particles only where recycling
         // exists (an inflow face); elsewhere they are all 0
@@ -1302,19 +1460,36 @@ mpm_status mpm_read_state(mpm_sim* s, int field, double* out, int64_t count)
             for (int64_t k = 0; k < np; ++k) out[k] = 0.0;
             return MPM_OK;
         }
-        return read_u32(s, b.gen, np, out);
+        return u32_field(7, out);
     case MPM_FIELD_KEY: {
         // keys of the current order, expanded from its cell starts
-        if (np == 0) return MPM_OK;
+        uint32_t* tcs = (uint32_t*)dalloc(s, (size_t)(s->G.nkey + 1) * 4);
         uint32_t* tk = (uint32_t*)dalloc(s, (size_t)np * 4);
-        if (!tk) return fail(s, MPM_ENOMEM, "device allocation failed");
+        if (!tcs || !tk) {
+            dfree(s, tcs);
+            dfree(s, tk);
+            return fail(s, MPM_ENOMEM, "device allocation failed");
+        }
+        compact_starts(tcs);
         k_keys_from_start<<<std::min<int64_t>(nblk(s->G.nkey), s->sms * 16), kThreads, 0, s->stream>>>(
-            s->cs[s->cur], s->G.nkey, tk);
+            tcs, s->G.nkey, tk);
         st = read_u32(s, tk, np, out);
+        dfree(s, tcs);
         dfree(s, tk);
         return st;
     }
-    case MPM_FIELD_CELLSTART: return read_u32(s, s->cs[s->cur], s->G.nkey + 1, out);
+    case MPM_FIELD_CELLSTART: {
+        if (np == 0) {
+            for (int64_t k = 0; k <= s->G.nkey; ++k) out[k] = 0.0;
+            return MPM_OK;
+        }
+        uint32_t* tcs = (uint32_t*)dalloc(s, (size_t)(s->G.nkey + 1) * 4);
+        if (!tcs) return fail(s, MPM_ENOMEM, "device allocation failed");
+        compact_starts(tcs);
+        st = read_u32(s, tcs, s->G.nkey + 1, out);
+        dfree(s, tcs);
+        return st;
+    }
     case MPM_FIELD_CLOCK: {
         Clock c;
         CK(cudaMemcpyAsync(&c, s->clk, sizeof(Clock), cudaMemcpyDeviceToHost, s->stream), "read clock");
@@ -1322,6 +1497,7 @@ mpm_status mpm_read_state(mpm_sim* s, int field, double* out, int64_t count)
         out[0] = c.t;
         out[1] = c.dt_next;
         out[2] = (double)c.step;
+        out[3] = (double)c.relayouts;
         if (!s->started) {
             double dt0 = 0.0;
             if ((st = mpm_cfl_dt(s, &dt0))) return st;

@@ -38,8 +38,8 @@ struct mpm_batch {
     bool graph_ok = true;
     int64_t recordings = 0;
     std::vector<BatchGroup> groups;
-    size_t common_off = 0, zero_off = 0, scan_off = 0, far_off = 0;
-    int nzero = 0, nscan = 0, nfar = 0;
+    size_t common_off = 0, zero_off = 0, scan_off = 0;
+    int nzero = 0, nscan = 0;
     int64_t launches = 0;
     std::string err;
 };
@@ -83,22 +83,24 @@ void batch_launch_step(mpm_batch* b)
             ++l;
         }
     kb_finalize<<<nb, 128, 0, st>>>(common, n);
-    const TileRef* sl = reinterpret_cast<const TileRef*>(dev + b->scan_off);
-    kb_scan_reduce<<<b->nscan, kScanThreads, 0, st>>>(common, sl);
-    kb_scan_partials<<<n, kScanThreads, 0, st>>>(common);
-    kb_scan_down<<<b->nscan, kScanThreads, 0, st>>>(common, sl);
-    l += 4;
-    if (b->nfar > 0) {
-        kb_far_place<<<b->nfar, 256, 0, st>>>(common, reinterpret_cast<const TileRef*>(dev + b->far_off));
-        ++l;
-    }
-    for (const BatchGroup& g : b->groups) {
-        g.vt->blaunch(3, dev + g.desc_off, reinterpret_cast<const TileRef*>(dev + g.tl_off), g.ntl, g.smem[3], g.per,
-                      st);
-        ++l;
-    }
+    ++l;
+    // re-order: changed tiles; the relayout of a member whose tile outgrew
+    // its region (the kernels return at once for the other members)
+    auto stage = [&](int k) {
+        for (const BatchGroup& g : b->groups) {
+            g.vt->blaunch(k, dev + g.desc_off, reinterpret_cast<const TileRef*>(dev + g.tl_off), g.ntl, g.smem[3],
+                          g.per, st);
+            ++l;
+        }
+    };
+    stage(3);
+    stage(4);
+    kb_relayout_bases<<<n, 1024, 0, st>>>(common);
+    ++l;
+    stage(5);
+    kb_step_end<<<b->nscan, kScanThreads, 0, st>>>(common, reinterpret_cast<const TileRef*>(dev + b->scan_off));
     kb_flip<<<nb, 128, 0, st>>>(common, n);
-    b->launches = l + 1;
+    b->launches = l + 2;
 }
 
 // Descriptors, block lists and the graph of one batched step.
@@ -128,7 +130,7 @@ mpm_status batch_build(mpm_batch* b)
     }
     // host image of the device buffer
     std::vector<BatchCommon> common(n);
-    std::vector<TileRef> zl, sl, fl;
+    std::vector<TileRef> zl, sl;
     for (int i = 0; i < n; ++i) {
         const mpm_sim* s = b->members[i];
         BatchCommon& c = common[i];
@@ -137,18 +139,19 @@ mpm_status batch_build(mpm_batch* b)
         c.grid16 = (uint4*)s->grid;
         c.n16 = (int64_t)(s->grid_bytes / 16);
         c.count = s->count;
-        c.cs[0] = s->cs[0];
-        c.cs[1] = s->cs[1];
-        c.cscan_part = s->cscan_part;
         c.nkey = s->G.nkey;
-        c.far = s->far;
-        c.far_cap = s->far_cap;
-        c.perm = s->perm;
+        c.ntiles = s->G.ntiles;
+        c.tvol = s->G.Tvol;
+        c.mwords = s->mwords;
+        c.dirty = s->dirty;
+        c.ring = s->ring;
+        c.tbase = s->tbase;
+        c.tbase_next = s->tbase_next;
+        c.tcount = s->tcount;
         c.cfl_h = s->G.cfl * s->G.h;
         for (int64_t k = 0; k * kZeroChunk < c.n16; ++k) zl.push_back(TileRef{i, (int)k});
+        // (member, k): span counts and tiles [k, k + 1) * kScanTile (nkey >= ntiles)
         for (int64_t k = 0; k < scan_blocks(c.nkey); ++k) sl.push_back(TileRef{i, (int)k});
-        if (s->far_cap)
-            for (int k = 0; k < kFarBlocks; ++k) fl.push_back(TileRef{i, k});
     }
     size_t off = 0;
     b->common_off = off;
@@ -157,8 +160,6 @@ mpm_status batch_build(mpm_batch* b)
     off = align256(off + zl.size() * sizeof(TileRef));
     b->scan_off = off;
     off = align256(off + sl.size() * sizeof(TileRef));
-    b->far_off = off;
-    off = align256(off + fl.size() * sizeof(TileRef));
     std::vector<std::vector<char>> gdesc(b->groups.size());
     std::vector<std::vector<TileRef>> gtl(b->groups.size());
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
@@ -185,14 +186,12 @@ mpm_status batch_build(mpm_batch* b)
     memcpy(img.data() + b->common_off, common.data(), n * sizeof(BatchCommon));
     if (!zl.empty()) memcpy(img.data() + b->zero_off, zl.data(), zl.size() * sizeof(TileRef));
     if (!sl.empty()) memcpy(img.data() + b->scan_off, sl.data(), sl.size() * sizeof(TileRef));
-    if (!fl.empty()) memcpy(img.data() + b->far_off, fl.data(), fl.size() * sizeof(TileRef));
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         memcpy(img.data() + b->groups[gi].desc_off, gdesc[gi].data(), gdesc[gi].size());
         memcpy(img.data() + b->groups[gi].tl_off, gtl[gi].data(), gtl[gi].size() * sizeof(TileRef));
     }
     b->nzero = (int)zl.size();
     b->nscan = (int)sl.size();
-    b->nfar = (int)fl.size();
     // the previous buffer may still be read by queued steps: wait before reuse
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -332,7 +331,7 @@ mpm_status mpm_batch_step_async(mpm_batch* b, int64_t nsteps)
     }
     const cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return bfail(b, MPM_ECUDA, std::string("launch: ") + cudaGetErrorString(le));
-    // every step moves each member's state to its other buffer
+    // every step switches each member to its other tile-buffer table
     for (mpm_sim* s : b->members) {
         if (nsteps & 1) s->cur ^= 1;
         s->launches += b->launches * nsteps / (int64_t)b->members.size();

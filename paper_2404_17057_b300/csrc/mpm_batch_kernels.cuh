@@ -25,12 +25,13 @@ struct BatchCommon {
     uint4* grid16;
     int64_t n16;
     uint32_t* count;
-    uint32_t* cs[2];
-    uint32_t* cscan_part;
     int64_t nkey;
-    uint2* far;
-    uint32_t far_cap;
-    uint32_t* perm;
+    int ntiles, mwords, tvol;
+    uint32_t* dirty;
+    unsigned long long* ring;
+    uint32_t* tbase;
+    uint32_t* tbase_next;
+    uint32_t* tcount;
     double cfl_h;
 };
 
@@ -41,14 +42,16 @@ struct BatchProb {
     Grid<A, R> gr;
     FieldPtrs p2g_out, g2p_out;     // single-precision kernels: grid fields they add into
     uint32_t* cs[2];
+    uint8_t* tpar[2];               // buffer of each tile, by step parity
+    uint32_t* tbase;
+    uint32_t* tbase_next;
+    uint32_t* tcount;
     Reorder ro;
-    uint32_t* perm;
     int64_t np;
     Clock* clk;
 };
 
 constexpr int kZeroChunk = 256 * 16;    // 16-byte words cleared per block
-constexpr int kFarBlocks = 8;           // blocks placing one member's recycled particles
 
 template <class T>
 __device__ __forceinline__ void load_shared(T& dst, const T& src)
@@ -88,34 +91,27 @@ __global__ void kb_zero(const BatchCommon* __restrict__ c, const TileRef* __rest
     for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) d.grid16[i] = make_uint4(0, 0, 0, 0);
 }
 
-// Counts of the new spans -> cell starts of the other buffer, per member.
-__global__ void __launch_bounds__(kScanThreads) kb_scan_reduce(const BatchCommon* __restrict__ c,
-                                                              const TileRef* __restrict__ bl)
-{
-    const TileRef r = bl[blockIdx.x];
-    const BatchCommon& d = c[r.prob];
-    scan_reduce_block(d.count, d.nkey, d.cscan_part, r.tile);
-}
-
-__global__ void __launch_bounds__(kScanThreads) kb_scan_partials(const BatchCommon* __restrict__ c)
+// Relayout of a member whose tile outgrew its region: the new regions (one
+// block per member).
+__global__ void __launch_bounds__(1024) kb_relayout_bases(const BatchCommon* __restrict__ c)
 {
     const BatchCommon& d = c[blockIdx.x];
-    scan_partials_block(d.cscan_part, scan_blocks(d.nkey));
+    if (!d.clk->overflow) return;
+    relayout_bases_block(d.tcount, d.ntiles, d.tbase_next);
 }
 
-__global__ void __launch_bounds__(kScanThreads) kb_scan_down(const BatchCommon* __restrict__ c,
-                                                            const TileRef* __restrict__ bl)
+// End of a member's step: block (member, k) finishes the re-order of the
+// tiles [k, k + 1) * kScanTile (marks cleared, the regions of a relayout
+// installed).
+__global__ void __launch_bounds__(kScanThreads) kb_step_end(const BatchCommon* __restrict__ c,
+                                                           const TileRef* __restrict__ bl)
 {
     const TileRef r = bl[blockIdx.x];
     const BatchCommon& d = c[r.prob];
-    scan_down_block(d.count, d.nkey, d.cscan_part, d.cs[1 - d.clk->par], 1, r.tile);
-}
-
-__global__ void kb_far_place(const BatchCommon* __restrict__ c, const TileRef* __restrict__ bl)
-{
-    const TileRef r = bl[blockIdx.x];
-    const BatchCommon& d = c[r.prob];
-    far_place_block(d.far, d.far_cap, d.count, d.cs[1 - d.clk->par], d.perm, d.clk, (unsigned)r.tile, kFarBlocks);
+    const int64_t b = (int64_t)r.tile * kScanTile;
+    const Reorder ro = {d.count, nullptr, 0u, d.mwords, d.ring, d.dirty};
+    for (int64_t t = b + threadIdx.x; t < min(b + (int64_t)kScanTile, (int64_t)d.ntiles); t += blockDim.x)
+        reorder_done_tile(d.tvol, ro, d.clk, d.tbase, d.tbase_next, (int)t, d.ntiles);
 }
 
 // ------------------------------------------------------------ per tile
@@ -125,13 +121,14 @@ __global__ void kb_far_place(const BatchCommon* __restrict__ c, const TileRef* _
     const TileRef r = tl[blockIdx.x];            \
     load_shared(p, bp[r.prob]);                  \
     __syncthreads();                             \
-    const int par = p.clk->par;
+    const int par = p.clk->par;                  \
+    const int tp = p.tpar[par][r.tile];
 
 template <int D, int P, class R, class A>
 __global__ void __launch_bounds__(256) kb_p2g(const BatchProb<R, A>* __restrict__ bp, const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    p2g_tile<D, P, R, A>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, r.tile);
+    p2g_tile<D, P, R, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, r.tile);
 }
 
 template <int D, int P, class R, class A>
@@ -139,14 +136,14 @@ __global__ void __launch_bounds__(256) kb_grid_g2p(const BatchProb<R, A>* __rest
                                                    const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    grid_g2p_tile<D, P, R, A>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, r.tile);
+    grid_g2p_tile<D, P, R, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, r.tile);
 }
 
 template <int D, int P, class R, class A>
 __global__ void __launch_bounds__(256) kb_g2pd(const BatchProb<R, A>* __restrict__ bp, const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    g2pd_tile<D, P, R, A>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, p.ro, r.tile);
+    g2pd_tile<D, P, R, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, p.ro, r.tile, tp);
 }
 
 template <int D, int P, bool PER>
@@ -154,7 +151,7 @@ __global__ void __launch_bounds__(kP2GThreads, 6) kb_p2g_span(const BatchProb<fl
                                                               const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(float, float)
-    p2g_span_tile<D, P, PER>(p.G, p.pt[par], p.p2g_out, p.cs[par], p.clk, r.tile);
+    p2g_span_tile<D, P, PER>(p.G, p.pt[tp], p.p2g_out, p.cs[tp], p.clk, r.tile);
 }
 
 template <int P, class R, class A>
@@ -162,7 +159,7 @@ __global__ void __launch_bounds__(kP2GSpan2dThreads, 6) kb_p2g_span2d(const Batc
                                                                       const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    p2g_span2d_tile<P, R, A>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, r.tile);
+    p2g_span2d_tile<P, R, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, r.tile);
 }
 
 template <int P, class R, class A>
@@ -170,7 +167,7 @@ __global__ void __launch_bounds__(kG2PSpan2dThreads, 4)
     kb_grid_g2p_span2d(const BatchProb<R, A>* __restrict__ bp, const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    grid_g2p_span2d_tile<P, R, A>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, r.tile);
+    grid_g2p_span2d_tile<P, R, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, r.tile);
 }
 
 template <int D, int P, bool PER>
@@ -178,7 +175,7 @@ __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 3)
     kb_grid_g2p_span(const BatchProb<float, float>* __restrict__ bp, const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(float, float)
-    grid_g2p_span_tile<D, P, PER>(p.G, p.pt[par], p.gr, p.g2p_out, p.cs[par], p.clk, r.tile);
+    grid_g2p_span_tile<D, P, PER>(p.G, p.pt[tp], p.gr, p.g2p_out, p.cs[tp], p.clk, r.tile);
 }
 
 template <int D, int P, class A>
@@ -186,16 +183,52 @@ __global__ void __launch_bounds__(kG2PDThreads, kG2PDBlocks) kb_g2pd_fast(const 
                                                              const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(float, A)
-    g2pd_fast_tile<D, P, A>(p.G, p.pt[par], p.gr, p.cs[par], p.clk, p.ro, r.tile);
+    g2pd_fast_tile<D, P, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, p.ro, r.tile, tp);
+}
+
+// The re-order arguments of member p at step parity par.
+template <class R, class A>
+__device__ __forceinline__ void batch_reorder_args(const BatchProb<R, A>& p, int par, ReorderArgs<R>& a)
+{
+    a.pt[0] = p.pt[0];
+    a.pt[1] = p.pt[1];
+    a.cs[0] = p.cs[0];
+    a.cs[1] = p.cs[1];
+    a.tpar_old = p.tpar[par];
+    a.tpar_new = p.tpar[1 - par];
+    a.tbase = p.tbase;
+    a.tbase_next = p.tbase_next;
+    a.tcount = p.tcount;
+    a.ro = p.ro;
+    a.clk = p.clk;
+}
+
+// mode 0: the member's changed tiles; mode 1: its relayout (if a tile
+// overflowed)
+template <int D, class R, class A>
+__global__ void __launch_bounds__(kReorderThreads, 3) kb_reorder(const BatchProb<R, A>* __restrict__ bp,
+                                                                 const TileRef* __restrict__ tl, int mode)
+{
+    MPM_BATCH_PROLOGUE(R, A)
+    (void)tp;
+    __shared__ ReorderArgs<R> a;
+    if (threadIdx.x == 0) batch_reorder_args(p, par, a);
+    __syncthreads();
+    if (mode == 1 && !p.clk->overflow) return;
+    reorder_tile<D, R>(p.G, a, mode, r.tile);
 }
 
 template <int D, class R, class A>
-__global__ void __launch_bounds__(kReorderThreads, 3) kb_reorder(const BatchProb<R, A>* __restrict__ bp,
-                                                                 const TileRef* __restrict__ tl)
+__global__ void __launch_bounds__(kReorderThreads) kb_consolidate(const BatchProb<R, A>* __restrict__ bp,
+                                                                  const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    reorder_tile<D, R>(p.G, p.pt[par], p.pt[1 - par], p.cs[par], p.cs[1 - par], p.ro.count, p.perm, p.np, p.ro.ring,
-                       p.ro.mwords, p.clk, r.tile);
+    (void)tp;
+    if (!p.clk->overflow) return;
+    __shared__ ReorderArgs<R> a;
+    if (threadIdx.x == 0) batch_reorder_args(p, par, a);
+    __syncthreads();
+    consolidate_tile<D, R>(p.G, a, r.tile);
 }
 
 #undef MPM_BATCH_PROLOGUE

@@ -199,7 +199,7 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
                                               const uint32_t* __restrict__ cs, Clock* clk, const int tile)
 {
     if (!clk->active) return;
-    const int64_t kb = (int64_t)tile * G.Tvol;
+    const int64_t kb = tile_cs0(G, tile);
     if (cs[kb] == cs[kb + G.Tvol]) return;
     extern __shared__ __align__(16) float sm[];
     constexpr int NS = P + 1, NF = 1 + 2 * D, NYZ = (D == 3) ? NS * NS : NS, NN = NYZ * NS;
@@ -386,11 +386,14 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
 // tiles: the tiles of one colour pass (block b runs tiles[b]), or NULL (block
 // b runs tile b)
 template <int D, int P, bool PER>
-__global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, Particles<float> pt, FieldPtrs out,
-                                                              const uint32_t* __restrict__ cs, Clock* clk,
+__global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, TileState<float> ts, FieldPtrs out, Clock* clk,
                                                               const uint32_t* __restrict__ tiles)
 {
-    p2g_span_tile<D, P, PER>(G, pt, out, cs, clk, tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x);
+    const int t = tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x;
+    // one inlined copy per buffer, so that the buffer's pointers stay
+    // constant-bank operands
+    if (ts.tpar[t]) p2g_span_tile<D, P, PER>(G, ts.pt[1], out, ts.cs[1], clk, t);
+    else p2g_span_tile<D, P, PER>(G, ts.pt[0], out, ts.cs[0], clk, t);
 }
 
 // ------------------------------- 2D span-per-lane kernels, 64-bit sums
@@ -522,7 +525,7 @@ __device__ __forceinline__ void p2g_span2d_tile(const Geom& G, const Particles<R
                                                 const uint32_t* __restrict__ cs, Clock* clk, const int tile)
 {
     if (!clk->active) return;
-    const int64_t kb = (int64_t)tile * G.Tvol;
+    const int64_t kb = tile_cs0(G, tile);
     if (cs[kb] == cs[kb + G.Tvol]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A* swin = reinterpret_cast<A*>(smem_raw);
@@ -553,10 +556,12 @@ __device__ __forceinline__ void p2g_span2d_tile(const Geom& G, const Particles<R
 constexpr int kP2GSpan2dThreads = 64;
 
 template <int P, class R, class A>
-__global__ void __launch_bounds__(kP2GSpan2dThreads, 8) k_p2g_span2d(Geom G, Particles<R> pt, Grid<A, R> gr,
-                                                                     const uint32_t* __restrict__ cs, Clock* clk)
+__global__ void __launch_bounds__(kP2GSpan2dThreads, 8) k_p2g_span2d(Geom G, TileState<R> ts, Grid<A, R> gr,
+                                                                     Clock* clk)
 {
-    p2g_span2d_tile<P, R, A>(G, pt, gr, cs, clk, blockIdx.x);
+    const int t = blockIdx.x;
+    if (ts.tpar[t]) p2g_span2d_tile<P, R, A>(G, ts.pt[1], gr, ts.cs[1], clk, t);
+    else p2g_span2d_tile<P, R, A>(G, ts.pt[0], gr, ts.cs[0], clk, t);
 }
 
 // Grid update + G2P + P2G: the acceleration window is built as in the
@@ -573,7 +578,7 @@ __device__ __forceinline__ void grid_g2p_span2d_tile(const Geom& G, const Partic
 {
     typedef Op<R> O;
     if (!clk->active) return;
-    const int64_t kb = (int64_t)tile * G.Tvol;
+    const int64_t kb = tile_cs0(G, tile);
     if (cs[kb] == cs[kb + G.Tvol]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int W = G.Wvol, W0 = G.W[0];
@@ -681,10 +686,12 @@ __device__ __forceinline__ void grid_g2p_span2d_tile(const Geom& G, const Partic
 }
 
 template <int P, class R, class A>
-__global__ void __launch_bounds__(kG2PSpan2dThreads, 4) k_grid_g2p_span2d(Geom G, Particles<R> pt, Grid<A, R> gr,
-                                                                          const uint32_t* __restrict__ cs, Clock* clk)
+__global__ void __launch_bounds__(kG2PSpan2dThreads, 4) k_grid_g2p_span2d(Geom G, TileState<R> ts, Grid<A, R> gr,
+                                                                          Clock* clk)
 {
-    grid_g2p_span2d_tile<P, R, A>(G, pt, gr, cs, clk, blockIdx.x);
+    const int t = blockIdx.x;
+    if (ts.tpar[t]) grid_g2p_span2d_tile<P, R, A>(G, ts.pt[1], gr, ts.cs[1], clk, t);
+    else grid_g2p_span2d_tile<P, R, A>(G, ts.pt[0], gr, ts.cs[0], clk, t);
 }
 
 // ----------------------------------------- K2: grid update + G2P + P2G
@@ -756,7 +763,7 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
 {
     typedef K2Cfg<D> C;
     if (!clk->active) return;
-    const int64_t kb = (int64_t)tile * G.Tvol;
+    const int64_t kb = tile_cs0(G, tile);
     if (cs[kb] == cs[kb + G.Tvol]) return;
     extern __shared__ __align__(16) float sm[];
     constexpr int NS = P + 1, NYZ = (D == 3) ? NS * NS : NS, NN = NYZ * NS;
@@ -942,12 +949,14 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
 }
 
 template <int D, int P, bool PER>
-__global__ void __launch_bounds__(K2Cfg<D>::kThreads, 4) k_grid_g2p_span(Geom G, Particles<float> pt,
+__global__ void __launch_bounds__(K2Cfg<D>::kThreads, 4) k_grid_g2p_span(Geom G, TileState<float> ts,
                                                                          Grid<float, float> gr, FieldPtrs out,
-                                                                         const uint32_t* __restrict__ cs, Clock* clk,
+                                                                         Clock* clk,
                                                                          const uint32_t* __restrict__ tiles)
 {
-    grid_g2p_span_tile<D, P, PER>(G, pt, gr, out, cs, clk, tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x);
+    const int t = tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x;
+    if (ts.tpar[t]) grid_g2p_span_tile<D, P, PER>(G, ts.pt[1], gr, out, ts.cs[1], clk, t);
+    else grid_g2p_span_tile<D, P, PER>(G, ts.pt[0], gr, out, ts.cs[0], clk, t);
 }
 
 // ------------------------------- K3: G2PD + particle update + move + key
@@ -961,11 +970,11 @@ constexpr int kG2PDBlocks = 5;
 template <int D, int P, class A>
 __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<float>& pt, const Grid<A, float>& gr,
                                                const uint32_t* __restrict__ cs, Clock* clk, const Reorder& ro,
-                                               const int tile)
+                                               const int tile, const int tp)
 {
     if (!clk->active) return;
-    const uint32_t beg = cs[(int64_t)tile * G.Tvol];
-    const uint32_t end = cs[(int64_t)(tile + 1) * G.Tvol];
+    const uint32_t beg = cs[tile_cs0(G, tile)];
+    const uint32_t end = cs[tile_cs0(G, tile) + G.Tvol];
     if (beg == end) return;
     // per node: 3D {Vb_x, Vb_y, Vb_z, V2_y} + {V2_x, V2_z}; 2D {Vb_x, Vb_y, V2_x, V2_y}
     extern __shared__ __align__(16) float4 sn[];
@@ -1187,7 +1196,7 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
 #pragma unroll
         for (int a = 0; a < D; ++a) old[a] = so[a] + l[a];
         pt.key[k] = record_key(G, ro, clk, key_of<float>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, tile, old,
-                               err);
+                               err, tp);
         pt.E[k] = En_s;
         pt.rho[k] = rn_s;
         pt.Q[k] = Qn_s;
@@ -1206,10 +1215,12 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
 }
 
 template <int D, int P, class A>
-__global__ void __launch_bounds__(kG2PDThreads, kG2PDBlocks) k_g2pd_fast(Geom G, Particles<float> pt, Grid<A, float> gr,
-                                                            const uint32_t* __restrict__ cs, Clock* clk, Reorder ro)
+__global__ void __launch_bounds__(kG2PDThreads, kG2PDBlocks) k_g2pd_fast(Geom G, TileState<float> ts,
+                                                                         Grid<A, float> gr, Clock* clk, Reorder ro)
 {
-    g2pd_fast_tile<D, P, A>(G, pt, gr, cs, clk, ro, blockIdx.x);
+    const int t = blockIdx.x;
+    if (ts.tpar[t]) g2pd_fast_tile<D, P, A>(G, ts.pt[1], gr, ts.cs[1], clk, ro, t, 1);
+    else g2pd_fast_tile<D, P, A>(G, ts.pt[0], gr, ts.cs[0], clk, ro, t, 0);
 }
 
 }  // namespace mpm

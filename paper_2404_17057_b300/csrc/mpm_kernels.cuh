@@ -24,11 +24,12 @@ constexpr uint32_t kFarFlag = 0x80000000u;   // key bit of a particle recycled t
 
 // Per-step re-order bookkeeping written by the G2PD step.
 struct Reorder {
-    uint32_t* count;               // particles per new span; cleared by the re-order
-    uint2* far;                    // particles recycled this step: {new key, old index}
+    uint32_t* count;               // per span: particles gained minus lost in the step (mod 2^32)
+    uint2* far;                    // particles recycled this step: {new key, old slot | buffer << 31}
     uint32_t far_cap;              // entries of far (0: the problem has no inflow face)
     int mwords;                    // words of ring bits per tile
     unsigned long long* ring;      // per tile: parts of its one-span ring that particles entered from
+    uint32_t* dirty;               // per tile: its span lists change in this step
 };
 
 struct Geom {
@@ -53,9 +54,23 @@ struct Clock {
     int active, done, last, err;
     unsigned long long vmax_bits, cmax_bits;   // bits of non-negative doubles
     unsigned nfar;                             // recycled particles this step
-    int par;                                   // batched runs: buffer holding the state
+    int par;                                   // batched runs: parity of the step (tile-buffer table in use)
     long long step_end;                        // > 0: no step starts at or after this count
+    unsigned overflow;                         // a tile outgrew its region in this step's re-order
+    long long relayouts;                       // steps whose re-order laid the state out again
 };
+
+// Tiles own regions of the particle buffers: tile t's particles occupy the
+// first n_t slots of its region in buffer tpar[t], span after span, and its
+// cell starts are the Tvol + 1 entries tile_cs0(t) .. tile_cs0(t) + Tvol of
+// cs[tpar[t]] (the start of each span and the end of the tile's particles).
+__host__ __device__ inline int64_t tile_cs0(const Geom& G, int64_t t) { return t * (int64_t)(G.Tvol + 1); }
+// Entry of the cell-start table of the span with key `key`.
+__host__ __device__ inline int64_t cs_index(const Geom& G, uint32_t key)
+{
+    return (int64_t)key + (int64_t)(key >> (G.tsh[0] + G.tsh[1] + G.tsh[2]));
+}
+
 
 // Rows of spans (y, z) of a tile and its one-span ring, times three x-parts
 // (the tile's own x-range and the span before and after it).
@@ -107,20 +122,33 @@ __device__ __forceinline__ int ring_bit(const Geom& G, uint32_t t, const int old
     return 3 * (idx[2] * ny + idx[1]) + idx[0];
 }
 
-// New key of particle k: count it for its span; recycled particles go to the
-// far list (they may jump anywhere) and carry the flag bit.
+// New key of particle k (slot k of buffer tp).  A particle that changes span
+// moves one count from its old span to its new one (most particles keep their
+// span and cost nothing here) and marks the tile it leaves and the tile it
+// enters as changed; one that enters another tile marks the ring part it
+// comes from.  Recycled particles go to the far list (they may jump anywhere)
+// and carry the flag bit.
 __device__ __forceinline__ uint32_t record_key(const Geom& G, const Reorder& ro, Clock* clk, uint32_t key,
-                                               bool recycled, uint32_t k, int tile, const int old[3], int& err)
+                                               bool recycled, uint32_t k, int tile, const int old[3], int& err,
+                                               int tp)
 {
-    atomicAdd(&ro.count[key], 1u);
+    const int lsh = G.tsh[0] + G.tsh[1] + G.tsh[2];
+    const uint32_t nt = key >> lsh;
+    const int lo[3] = {old[0] & (G.T[0] - 1), old[1] & (G.T[1] - 1), old[2] & (G.T[2] - 1)};
+    const uint32_t okey = ((uint32_t)tile << lsh) | (uint32_t)((((lo[2] << G.tsh[1]) + lo[1]) << G.tsh[0]) | lo[0]);
+    if (recycled || key != okey) {
+        atomicAdd(&ro.count[key], 1u);
+        atomicSub(&ro.count[okey], 1u);
+        ro.dirty[tile] = 1u;
+        ro.dirty[nt] = 1u;
+    }
     if (recycled) {
         const unsigned slot = atomicAdd(&clk->nfar, 1u);
-        if (slot < ro.far_cap) ro.far[slot] = make_uint2(key, k);
+        if (slot < ro.far_cap) ro.far[slot] = make_uint2(key, k | ((uint32_t)tp << 31));
         else err |= ERR_TILE;
         return key | kFarFlag;
     }
     // a particle that enters another tile: mark the ring part it comes from
-    const uint32_t nt = key >> (G.tsh[0] + G.tsh[1] + G.tsh[2]);
     if (nt != (uint32_t)tile) {
         const int bit = ring_bit(G, nt, old);
         if (bit >= 0) atomicOr(&ro.ring[(int64_t)nt * ro.mwords + (bit >> 6)], 1ull << (bit & 63));
@@ -139,6 +167,14 @@ struct Particles {
     uint32_t* id;
     uint32_t* key;
     uint32_t* gen;   // times the particle has been recycled (keys its Philox draw)
+};
+
+// The particle state seen by the tile kernels.
+template <class R>
+struct TileState {
+    Particles<R> pt[2];
+    uint32_t* cs[2];
+    const uint8_t* tpar;           // buffer of each tile
 };
 
 template <class A, class R>
@@ -442,8 +478,8 @@ __device__ __forceinline__ void p2g_tile(const Geom& G, const Particles<R>& pt, 
 {
     typedef Op<R> O;
     if (!clk->active) return;
-    const uint32_t beg = cellstart[(int64_t)tile * G.Tvol];
-    const uint32_t end = cellstart[(int64_t)(tile + 1) * G.Tvol];
+    const uint32_t beg = cellstart[tile_cs0(G, tile)];
+    const uint32_t end = cellstart[tile_cs0(G, tile) + G.Tvol];
     if (beg == end) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A* s = reinterpret_cast<A*>(smem_raw);
@@ -535,10 +571,11 @@ __device__ __forceinline__ void p2g_tile(const Geom& G, const Particles<R>& pt, 
 }
 
 template <int D, int P, class R, class A>
-__global__ void __launch_bounds__(256) k_p2g(Geom G, Particles<R> pt, Grid<A, R> gr, const uint32_t* cellstart,
-                                             Clock* clk)
+__global__ void __launch_bounds__(256) k_p2g(Geom G, TileState<R> ts, Grid<A, R> gr, Clock* clk)
 {
-    p2g_tile<D, P, R, A>(G, pt, gr, cellstart, clk, blockIdx.x);
+    const int t = blockIdx.x;
+    if (ts.tpar[t]) p2g_tile<D, P, R, A>(G, ts.pt[1], gr, ts.cs[1], clk, t);
+    else p2g_tile<D, P, R, A>(G, ts.pt[0], gr, ts.cs[0], clk, t);
 }
 
 // ----------------------------------------------- grid update + G2P + P2G
@@ -575,8 +612,8 @@ __device__ __forceinline__ void grid_g2p_tile(const Geom& G, const Particles<R>&
 {
     typedef Op<R> O;
     if (!clk->active) return;
-    const uint32_t beg = cellstart[(int64_t)tile * G.Tvol];
-    const uint32_t end = cellstart[(int64_t)(tile + 1) * G.Tvol];
+    const uint32_t beg = cellstart[tile_cs0(G, tile)];
+    const uint32_t end = cellstart[tile_cs0(G, tile) + G.Tvol];
     if (beg == end) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int W = G.Wvol;
@@ -671,22 +708,24 @@ __device__ __forceinline__ void grid_g2p_tile(const Geom& G, const Particles<R>&
 }
 
 template <int D, int P, class R, class A>
-__global__ void __launch_bounds__(256) k_grid_g2p(Geom G, Particles<R> pt, Grid<A, R> gr,
-                                                  const uint32_t* cellstart, Clock* clk)
+__global__ void __launch_bounds__(256) k_grid_g2p(Geom G, TileState<R> ts, Grid<A, R> gr, Clock* clk)
 {
-    grid_g2p_tile<D, P, R, A>(G, pt, gr, cellstart, clk, blockIdx.x);
+    const int t = blockIdx.x;
+    if (ts.tpar[t]) grid_g2p_tile<D, P, R, A>(G, ts.pt[1], gr, ts.cs[1], clk, t);
+    else grid_g2p_tile<D, P, R, A>(G, ts.pt[0], gr, ts.cs[0], clk, t);
 }
 
 // ------------------------------------ G2PD + particle update + move + key
 
 template <int D, int P, class R, class A>
 __device__ __forceinline__ void g2pd_tile(const Geom& G, const Particles<R>& pt, const Grid<A, R>& gr,
-                                          const uint32_t* cellstart, Clock* clk, const Reorder& ro, const int tile)
+                                          const uint32_t* cellstart, Clock* clk, const Reorder& ro, const int tile,
+                                          const int tp)
 {
     typedef Op<R> O;
     if (!clk->active) return;
-    const uint32_t beg = cellstart[(int64_t)tile * G.Tvol];
-    const uint32_t end = cellstart[(int64_t)(tile + 1) * G.Tvol];
+    const uint32_t beg = cellstart[tile_cs0(G, tile)];
+    const uint32_t end = cellstart[tile_cs0(G, tile) + G.Tvol];
     if (beg == end) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int W = G.Wvol;
@@ -844,7 +883,8 @@ __device__ __forceinline__ void g2pd_tile(const Geom& G, const Particles<R>& pt,
         int old[3] = {0, 0, 0};
 #pragma unroll
         for (int a = 0; a < D; ++a) old[a] = wrap_span(G, a, sx[a].c);
-        pt.key[k] = record_key(G, ro, clk, key_of<R>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, tile, old, err);
+        pt.key[k] = record_key(G, ro, clk, key_of<R>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, tile, old, err,
+                               tp);
         pt.E[k] = En_s;
         pt.rho[k] = rn_s;
         pt.Q[k] = Qn_s;
@@ -863,10 +903,11 @@ __device__ __forceinline__ void g2pd_tile(const Geom& G, const Particles<R>& pt,
 }
 
 template <int D, int P, class R, class A>
-__global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R> gr, const uint32_t* cellstart,
-                                              Clock* clk, Reorder ro)
+__global__ void __launch_bounds__(256) k_g2pd(Geom G, TileState<R> ts, Grid<A, R> gr, Clock* clk, Reorder ro)
 {
-    g2pd_tile<D, P, R, A>(G, pt, gr, cellstart, clk, ro, blockIdx.x);
+    const int t = blockIdx.x;
+    if (ts.tpar[t]) g2pd_tile<D, P, R, A>(G, ts.pt[1], gr, ts.cs[1], clk, ro, t, 1);
+    else g2pd_tile<D, P, R, A>(G, ts.pt[0], gr, ts.cs[0], clk, ro, t, 0);
 }
 
 // ---------------------------------------------------------- time control
@@ -875,6 +916,7 @@ __global__ void __launch_bounds__(256) k_g2pd(Geom G, Particles<R> pt, Grid<A, R
 __device__ __forceinline__ void prepare_clock(Clock& c)
 {
     c.nfar = 0u;
+    c.overflow = 0u;
     if (c.done || c.err || (c.step_end > 0 && c.step >= c.step_end)) { c.active = 0; return; }
     double h = c.dt_fixed > 0.0 ? c.dt_fixed : c.dt_next;
     if (!(h > 0.0)) { c.err |= ERR_NONFINITE; c.active = 0; return; }
@@ -918,14 +960,55 @@ __global__ void k_set_params(Clock* clk, double dt_fixed, double t_end)
     }
 }
 
+// Particles of each tile (from its cell starts).
+template <class R>
+__global__ void k_tile_counts(Geom G, TileState<R> ts, uint32_t* counts)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < G.ntiles;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t* cs = ts.cs[ts.tpar[t]];
+        counts[t] = cs[tile_cs0(G, t) + G.Tvol] - cs[tile_cs0(G, t)];
+    }
+}
+
+// Buffer and slot of the particle at position j of the key order; toff[t] is
+// the number of particles in the tiles before t (ntiles + 1 entries).
+template <class R>
+__device__ __forceinline__ int order_slot(const Geom& G, const TileState<R>& ts, const uint32_t* toff, int64_t j,
+                                          uint32_t& slot)
+{
+    int lo = 0, hi = G.ntiles - 1;      // the last tile whose first position is <= j
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int64_t)toff[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    const int tp = ts.tpar[lo];
+    slot = ts.cs[tp][tile_cs0(G, lo)] + (uint32_t)(j - (int64_t)toff[lo]);
+    return tp;
+}
+
+// out[j] = the field (a0 in buffer 0, a1 in buffer 1) of the particle at
+// position j of the key order.
+template <class T, class R>
+__global__ void k_compact(Geom G, TileState<R> ts, const uint32_t* toff, const T* a0, const T* a1, T* out, int64_t n)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t q;
+        const int tp = order_slot(G, ts, toff, j, q);
+        out[j] = tp ? a1[q] : a0[q];
+    }
+}
+
 // Initial CFL maxima over the particle state (Vbar := V before the first step).
 template <int D, class R>
-__global__ void k_cfl_init(Geom G, Particles<R> pt, int64_t n, Clock* clk)
+__global__ void k_cfl_init(Geom G, TileState<R> ts, const uint32_t* toff, int64_t n, Clock* clk)
 {
     typedef Op<R> O;
     R vmax = (R)0, cmax = (R)0;
     const R gm1 = (R)(G.gamma - 1.0), gam = (R)G.gamma;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t k;
+        const Particles<R>& pt = ts.pt[order_slot(G, ts, toff, j, k)];
         R v2 = (R)0;
 #pragma unroll
         for (int a = 0; a < D; ++a) v2 = O::add(v2, O::mul(pt.v[a][k], pt.v[a][k]));
@@ -997,11 +1080,14 @@ __global__ void k_gather(Particles<R> in, Particles<R> out, const uint32_t* perm
 // FP64 sums for the conservation diagnostics: one partial per block, summed
 // by k_cons_final in a fixed order (deterministic).
 template <int D, class R>
-__global__ void __launch_bounds__(256) k_cons_partial(Particles<R> pt, int64_t n, double* partial)
+__global__ void __launch_bounds__(256) k_cons_partial(Geom G, TileState<R> ts, const uint32_t* toff, int64_t n,
+                                                      double* partial)
 {
     __shared__ double sh[5][256];
     double s[5] = {0, 0, 0, 0, 0};
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t k;
+        const Particles<R>& pt = ts.pt[order_slot(G, ts, toff, j, k)];
         double M = (double)pt.M[k], v2 = 0.0;
 #pragma unroll
         for (int a = 0; a < D; ++a) {

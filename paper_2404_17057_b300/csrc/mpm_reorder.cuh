@@ -1,24 +1,37 @@
-// mpm_reorder.cuh -- per-step stable re-order of the particles (Sec. 3 step xii).
+// mpm_reorder.cuh -- per-step stable re-order of the particles (Sec. 3 step xii)
+// on tiles that own regions of the particle buffers.
 //
-// After the G2PD step every particle carries its new span key, and the
-// particles of every new span have been counted.  The time-step rule of
-// Sec. 4.1 (checked by the G2PD step) keeps every particle within one span of
-// where it was, so the particles that end up in a tile all come from the
-// tile's old spans and one ring of old spans around it.  One CTA per tile:
+// Tile t's particles occupy the first n_t slots of its region [tbase[t],
+// tbase[t + 1]) in buffer tpar[t], span after span; its cell starts are the
+// entries tile_cs0(t) .. tile_cs0(t) + Tvol of cs[tpar[t]].  The G2PD step
+// writes each particle's new key, moves one count from the old span to the
+// new one of every particle that changes span, marks the tiles whose lists
+// change (a particle left or entered one of their spans) and the ring parts
+// particles entered a tile from, and lists the particles recycled at the
+// inflow.  The time-step rule of Sec. 4.1 (checked
+// by the G2PD step) keeps every other particle within one span of where it
+// was, so the particles that end up in a tile come from the tile's old spans
+// and one ring of spans around it.
 //
-//   1. lists the old index ranges of that neighbourhood (one range per row of
-//      spans inside the tile, single spans outside it), ordered by old index;
-//   2. streams the keys of those ranges (coalesced) and compacts the particles
-//      whose new key lies in the tile into shared memory, in old order;
-//   3. ranks them per new span with per-warp counters (stable: a span keeps
-//      its particles' previous order) and copies each particle's state from
-//      the old buffer straight to its slot in the new one;
-//   4. appends the particles recycled at the inflow during the step (they
-//      were given the tail slots of their span by k_far_place), ordered by id.
-//
-// Scan of the counts into the new cell starts happens before (mpm_sort.cuh).
+// Pass 0, one tile at a time per CTA:
+//   - a tile whose lists did not change keeps its particles where they are
+//     (most of a domain at rest costs nothing);
+//   - a changed tile lists the old slot ranges of that neighbourhood, streams
+//     their keys, compacts the particles that now belong to it in old order,
+//     ranks them per new span (stable: a span keeps its particles' previous
+//     order) and copies each into its new slot in the same region of the
+//     other buffer; the particles recycled into it follow the others of
+//     their span, ordered by id; then it switches to that buffer;
+//   - a tile that would outgrow its region raises the clock's overflow flag
+//     and writes nothing.
+// If any tile overflowed, the state is laid out again: every tile's old
+// particles are first brought into buffer 0 (k_consolidate), regions are
+// sized anew from the new counts (k_relayout_bases), and pass 1 rebuilds
+// every tile from buffer 0 into buffer 1.  k_reorder_done clears the step's
+// marks and installs the new regions.
 #pragma once
 #include "mpm_kernels.cuh"
+#include "mpm_sort.cuh"
 
 namespace mpm {
 
@@ -28,11 +41,17 @@ constexpr int kReorderItems = 8;                                  // keys per th
 constexpr int kReorderChunk = kReorderThreads * kReorderItems;
 constexpr int kReorderCap = 6144;                                 // compacted particles per flush
 constexpr int kReorderMaxRanges = 1024;
+constexpr int kReorderFarCap = 1024;                              // recycled arrivals per tile
+
+// Region of a tile with n particles: room for twice as many plus 64, in
+// multiples of 32 slots (128-byte aligned starts in single precision).
+__host__ __device__ inline uint32_t region_slots(uint32_t n) { return (2u * n + 64u + 31u) & ~31u; }
 
 __host__ inline size_t reorder_smem(const Geom& G)
 {
     const size_t T = (size_t)G.Tvol, nr = (size_t)reorder_ranges(G);
-    return ((kReorderWarps + 2) * T + kReorderCap + 4 * nr + 2 + kReorderWarps) * 4 + kReorderCap * 2;
+    return ((kReorderWarps + 3) * T + kReorderCap + 4 * nr + 2 + kReorderWarps) * 4 + kReorderCap * 2 +
+           (size_t)kReorderFarCap * 8;
 }
 
 // The recycle count (gen) is read only by recycling, so problems without an
@@ -58,26 +77,28 @@ __device__ __forceinline__ void copy_particle(const Particles<R>& in, const Part
     if (with_gen) out.gen[j] = gen;
 }
 
-// Copy kB particles per lane, q[u] -> j[u] where ok[u]: all loads first, so
-// that 12 kB independent loads per lane are in flight.
+// Copy kB particles per lane, slot q[u] of buffer b[u] -> slot j[u] of out,
+// where ok[u]: all loads first, so that 12 kB independent loads per lane are
+// in flight.
 template <int kB, class R>
-__device__ __forceinline__ void copy_batch(const Particles<R>& in, const Particles<R>& out, int D, const uint32_t* q,
-                                           const uint32_t* j, const bool* ok, bool with_gen)
+__device__ __forceinline__ void copy_batch(const Particles<R>* in, const Particles<R>& out, int D, const uint32_t* q,
+                                           const int* b, const uint32_t* j, const bool* ok, bool with_gen)
 {
     R xv[kB][6], M[kB], rho[kB], E[kB], Q[kB];
     uint32_t id[kB], gen[kB];
 #pragma unroll
     for (int u = 0; u < kB; ++u) {
         if (!ok[u]) continue;
+        const Particles<R>& s = in[b[u]];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            if (a < D) { xv[u][a] = in.x[a][q[u]]; xv[u][3 + a] = in.v[a][q[u]]; }
-        M[u] = in.M[q[u]];
-        rho[u] = in.rho[q[u]];
-        E[u] = in.E[q[u]];
-        Q[u] = in.Q[q[u]];
-        id[u] = in.id[q[u]];
-        gen[u] = with_gen ? in.gen[q[u]] : 0u;
+            if (a < D) { xv[u][a] = s.x[a][q[u]]; xv[u][3 + a] = s.v[a][q[u]]; }
+        M[u] = s.M[q[u]];
+        rho[u] = s.rho[q[u]];
+        E[u] = s.E[q[u]];
+        Q[u] = s.Q[q[u]];
+        id[u] = s.id[q[u]];
+        gen[u] = with_gen ? s.gen[q[u]] : 0u;
     }
 #pragma unroll
     for (int u = 0; u < kB; ++u) {
@@ -94,60 +115,123 @@ __device__ __forceinline__ void copy_batch(const Particles<R>& in, const Particl
     }
 }
 
-// Recycled particles may land anywhere: each takes a slot at the end of its
-// new span's segment (count[K] counts down to the span's stayers); their
-// order inside the span is fixed by k_reorder (by id).
-__device__ __forceinline__ void far_place_block(const uint2* __restrict__ far, uint32_t far_cap,
-                                                uint32_t* __restrict__ count, const uint32_t* __restrict__ cs_new,
-                                                uint32_t* __restrict__ perm, const Clock* clk, unsigned blk,
-                                                unsigned nblk)
-{
-    if (!clk->active) return;
-    const unsigned F = min(clk->nfar, far_cap);
-    for (unsigned i = blk * blockDim.x + threadIdx.x; i < F; i += nblk * blockDim.x) {
-        const uint2 e = far[i];
-        const uint32_t r = atomicSub(&count[e.x], 1u) - 1u;
-        const uint32_t pos = cs_new[e.x] + r;
-        if (pos < cs_new[e.x + 1]) perm[pos] = e.y;
-    }
-}
+// What one re-order pass needs of a simulation.
+template <class R>
+struct ReorderArgs {
+    Particles<R> pt[2];
+    uint32_t* cs[2];
+    const uint8_t* tpar_old;        // buffer of each tile during the step
+    uint8_t* tpar_new;              // ... after the re-order
+    const uint32_t* tbase;          // regions (ntiles + 1 entries)
+    uint32_t* tbase_next;           // regions of a relayout
+    uint32_t* tcount;               // particles of each tile after the step
+    Reorder ro;
+    Clock* clk;
+};
 
-__global__ void k_far_place(const uint2* __restrict__ far, uint32_t far_cap, uint32_t* __restrict__ count,
-                            const uint32_t* __restrict__ cs_new, uint32_t* __restrict__ perm, const Clock* clk)
-{
-    far_place_block(far, far_cap, count, cs_new, perm, clk, blockIdx.x, gridDim.x);
-}
-
+// Tile t, pass `mode` (0: changed tiles into their other buffer; 1: relayout,
+// every tile from buffer 0 into buffer 1, only if a tile overflowed).
 template <int D, class R>
-__device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& in, const Particles<R>& out,
-                                             const uint32_t* __restrict__ cs_old, uint32_t* cs_new,
-                                             uint32_t* __restrict__ count, uint32_t* perm, int64_t n,
-                                             unsigned long long* __restrict__ ring, int mwords, Clock* clk, const int t)
+__device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>& A, const int mode, const int t)
 {
     extern __shared__ __align__(16) uint32_t reorder_sm[];
     const int Tvol = G.Tvol;
     const int nrmax = reorder_ranges(G);
-    uint32_t* cnt = reorder_sm;                                 // [warp][span of tile]
+    uint32_t* cnt = reorder_sm;                           // [warp][span of tile]
     uint32_t* base = cnt + kReorderWarps * Tvol;          // next slot of each span
     uint32_t* endv = base + Tvol;                         // end of each span's stayers
-    uint32_t* list_q = endv + Tvol;                       // compacted old indices
-    uint32_t* ustart = list_q + kReorderCap;              // ranges as listed
+    uint32_t* news = endv + Tvol;                         // new start of each span
+    uint32_t* list_q = news + Tvol;                       // compacted slots (bit 31: buffer)
+    uint32_t* ustart = list_q + kReorderCap;              // ranges as listed (bit 31: buffer)
     uint32_t* ulen = ustart + nrmax;
-    uint32_t* sstart = ulen + nrmax;                      // ranges by old index
+    uint32_t* sstart = ulen + nrmax;                      // ranges by old slot
     uint32_t* soff = sstart + nrmax;                      // exclusive prefix of lengths (nrmax + 1)
     uint32_t* wsum = soff + nrmax + 1;                    // per-warp totals (+1 spare)
     uint16_t* list_k = reinterpret_cast<uint16_t*>(wsum + kReorderWarps + 1);
+    uint2* farl = reinterpret_cast<uint2*>(list_k + kReorderCap);   // {local span, slot | buffer}, by id
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t K0 = (int64_t)t * Tvol;
+    const int64_t C0 = tile_cs0(G, t);
+    Clock* clk = A.clk;
+    const bool relayout = mode == 1;
+    const int tp = relayout ? 0 : A.tpar_old[t];
+    __shared__ int s_skip;
 
-    if (!clk->active) {
-        // no step was taken: same order, same cell starts
-        const uint32_t b = cs_old[K0], e = cs_old[K0 + Tvol];
-        for (uint32_t j = b + tid; j < e; j += kReorderThreads) copy_particle(in, out, D, j, j, G.inflow_face >= 0);
-        const int last = (t == G.ntiles - 1) ? 1 : 0;
-        for (int k = tid; k < Tvol + last; k += kReorderThreads) cs_new[K0 + k] = cs_old[K0 + k];
-        return;
+    if (!relayout) {
+        // an unchanged tile (and every tile of a step that was not taken)
+        if (!clk->active || !A.ro.dirty[t]) {
+            if (tid == 0) {
+                A.tpar_new[t] = (uint8_t)tp;
+                A.tcount[t] = A.cs[tp][C0 + Tvol] - A.cs[tp][C0];
+            }
+            return;
+        }
+    }
+    const int dst = relayout ? 1 : 1 - tp;
+    const uint32_t* rb = relayout ? A.tbase_next : A.tbase;
+    const uint32_t rbeg = rb[t], rcap = rb[t + 1] - rb[t];
+    const Particles<R>& out = A.pt[dst];
+    int err = 0;
+
+    // new span counts (old counts plus the step's changes) -> new starts
+    // (block scan), and the tile's total
+    const uint32_t* cso = A.cs[tp];          // the tile's old cell starts (relayout: consolidated)
+    uint32_t total = 0;
+    for (int k0 = 0; k0 < Tvol; k0 += kReorderThreads) {
+        const int k = k0 + tid;
+        const uint32_t c = k < Tvol ? cso[C0 + k + 1] - cso[C0 + k] + A.ro.count[K0 + k] : 0u;
+        const uint32_t inc = block_inclusive_scan(c, wsum);
+        if (k < Tvol) news[k] = rbeg + total + inc - c;
+        if (tid == kReorderThreads - 1) wsum[kReorderWarps] = inc;
+        __syncthreads();
+        total += wsum[kReorderWarps];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        s_skip = 0;
+        if (!relayout) A.tcount[t] = total;
+        if (total > rcap) {
+            if (!relayout) atomicOr(&clk->overflow, 1u);
+            else atomicOr(&clk->err, ERR_TILE);
+            s_skip = 1;
+            A.tpar_new[t] = (uint8_t)tp;
+        }
+    }
+    __syncthreads();
+    if (s_skip) return;
+
+    // particles recycled into this tile (they may come from anywhere)
+    const int lsh = G.tsh[0] + G.tsh[1] + G.tsh[2];
+    const uint32_t lmask = (uint32_t)Tvol - 1u;
+    __shared__ uint32_t s_nfar;
+    if (tid == 0) s_nfar = 0;
+    for (int k = tid; k < Tvol; k += kReorderThreads) {
+        endv[k] = 0u;
+#pragma unroll
+        for (int w = 0; w < kReorderWarps; ++w) cnt[w * Tvol + k] = 0u;
+    }
+    __syncthreads();
+    const uint32_t F = A.ro.far_cap ? min(clk->nfar, A.ro.far_cap) : 0u;
+    for (uint32_t i = tid; i < F; i += kReorderThreads) {
+        const uint2 e = A.ro.far[i];
+        if ((e.x >> lsh) != (uint32_t)t) continue;
+        const uint32_t at = atomicAdd(&s_nfar, 1u);
+        if (at < (uint32_t)kReorderFarCap) {
+            farl[at] = make_uint2(e.x & lmask, relayout ? (e.y & 0x7fffffffu) : e.y);
+            atomicAdd(&endv[e.x & lmask], 1u);      // recycled arrivals per span (for now)
+        } else {
+            err |= ERR_TILE;
+        }
+    }
+    __syncthreads();
+    const uint32_t nfar = min(s_nfar, (uint32_t)kReorderFarCap);
+    for (int k = tid; k < Tvol; k += kReorderThreads) {
+        const uint32_t nf = endv[k];
+        const uint32_t c = (k + 1 < Tvol ? news[k + 1] : rbeg + total) - news[k];
+        if (nf > c) err |= ERR_TILE;
+        base[k] = news[k];
+        endv[k] = news[k] + (nf > c ? 0u : c - nf);
     }
 
     // tile position and its real spans
@@ -166,21 +250,22 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
     const int nrows = ny * nz;
     int nr = 3 * nrows;
     // ring parts that particles entered this tile from (set by the G2PD step)
+    const int mwords = A.ro.mwords;
     __shared__ unsigned long long rbits[kReorderMaxRanges / 64];
     for (int w = tid; w < kReorderMaxRanges / 64; w += kReorderThreads)
-        rbits[w] = w < mwords ? ring[(int64_t)t * mwords + w] : 0ull;
-
-    for (int k = tid; k < kReorderWarps * Tvol; k += kReorderThreads) cnt[k] = 0u;
-    int err = 0;
-    for (int k = tid; k < Tvol; k += kReorderThreads) {
-        const uint32_t s0 = cs_new[K0 + k], s1 = cs_new[K0 + k + 1];
-        uint32_t stay = count[K0 + k];
-        if (stay > s1 - s0) { err |= ERR_TILE; stay = 0; }
-        base[k] = s0;
-        endv[k] = s0 + stay;
-    }
+        rbits[w] = w < mwords ? A.ro.ring[(int64_t)t * mwords + w] : 0ull;
     __syncthreads();
-    // 1. old index ranges of the tile's rows and of the ring parts entered
+    // old slot range of the spans a0..a1 of one row (one tile), in the
+    // buffer that tile's particles are in
+    auto range = [&](const int a0[3], const int a1[3], uint32_t& b, uint32_t& l) {
+        const uint32_t k0 = key_of<float>(G, a0), k1 = key_of<float>(G, a1);
+        const int src = relayout ? 0 : A.tpar_old[k0 >> lsh];
+        const uint32_t* cso = A.cs[src];
+        b = cso[cs_index(G, k0)];
+        l = cso[cs_index(G, k1) + 1] - b;
+        b |= (uint32_t)src << 31;
+    };
+    // 1. old slot ranges of the tile's rows and of the ring parts entered
     for (int row = tid; row < nrows; row += kReorderThreads) {
         const int iy = row % ny, iz = row / ny;
         const bool inner = iy <= hi[1] - lo[1] && iz <= hi[2] - lo[2];
@@ -191,8 +276,7 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
             uint32_t b = 0, l = 0;
             if (inner || marked(3 * row)) {
                 const int a0[3] = {lo[0], y, z}, a1[3] = {hi[0], y, z};
-                b = cs_old[key_of<float>(G, a0)];
-                l = cs_old[key_of<float>(G, a1) + 1] - b;
+                range(a0, a1, b, l);
             }
             ustart[3 * row] = b;
             ulen[3 * row] = l;
@@ -201,16 +285,15 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
             uint32_t b = 0, l = 0;
             if (j < nex[0] && marked(3 * row + 1 + j)) {
                 const int sp[3] = {ex[0][j], y, z};
-                const uint32_t k = key_of<float>(G, sp);
-                b = cs_old[k];
-                l = cs_old[k + 1] - b;
+                range(sp, sp, b, l);
             }
             ustart[3 * row + 1 + j] = b;
             ulen[3 * row + 1 + j] = l;
         }
     }
     __syncthreads();
-    // the non-empty ranges, ordered by old index (one warp: typically the
+    // the non-empty ranges, ordered by (buffer, slot) -- within one buffer by
+    // old position, which is the old key order (one warp: typically the
     // tile's own rows and a few ring parts)
     __shared__ int nr_used;
     if (warp == 0) {
@@ -228,11 +311,18 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
             k += __popc(m);
         }
         __syncwarp();
-        // non-empty ranges are disjoint: their starts differ
+        // non-empty ranges are disjoint: their (buffer, start) pairs differ.
+        // Old key order across buffers: regions are in tile order in both
+        // buffers, so ordering by the slot alone (buffer bit dropped) is the
+        // old key order.
         for (int i = lane; i < k; i += 32) {
             const uint32_t si = ustart[i];
+            const uint32_t sv = si & 0x7fffffffu;
             int rank = 0;
-            for (int j = 0; j < k; ++j) rank += ustart[j] < si ? 1 : 0;
+            for (int j = 0; j < k; ++j) {
+                const uint32_t vj = ustart[j] & 0x7fffffffu;
+                rank += (vj < sv || (vj == sv && ustart[j] < si)) ? 1 : 0;
+            }
             sstart[rank] = si;
             soff[rank] = ulen[i];    // length for now; prefix below
         }
@@ -258,8 +348,7 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
     __syncthreads();
     nr = nr_used;
     const uint32_t C = soff[nr];
-    const int lsh = G.tsh[0] + G.tsh[1] + G.tsh[2];
-    const uint32_t lmask = (uint32_t)Tvol - 1u;
+    const bool with_gen = G.inflow_face >= 0;
 
     uint32_t L = 0;
     for (uint32_t cb = 0; cb < C; cb += kReorderChunk) {
@@ -284,10 +373,10 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
                 } else {
                     while (soff[r + 1] <= c) ++r;
                 }
-                const uint32_t q = sstart[r] + (c - soff[r]);
-                const uint32_t k = in.key[q];
+                const uint32_t qb = sstart[r] + (c - soff[r]);      // bit 31 carried from the range
+                const uint32_t k = A.pt[qb >> 31].key[qb & 0x7fffffffu];
                 hit = (k >> lsh) == (uint32_t)t;
-                myq[i] = q;
+                myq[i] = qb;
                 mykl[i] = k & lmask;
             }
             bal[i] = __ballot_sync(0xffffffffu, hit);
@@ -343,6 +432,7 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
         constexpr int kB = sizeof(R) == 4 ? 4 : 2;     // particles per lane per batch
         for (uint32_t j0 = wb; j0 < we; j0 += 32 * kB) {
             uint32_t qv[kB], pv[kB];
+            int bv[kB];
             bool okv[kB];
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
@@ -351,19 +441,21 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
                 const uint32_t kl = valid ? list_k[j] : 0xffffffffu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, kl);
                 const int leader = __ffs(peers) - 1;
-                uint32_t bv = 0;
-                if (valid && lane == leader) bv = wc[kl];
-                bv = __shfl_sync(0xffffffffu, bv, leader);
-                const uint32_t pos = bv + __popc(peers & lt);
+                uint32_t b0 = 0;
+                if (valid && lane == leader) b0 = wc[kl];
+                b0 = __shfl_sync(0xffffffffu, b0, leader);
+                const uint32_t pos = b0 + __popc(peers & lt);
                 okv[u] = valid && pos < endv[kl];
                 if (valid && !okv[u]) err |= ERR_TILE;
-                qv[u] = valid ? list_q[j] : 0u;
+                const uint32_t qb = valid ? list_q[j] : 0u;
+                qv[u] = qb & 0x7fffffffu;
+                bv[u] = (int)(qb >> 31);
                 pv[u] = pos;
                 __syncwarp();
-                if (valid && lane == leader) wc[kl] = bv + __popc(peers);
+                if (valid && lane == leader) wc[kl] = b0 + __popc(peers);
                 __syncwarp();
             }
-            copy_batch<kB>(in, out, D, qv, pv, okv, G.inflow_face >= 0);
+            copy_batch<kB>(A.pt, out, D, qv, bv, pv, okv, with_gen);
         }
         __syncthreads();
         for (int k = tid; k < kReorderWarps * Tvol; k += kReorderThreads) cnt[k] = 0u;
@@ -371,40 +463,174 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const Particles<R>& 
         __syncthreads();
     }
 
-    for (int w = tid; w < mwords; w += kReorderThreads) ring[(int64_t)t * mwords + w] = 0ull;
-    // 4. every span got exactly its stayers; then its recycled particles by id
-    for (int k = tid; k < Tvol; k += kReorderThreads) {
-        const int64_t K = K0 + k;
-        if (count[K]) count[K] = 0u;
-        if (base[k] != endv[k]) { err |= ERR_TILE; continue; }
-        const uint32_t fb = endv[k], fe = cs_new[K + 1];
-        if (fb == fe) continue;
-        if (fb > fe || perm == nullptr) { err |= ERR_TILE; continue; }
-        bool ok = true;
-        for (uint32_t i = fb; i < fe; ++i) ok = ok && (int64_t)perm[i] < n;
-        if (!ok) { err |= ERR_TILE; continue; }
-        for (uint32_t i = fb + 1; i < fe; ++i) {
-            const uint32_t v = perm[i], vid = in.id[v];
-            uint32_t j = i;
-            while (j > fb && in.id[perm[j - 1]] > vid) { perm[j] = perm[j - 1]; --j; }
-            perm[j] = v;
+    // 4. every span got exactly its stayers; then its recycled particles by
+    // id (the tile's recycled arrivals, sorted by (span, id): few)
+    if (nfar > 0) {
+        if (tid == 0) {
+            for (uint32_t i = 1; i < nfar; ++i) {
+                const uint2 v = farl[i];
+                const uint32_t vid = A.pt[v.y >> 31].id[v.y & 0x7fffffffu];
+                uint32_t j = i;
+                while (j > 0) {
+                    const uint2 u = farl[j - 1];
+                    const uint32_t uid = A.pt[u.y >> 31].id[u.y & 0x7fffffffu];
+                    if (u.x < v.x || (u.x == v.x && uid < vid)) break;
+                    farl[j] = u;
+                    --j;
+                }
+                farl[j] = v;
+            }
         }
-        for (uint32_t i = fb; i < fe; ++i) copy_particle(in, out, D, perm[i], i, true);
+        __syncthreads();
+        // arrivals of one span are consecutive in farl: place each after the
+        // span's stayers
+        for (uint32_t i = tid; i < nfar; i += kReorderThreads) {
+            const uint2 v = farl[i];
+            uint32_t first = i;
+            while (first > 0 && farl[first - 1].x == v.x) --first;
+            const uint32_t pos = endv[v.x] + (i - first);
+            if (pos < (v.x + 1 < (uint32_t)Tvol ? news[v.x + 1] : rbeg + total))
+                copy_particle(A.pt[v.y >> 31], out, D, v.y & 0x7fffffffu, pos, true);
+            else
+                err |= ERR_TILE;
+        }
+    }
+    for (int k = tid; k < Tvol; k += kReorderThreads)
+        if (base[k] != endv[k]) err |= ERR_TILE;
+    // the new cell starts, and the tile's buffer
+    uint32_t* csn = A.cs[dst];
+    for (int k = tid; k < Tvol; k += kReorderThreads) csn[C0 + k] = news[k];
+    if (tid == 0) {
+        csn[C0 + Tvol] = rbeg + total;
+        A.tpar_new[t] = (uint8_t)dst;
     }
     if (err) atomicOr(&clk->err, err);
 }
 
+// Pass `mode` over the tiles of one simulation (persistent CTAs).
 template <int D, class R>
-__global__ void __launch_bounds__(kReorderThreads, 3) k_reorder(Geom G, Particles<R> in, Particles<R> out,
-                                                             const uint32_t* __restrict__ cs_old, uint32_t* cs_new,
-                                                             uint32_t* __restrict__ count, uint32_t* perm, int64_t n,
-                                                             unsigned long long* __restrict__ ring, int mwords,
-                                                             Clock* clk)
+__global__ void __launch_bounds__(kReorderThreads, 3) k_reorder(Geom G, ReorderArgs<R> A, int mode)
 {
-    reorder_tile<D, R>(G, in, out, cs_old, cs_new, count, perm, n, ring, mwords, clk, blockIdx.x);
+    if (mode == 1 && !A.clk->overflow) return;
+    for (int t = blockIdx.x; t < G.ntiles; t += gridDim.x) {
+        reorder_tile<D, R>(G, A, mode, t);
+        __syncthreads();
+    }
 }
 
-// Sorted keys from the cell-start table (for reading the state back).
+// Relayout, step 1: the old particles (with the new keys the G2PD step gave
+// them) and the cell starts of every tile in buffer 1 are copied to the same
+// slots / entries of buffer 0.
+template <int D, class R>
+__device__ __forceinline__ void consolidate_tile(const Geom& G, const ReorderArgs<R>& A, const int t)
+{
+    if (A.tpar_old[t] != 1) return;
+    const int64_t C0 = tile_cs0(G, t);
+    const uint32_t b = A.cs[1][C0], e = A.cs[1][C0 + G.Tvol];
+    for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+        copy_particle(A.pt[1], A.pt[0], D, j, j, true);
+        A.pt[0].key[j] = A.pt[1].key[j];
+    }
+    for (int k = threadIdx.x; k <= G.Tvol; k += blockDim.x) A.cs[0][C0 + k] = A.cs[1][C0 + k];
+}
+
+template <int D, class R>
+__global__ void __launch_bounds__(kReorderThreads) k_consolidate(Geom G, ReorderArgs<R> A)
+{
+    if (!A.clk->overflow) return;
+    for (int t = blockIdx.x; t < G.ntiles; t += gridDim.x) consolidate_tile<D, R>(G, A, t);
+}
+
+// Relayout, step 2: regions sized for the new counts (one block).
+__device__ __forceinline__ void relayout_bases_block(const uint32_t* tcount, int ntiles, uint32_t* tbase_next)
+{
+    __shared__ uint32_t ws[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b = 0; b < ntiles; b += blockDim.x) {
+        const int i = b + threadIdx.x;
+        const uint32_t v = i < ntiles ? region_slots(tcount[i]) : 0u;
+        const uint32_t inc = block_inclusive_scan(v, ws);
+        const uint32_t c = carry;
+        if (i < ntiles) tbase_next[i] = c + inc - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = c + inc;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tbase_next[ntiles] = carry;
+}
+
+__global__ void __launch_bounds__(1024) k_relayout_bases(const uint32_t* tcount, int ntiles, uint32_t* tbase_next,
+                                                         const Clock* clk)
+{
+    if (!clk->overflow) return;
+    relayout_bases_block(tcount, ntiles, tbase_next);
+}
+
+// End of the re-order: clear the changed tiles' marks, install the regions of
+// a relayout.
+__device__ __forceinline__ void reorder_done_tile(int tvol, const Reorder& ro, Clock* clk, uint32_t* tbase,
+                                                  const uint32_t* tbase_next, int t, int ntiles)
+{
+    // only a changed tile has count changes and ring marks
+    if (ro.dirty[t]) {
+        for (int w = 0; w < ro.mwords; ++w) ro.ring[(int64_t)t * ro.mwords + w] = 0ull;
+        uint4* c4 = reinterpret_cast<uint4*>(ro.count + (int64_t)t * tvol);
+        for (int k = 0; k < tvol / 4; ++k) c4[k] = make_uint4(0u, 0u, 0u, 0u);
+        ro.dirty[t] = 0u;
+    }
+    if (clk->overflow) {
+        tbase[t] = tbase_next[t];
+        if (t == ntiles - 1) tbase[ntiles] = tbase_next[ntiles];
+        if (t == 0) clk->relayouts += 1;
+    }
+}
+
+__global__ void k_reorder_done(Geom G, Reorder ro, Clock* clk, uint32_t* tbase, const uint32_t* tbase_next)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G.ntiles; t += gridDim.x * blockDim.x)
+        reorder_done_tile(G.Tvol, ro, clk, tbase, tbase_next, t, G.ntiles);
+}
+
+// Initial layout: the particles of a compact key order (cell starts cc[key],
+// nkey + 1 entries, of buffer `from`) spread into the regions tbase of buffer
+// `to`, with the per-tile cell starts cs_to.
+template <int D, class R>
+__global__ void k_spread(Geom G, Particles<R> from, Particles<R> to, const uint32_t* cc, const uint32_t* tbase,
+                         uint32_t* cs_to)
+{
+    for (int t = blockIdx.x; t < G.ntiles; t += gridDim.x) {
+        const int64_t K0 = (int64_t)t * G.Tvol, C0 = tile_cs0(G, t);
+        const uint32_t b = cc[K0], e = cc[K0 + G.Tvol], rb = tbase[t];
+        for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) copy_particle(from, to, D, j, rb + (j - b), true);
+        for (int k = threadIdx.x; k <= G.Tvol; k += blockDim.x) cs_to[C0 + k] = rb + (cc[K0 + k] - b);
+    }
+}
+
+// Particles of each tile from a compact cell-start table (nkey + 1 entries).
+__global__ void k_tile_counts_compact(const uint32_t* cc, int64_t ntiles, int tvol, uint32_t* counts)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x)
+        counts[t] = cc[(t + 1) * tvol] - cc[t * tvol];
+}
+
+// Compact cell starts (key order without gaps) from the per-tile table:
+// out[key] = toff[t] + (start of the span - start of the tile), out[nkey] = n.
+__global__ void k_compact_starts(Geom G, const uint32_t* cs0, const uint32_t* cs1, const uint8_t* tpar,
+                                 const uint32_t* toff, uint32_t* out)
+{
+    for (int64_t key = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; key <= G.nkey;
+         key += (int64_t)gridDim.x * blockDim.x) {
+        if (key == G.nkey) { out[key] = toff[G.ntiles]; continue; }
+        const int64_t t = key / G.Tvol;
+        const uint32_t* cs = tpar[t] ? cs1 : cs0;
+        const int64_t C0 = tile_cs0(G, t);
+        out[key] = toff[t] + (cs[C0 + (key - t * G.Tvol)] - cs[C0]);
+    }
+}
+
+// Sorted keys from a compact cell-start table (for reading the state back).
 __global__ void k_keys_from_start(const uint32_t* cs, int64_t nkey, uint32_t* out)
 {
     for (int64_t K = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; K < nkey; K += (int64_t)gridDim.x * blockDim.x)

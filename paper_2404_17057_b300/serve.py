@@ -27,8 +27,10 @@ from . import mpm as M
 
 
 def footprint_bytes(prob) -> int:
-    """Device bytes a problem holds while resident (particle state double
-    buffered with sort scratch, grid accumulators, masks)."""
+    """Device bytes a problem holds while resident: two particle buffers of
+    2 n + 95 x tiles slots (every tile owns a region with room to grow; tiles
+    hold at least 32 spans), the initial sort's scratch, grid accumulators,
+    masks, per-span and per-tile tables."""
     cfg = prob.cfg
     d = int(cfg["dim"])
     p = int(cfg["degree"])
@@ -41,9 +43,11 @@ def footprint_bytes(prob) -> int:
         per = cfg["bc"][2 * a] in ("periodic", 1)
         nodes *= (cfg["n"][a] if per else cfg["n"][a] + 2 * p - 1) + 3
         spans *= cfg["n"][a] + 1 + 64
-    part = 2 * n * ((2 * d + 4) * real + 12) + 4 * n * 4 + n * 8
+    tiles = spans // 32 + 1
+    slots = 2 * n + 95 * tiles
+    part = 2 * slots * ((2 * d + 4) * real + 12) + 4 * n * 4 + n * 8
     grid = (1 + 3 * d) * nodes * acc + nodes * (1 + d * real)
-    return int(part + grid + 4 * spans + (1 << 20))
+    return int(part + grid + 12 * spans + 32 * tiles + (1 << 20))
 
 
 @dataclasses.dataclass

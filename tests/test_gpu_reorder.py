@@ -61,7 +61,30 @@ def cylinder(precision):
     return f32(p) if precision != "fp64" else p
 
 
+def crowding(precision):
+    """A cluster of 400 particles moves at 0.3 spans a step through the last
+    spans of one tile (which switches buffers each time its lists change) into
+    the next tile, which held 8: that tile outgrows its region in step 7 and
+    the whole state is laid out again (relayout) from both buffers."""
+    n, h = [64, 32], 1.0 / 64
+    cfg = I.base_config(2, n, h, ["wall"] * 4, degree=2, precision=precision, tile=[32, 8, 0])
+    rng = np.random.default_rng(23)
+    xc = np.stack([np.full(400, 29.45 * h), (0.5 + 7.0 * rng.random(400)) * h])
+    xb = np.stack([(32.5 + 4 * np.arange(8)) * h, np.full(8, 4.0 * h)])
+    # a sparse lattice over the rest of the domain, one particle per 4 x 4 cells
+    gx, gy = np.meshgrid((2.5 + 4 * np.arange(16)) * h, (10.5 + 4 * np.arange(5)) * h, indexing="ij")
+    xr = np.stack([gx.ravel(), gy.ravel()])
+    x = np.concatenate([xc, xb, xr], axis=1)
+    N = x.shape[1]
+    v = np.zeros((2, N))
+    v[0, :400] = 1.0
+    p = I.Problem("crowding", cfg, x, v, np.full(N, 1e-4), np.ones(N), np.full(N, 0.025))
+    p.meta = {"dt": 0.3 * h}
+    return f32(p)
+
+
 CASES = [
+    ("crowding", "fp32", lambda: crowding("fp32")),
     ("blast3d_periodic", "fp32", lambda: periodic_blast("fp32")),
     ("blast3d_periodic", "fp32_fixed64", lambda: periodic_blast("fp32_fixed64")),
     ("cylinder", "fp32", lambda: cylinder("fp32")),
@@ -79,10 +102,11 @@ def test_step_reorder_equals_oracle_rule(name, precision, make):
     nkeys = sim.sizes()["keys"]
     prec32 = precision != "fp64"
     moved = recycled = 0
+    dt = (p.meta or {}).get("dt", 0.0) if name == "crowding" else 0.0
     for step in range(12):
         ids0 = sim.read("ID").astype(np.int64)
         gen0 = sim.read("GEN")
-        sim.step(1)
+        sim.step(1, dt=dt)
         ids1 = sim.read("ID").astype(np.int64)
         x1 = sim.read("X")
         key1 = sim.read("KEY").astype(np.int64)
@@ -103,4 +127,6 @@ def test_step_reorder_equals_oracle_rule(name, precision, make):
     assert moved > 0
     if name == "cylinder":
         assert recycled > 0
+    if name == "crowding":
+        assert sim.read("CLOCK")[3] >= 1      # a relayout happened
     sim.close()
