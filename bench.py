@@ -62,6 +62,10 @@ def parse():
                     help="C4 precision sweep on the cylinder with this many steps (0: skip)")
     ap.add_argument("--sweep-n", type=int, default=1024, help="cylinder x cells for the sweep")
     ap.add_argument("--sweep-out", default="c4_fields", help="directory for the sweep's fields")
+    ap.add_argument("--sweep-t-end", type=float, default=0.0,
+                    help="run every mode to this simulated time instead of a step count (the time the FP64 oracle "
+                         "reaches in --sweep steps): CFL steps depend on the largest particle speed, so equal step "
+                         "counts are not equal times")
     return ap.parse_args()
 
 
@@ -310,17 +314,22 @@ def c4_problem(n):
     return base
 
 
+C4_SAMPLE = 8   # the fields of every 8th particle id are written
+
+
 def sweep(args):
     """C4 on the GPU: the cylinder in FP32 (float atomics), FP32 + int64 fixed
     point (unit 1 and normalised units) and FP64, each run twice for
-    `--sweep` steps.  Writes each mode's fields (by particle id) to
-    `--sweep-out`/c4_<mode>.npz and reports whether the two runs agree bit for
-    bit.  The comparison with the FP64 oracle is tests/c4_compare.py."""
+    `--sweep` steps.  Reports whether the two runs agree bit for bit (all
+    particles) and writes each mode's fields of every C4_SAMPLE-th particle
+    id, in the storage precision, to `--sweep-out`/c4_<mode>.npz.  The
+    comparison with the FP64 oracle is tests/c4_compare.py."""
     from paper_2404_17057_b300 import inputs as I, mpm as M
     n = args.sweep_n
     base = c4_problem(n)
     os.makedirs(args.sweep_out, exist_ok=True)
-    out = {"workload": f"cylinder {n}x{n // 2}, {base.n_particles} particles, {args.sweep} steps",
+    span = f"to t = {args.sweep_t_end!r}" if args.sweep_t_end > 0 else f"{args.sweep} steps"
+    out = {"workload": f"cylinder {n}x{n // 2}, {base.n_particles} particles, {span}",
            "dir": args.sweep_out, "modes": {}}
     for name, prec, unit in c4_modes(base):
         runs = []
@@ -331,14 +340,19 @@ def sweep(args):
             p = I.Problem("c4", cfg, base.x, base.v, base.mass, base.rho, base.e, base.mask, base.normals)
             g = M.Simulation.from_problem(p)
             t0 = time.perf_counter()
-            g.step(args.sweep)
+            if args.sweep_t_end > 0:
+                g.step(100 * args.sweep, t_end=args.sweep_t_end)
+            else:
+                g.step(args.sweep)
             sec = time.perf_counter() - t0
             ig = np.argsort(g.read("ID"))
             runs.append({f: g.read(f)[..., ig] for f in ("RHO", "P", "E", "V", "X")})
             clock = g.read("CLOCK")
             g.close()
         same = all(np.array_equal(runs[0][f], runs[1][f]) for f in runs[0])
-        np.savez(os.path.join(args.sweep_out, f"c4_{name}.npz"), clock=clock, **runs[0])
+        dt = np.float64 if prec == "fp64" else np.float32
+        np.savez(os.path.join(args.sweep_out, f"c4_{name}.npz"), clock=clock, sample=C4_SAMPLE,
+                 **{f: a[..., ::C4_SAMPLE].astype(dt) for f, a in runs[0].items()})
         out["modes"][name] = {"bit_reproducible": bool(same), "seconds": sec, "t": float(clock[0]),
                               "steps": int(clock[2])}
     return out
