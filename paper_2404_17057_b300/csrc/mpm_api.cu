@@ -227,8 +227,7 @@ template <class R>
 TileState<R> tstate(const mpm_sim* s, int b)
 {
     TileState<R> ts;
-    ts.pt[0] = parts<R>(s->buf[0]);
-    ts.pt[1] = parts<R>(s->buf[1]);
+    ts.pt = parts<R>(s->buf[0]);
     ts.cs[0] = s->cs[0];
     ts.cs[1] = s->cs[1];
     ts.tpar = s->tpar[b];
@@ -372,8 +371,8 @@ struct Impl {
     static ReorderArgs<R> rargs(const mpm_sim* s, int b)
     {
         ReorderArgs<R> a;
-        a.pt[0] = parts<R>(s->buf[0]);
-        a.pt[1] = parts<R>(s->buf[1]);
+        a.pt = parts<R>(s->buf[0]);
+        a.nslots = (uint32_t)s->nslots;
         a.cs[0] = s->cs[0];
         a.cs[1] = s->cs[1];
         a.tpar_old = s->tpar[b];
@@ -420,13 +419,13 @@ struct Impl {
         BatchProb<R, A> d;
         memset(&d, 0, sizeof d);
         d.G = s->G;
-        d.pt[0] = parts<R>(s->buf[0]);
-        d.pt[1] = parts<R>(s->buf[1]);
+        d.pt = parts<R>(s->buf[0]);
         d.gr = grid_view<A, R>(s);
         if constexpr (kFast) {
             d.p2g_out = p2g_fields(d.gr);
             d.g2p_out = g2p_fields(d.gr);
         }
+        d.nslots = (uint32_t)s->nslots;
         d.cs[0] = s->cs[0];
         d.cs[1] = s->cs[1];
         d.tpar[0] = s->tpar[0];
@@ -550,16 +549,13 @@ struct Impl {
     {
         const TileState<R> ts = tstate<R>(s, s->cur);
         const unsigned nb = std::max(1u, std::min(nblk(s->np), (unsigned)s->sms * 16u));
-        const Particles<R>& p0 = ts.pt[0];
-        const Particles<R>& p1 = ts.pt[1];
+        const Particles<R>& p = ts.pt;
         if (f <= 5) {
-            const R* a0 = f == 0 ? p0.x[a] : f == 1 ? p0.v[a] : f == 2 ? p0.M : f == 3 ? p0.rho : f == 4 ? p0.E : p0.Q;
-            const R* a1 = f == 0 ? p1.x[a] : f == 1 ? p1.v[a] : f == 2 ? p1.M : f == 3 ? p1.rho : f == 4 ? p1.E : p1.Q;
-            k_compact<R, R><<<nb, kThreads, 0, st>>>(s->G, ts, s->toff, a0, a1, (R*)out, s->np);
+            const R* src = f == 0 ? p.x[a] : f == 1 ? p.v[a] : f == 2 ? p.M : f == 3 ? p.rho : f == 4 ? p.E : p.Q;
+            k_compact<R, R><<<nb, kThreads, 0, st>>>(s->G, ts, s->toff, src, (R*)out, s->np);
         } else {
-            const uint32_t* a0 = f == 6 ? p0.id : p0.gen;
-            const uint32_t* a1 = f == 6 ? p1.id : p1.gen;
-            k_compact<uint32_t, R><<<nb, kThreads, 0, st>>>(s->G, ts, s->toff, a0, a1, (uint32_t*)out, s->np);
+            k_compact<uint32_t, R><<<nb, kThreads, 0, st>>>(s->G, ts, s->toff, f == 6 ? p.id : p.gen, (uint32_t*)out,
+                                                            s->np);
         }
         s->launches += 1;
     }
@@ -574,7 +570,7 @@ struct Impl {
     {
         const unsigned nb = (unsigned)std::min<int64_t>(s->G.ntiles, (int64_t)s->sms * 8);
         k_spread<D, R><<<nb, kThreads, 0, st>>>(s->G, parts<R>(s->buf[1]), parts<R>(s->buf[0]), cc, s->tbase,
-                                                s->cs[0]);
+                                                s->cs[0]);   // compact order at the start of buffer 1 -> regions of 0
         s->launches += 1;
     }
 };
@@ -695,36 +691,43 @@ mpm_status make_geom(const mpm_config* c, Geom* G, std::string* why)
     return MPM_OK;
 }
 
+// Two buffers of n slots per field, in one array of 2 n (buffer 1 from slot
+// n), so that absolute slots address either buffer.
 mpm_status alloc_particles(mpm_sim* s, int64_t n, Buffers nb[2])
 {
     const int d = s->G.dim;
     const size_t rb = (size_t)n * s->rsize, ub = (size_t)n * 4;
-    for (int b = 0; b < 2; ++b) {
-        for (int a = 0; a < d; ++a) {
-            nb[b].x[a] = dalloc(s, rb);
-            nb[b].v[a] = dalloc(s, rb);
-            if (!nb[b].x[a] || !nb[b].v[a]) return MPM_ENOMEM;
-        }
-        nb[b].M = dalloc(s, rb);
-        nb[b].rho = dalloc(s, rb);
-        nb[b].E = dalloc(s, rb);
-        nb[b].Q = dalloc(s, rb);
-        nb[b].id = (uint32_t*)dalloc(s, ub);
-        nb[b].key = (uint32_t*)dalloc(s, ub);
-        nb[b].gen = (uint32_t*)dalloc(s, ub);
-        if (!nb[b].M || !nb[b].rho || !nb[b].E || !nb[b].Q || !nb[b].id || !nb[b].key || !nb[b].gen) return MPM_ENOMEM;
+    auto two = [&](void*& p0, void*& p1, size_t bytes) {
+        p0 = dalloc(s, 2 * bytes);
+        p1 = p0 ? (void*)((char*)p0 + bytes) : nullptr;
+        return p0 != nullptr;
+    };
+    bool ok = true;
+    for (int a = 0; a < d; ++a) {
+        ok = ok && two(nb[0].x[a], nb[1].x[a], rb);
+        ok = ok && two(nb[0].v[a], nb[1].v[a], rb);
     }
-    return MPM_OK;
+    ok = ok && two(nb[0].M, nb[1].M, rb) && two(nb[0].rho, nb[1].rho, rb) && two(nb[0].E, nb[1].E, rb) &&
+         two(nb[0].Q, nb[1].Q, rb);
+    void *i0 = nullptr, *i1 = nullptr, *k0 = nullptr, *k1 = nullptr, *g0 = nullptr, *g1 = nullptr;
+    ok = ok && two(i0, i1, ub) && two(k0, k1, ub) && two(g0, g1, ub);
+    nb[0].id = (uint32_t*)i0;
+    nb[1].id = (uint32_t*)i1;
+    nb[0].key = (uint32_t*)k0;
+    nb[1].key = (uint32_t*)k1;
+    nb[0].gen = (uint32_t*)g0;
+    nb[1].gen = (uint32_t*)g1;
+    return ok ? MPM_OK : MPM_ENOMEM;
 }
 
+// Buffer 1 lives inside buffer 0's allocations.
 void free_particles(mpm_sim* s, Buffers b[2])
 {
-    for (int k = 0; k < 2; ++k) {
-        for (int a = 0; a < 3; ++a) { dfree(s, b[k].x[a]); dfree(s, b[k].v[a]); }
-        dfree(s, b[k].M); dfree(s, b[k].rho); dfree(s, b[k].E); dfree(s, b[k].Q);
-        dfree(s, b[k].id); dfree(s, b[k].key); dfree(s, b[k].gen);
-        b[k] = Buffers();
-    }
+    for (int a = 0; a < 3; ++a) { dfree(s, b[0].x[a]); dfree(s, b[0].v[a]); }
+    dfree(s, b[0].M); dfree(s, b[0].rho); dfree(s, b[0].E); dfree(s, b[0].Q);
+    dfree(s, b[0].id); dfree(s, b[0].key); dfree(s, b[0].gen);
+    b[0] = Buffers();
+    b[1] = Buffers();
 }
 
 void drop_graphs(mpm_sim* s)
@@ -1033,8 +1036,8 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
     const int64_t np = s->np + n;
     // every tile's region holds region_slots(its count) <= 2 count + 95
     // slots, now and after any relayout: buffers of 2 np + 95 ntiles slots
-    const int64_t nslots = 2 * np + 95 * (int64_t)G.ntiles;
-    if (nslots > (int64_t)0x7FFFFFFF) return fail(s, MPM_EINVAL, "too many particles");
+    const int64_t nslots = (2 * np + 95 * (int64_t)G.ntiles + 31) & ~(int64_t)31;
+    if (2 * nslots > (int64_t)0xFFFFFFFF) return fail(s, MPM_EINVAL, "too many particles");
     Buffers nb[2];
     mpm_status st = alloc_particles(s, nslots, nb);
     if (st != MPM_OK) { free_particles(s, nb); return fail(s, st, "device allocation failed"); }

@@ -38,7 +38,8 @@ struct BatchCommon {
 template <class R, class A>
 struct BatchProb {
     Geom G;
-    Particles<R> pt[2];
+    Particles<R> pt;                // both buffers (absolute slots)
+    uint32_t nslots;
     Grid<A, R> gr;
     FieldPtrs p2g_out, g2p_out;     // single-precision kernels: grid fields they add into
     uint32_t* cs[2];
@@ -122,13 +123,13 @@ __global__ void __launch_bounds__(kScanThreads) kb_step_end(const BatchCommon* _
     load_shared(p, bp[r.prob]);                  \
     __syncthreads();                             \
     const int par = p.clk->par;                  \
-    const int tp = p.tpar[par][r.tile];
+    const uint32_t* csp = p.cs[p.tpar[par][r.tile]];
 
 template <int D, int P, class R, class A>
 __global__ void __launch_bounds__(256) kb_p2g(const BatchProb<R, A>* __restrict__ bp, const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    p2g_tile<D, P, R, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, r.tile);
+    p2g_tile<D, P, R, A>(p.G, p.pt, p.gr, csp, p.clk, r.tile);
 }
 
 template <int D, int P, class R, class A>
@@ -136,14 +137,14 @@ __global__ void __launch_bounds__(256) kb_grid_g2p(const BatchProb<R, A>* __rest
                                                    const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    grid_g2p_tile<D, P, R, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, r.tile);
+    grid_g2p_tile<D, P, R, A>(p.G, p.pt, p.gr, csp, p.clk, r.tile);
 }
 
 template <int D, int P, class R, class A>
 __global__ void __launch_bounds__(256) kb_g2pd(const BatchProb<R, A>* __restrict__ bp, const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    g2pd_tile<D, P, R, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, p.ro, r.tile, tp);
+    g2pd_tile<D, P, R, A>(p.G, p.pt, p.gr, csp, p.clk, p.ro, r.tile);
 }
 
 template <int D, int P, bool PER>
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(kP2GThreads, 6) kb_p2g_span(const BatchProb<fl
                                                               const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(float, float)
-    p2g_span_tile<D, P, PER>(p.G, p.pt[tp], p.p2g_out, p.cs[tp], p.clk, r.tile);
+    p2g_span_tile<D, P, PER>(p.G, p.pt, p.p2g_out, csp, p.clk, r.tile);
 }
 
 template <int P, class R, class A>
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kP2GSpan2dThreads, 6) kb_p2g_span2d(const Batc
                                                                       const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    p2g_span2d_tile<P, R, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, r.tile);
+    p2g_span2d_tile<P, R, A>(p.G, p.pt, p.gr, csp, p.clk, r.tile);
 }
 
 template <int P, class R, class A>
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(kG2PSpan2dThreads, 4)
     kb_grid_g2p_span2d(const BatchProb<R, A>* __restrict__ bp, const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    grid_g2p_span2d_tile<P, R, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, r.tile);
+    grid_g2p_span2d_tile<P, R, A>(p.G, p.pt, p.gr, csp, p.clk, r.tile);
 }
 
 template <int D, int P, bool PER>
@@ -175,23 +176,23 @@ __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 3)
     kb_grid_g2p_span(const BatchProb<float, float>* __restrict__ bp, const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(float, float)
-    grid_g2p_span_tile<D, P, PER>(p.G, p.pt[tp], p.gr, p.g2p_out, p.cs[tp], p.clk, r.tile);
+    grid_g2p_span_tile<D, P, PER>(p.G, p.pt, p.gr, p.g2p_out, csp, p.clk, r.tile);
 }
 
 template <int D, int P, class A>
-__global__ void __launch_bounds__(kG2PDThreads, kG2PDBlocks) kb_g2pd_fast(const BatchProb<float, A>* __restrict__ bp,
+__global__ void __launch_bounds__(kG2PDThreads, g2pd_blocks<D>()) kb_g2pd_fast(const BatchProb<float, A>* __restrict__ bp,
                                                              const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(float, A)
-    g2pd_fast_tile<D, P, A>(p.G, p.pt[tp], p.gr, p.cs[tp], p.clk, p.ro, r.tile, tp);
+    g2pd_fast_tile<D, P, A>(p.G, p.pt, p.gr, csp, p.clk, p.ro, r.tile);
 }
 
 // The re-order arguments of member p at step parity par.
 template <class R, class A>
 __device__ __forceinline__ void batch_reorder_args(const BatchProb<R, A>& p, int par, ReorderArgs<R>& a)
 {
-    a.pt[0] = p.pt[0];
-    a.pt[1] = p.pt[1];
+    a.pt = p.pt;
+    a.nslots = p.nslots;
     a.cs[0] = p.cs[0];
     a.cs[1] = p.cs[1];
     a.tpar_old = p.tpar[par];
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kReorderThreads, 3) kb_reorder(const BatchProb
                                                                  const TileRef* __restrict__ tl, int mode)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    (void)tp;
+    (void)csp;
     __shared__ ReorderArgs<R> a;
     if (threadIdx.x == 0) batch_reorder_args(p, par, a);
     __syncthreads();
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kReorderThreads) kb_consolidate(const BatchPro
                                                                   const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(R, A)
-    (void)tp;
+    (void)csp;
     if (!p.clk->overflow) return;
     __shared__ ReorderArgs<R> a;
     if (threadIdx.x == 0) batch_reorder_args(p, par, a);

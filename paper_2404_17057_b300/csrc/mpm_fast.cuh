@@ -390,10 +390,7 @@ __global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, TileState<f
                                                               const uint32_t* __restrict__ tiles)
 {
     const int t = tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x;
-    // one inlined copy per buffer, so that the buffer's pointers stay
-    // constant-bank operands
-    if (ts.tpar[t]) p2g_span_tile<D, P, PER>(G, ts.pt[1], out, ts.cs[1], clk, t);
-    else p2g_span_tile<D, P, PER>(G, ts.pt[0], out, ts.cs[0], clk, t);
+    p2g_span_tile<D, P, PER>(G, ts.pt, out, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
 }
 
 // ------------------------------- 2D span-per-lane kernels, 64-bit sums
@@ -560,8 +557,7 @@ __global__ void __launch_bounds__(kP2GSpan2dThreads, 8) k_p2g_span2d(Geom G, Til
                                                                      Clock* clk)
 {
     const int t = blockIdx.x;
-    if (ts.tpar[t]) p2g_span2d_tile<P, R, A>(G, ts.pt[1], gr, ts.cs[1], clk, t);
-    else p2g_span2d_tile<P, R, A>(G, ts.pt[0], gr, ts.cs[0], clk, t);
+    p2g_span2d_tile<P, R, A>(G, ts.pt, gr, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
 }
 
 // Grid update + G2P + P2G: the acceleration window is built as in the
@@ -690,8 +686,7 @@ __global__ void __launch_bounds__(kG2PSpan2dThreads, 4) k_grid_g2p_span2d(Geom G
                                                                           Clock* clk)
 {
     const int t = blockIdx.x;
-    if (ts.tpar[t]) grid_g2p_span2d_tile<P, R, A>(G, ts.pt[1], gr, ts.cs[1], clk, t);
-    else grid_g2p_span2d_tile<P, R, A>(G, ts.pt[0], gr, ts.cs[0], clk, t);
+    grid_g2p_span2d_tile<P, R, A>(G, ts.pt, gr, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
 }
 
 // ----------------------------------------- K2: grid update + G2P + P2G
@@ -955,22 +950,23 @@ __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 4) k_grid_g2p_span(Geom G,
                                                                          const uint32_t* __restrict__ tiles)
 {
     const int t = tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x;
-    if (ts.tpar[t]) grid_g2p_span_tile<D, P, PER>(G, ts.pt[1], gr, out, ts.cs[1], clk, t);
-    else grid_g2p_span_tile<D, P, PER>(G, ts.pt[0], gr, out, ts.cs[0], clk, t);
+    grid_g2p_span_tile<D, P, PER>(G, ts.pt, gr, out, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
 }
 
 // ------------------------------- K3: G2PD + particle update + move + key
 
 constexpr int kG2PDThreads = 128;
-// five resident blocks: 96 registers a thread (128 without the bound; the
-// extra warps hide more latency than the few spilled bytes cost)
-constexpr int kG2PDBlocks = 5;
+// resident blocks: in 3D four, 128 registers a thread (five blocks at 96
+// registers spill in the particle loop: 3.41 against 3.32 ms on the 256^3
+// blast); in 2D five (93 registers, no spills)
+template <int D>
+constexpr int g2pd_blocks() { return D == 3 ? 4 : 5; }
 
 // A: grid accumulator type (float, or int64 fixed point read back as float).
 template <int D, int P, class A>
 __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<float>& pt, const Grid<A, float>& gr,
                                                const uint32_t* __restrict__ cs, Clock* clk, const Reorder& ro,
-                                               const int tile, const int tp)
+                                               const int tile)
 {
     if (!clk->active) return;
     const uint32_t beg = cs[tile_cs0(G, tile)];
@@ -1054,6 +1050,9 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
         }
         if (!ok) { err |= ERR_TILE; continue; }
         const int base = (l[2] * W1 + l[1]) * W0 + l[0];
+        // the particle's old key (its span in this tile)
+        const uint32_t okey = ((uint32_t)tile << (G.tsh[0] + G.tsh[1] + G.tsh[2])) |
+                              (uint32_t)((((l[2] << G.tsh[1]) + l[1]) << G.tsh[0]) | l[0]);
         // Vbar = G2P(mv'/m); div V = trace of G2PD(mv2/m), summed x first,
         // then y, then z, two sums per packed FMA
         const float2* sn2 = reinterpret_cast<const float2*>(sn + W);
@@ -1192,11 +1191,8 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
         }
 #pragma unroll
         for (int a = 0; a < D; ++a) pt.x[a][k] = xn[a];
-        int old[3] = {0, 0, 0};
-#pragma unroll
-        for (int a = 0; a < D; ++a) old[a] = so[a] + l[a];
-        pt.key[k] = record_key(G, ro, clk, key_of<float>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, tile, old,
-                               err, tp);
+        pt.key[k] = record_key(G, ro, clk, key_of<float>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, tile, okey,
+                               err);
         pt.E[k] = En_s;
         pt.rho[k] = rn_s;
         pt.Q[k] = Qn_s;
@@ -1215,12 +1211,11 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
 }
 
 template <int D, int P, class A>
-__global__ void __launch_bounds__(kG2PDThreads, kG2PDBlocks) k_g2pd_fast(Geom G, TileState<float> ts,
+__global__ void __launch_bounds__(kG2PDThreads, g2pd_blocks<D>()) k_g2pd_fast(Geom G, TileState<float> ts,
                                                                          Grid<A, float> gr, Clock* clk, Reorder ro)
 {
     const int t = blockIdx.x;
-    if (ts.tpar[t]) g2pd_fast_tile<D, P, A>(G, ts.pt[1], gr, ts.cs[1], clk, ro, t, 1);
-    else g2pd_fast_tile<D, P, A>(G, ts.pt[0], gr, ts.cs[0], clk, ro, t, 0);
+    g2pd_fast_tile<D, P, A>(G, ts.pt, gr, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, ro, t);
 }
 
 }  // namespace mpm

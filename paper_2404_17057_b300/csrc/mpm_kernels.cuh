@@ -25,7 +25,7 @@ constexpr uint32_t kFarFlag = 0x80000000u;   // key bit of a particle recycled t
 // Per-step re-order bookkeeping written by the G2PD step.
 struct Reorder {
     uint32_t* count;               // per span: particles gained minus lost in the step (mod 2^32)
-    uint2* far;                    // particles recycled this step: {new key, old slot | buffer << 31}
+    uint2* far;                    // particles recycled this step: {new key, old slot}
     uint32_t far_cap;              // entries of far (0: the problem has no inflow face)
     int mwords;                    // words of ring bits per tile
     unsigned long long* ring;      // per tile: parts of its one-span ring that particles entered from
@@ -64,6 +64,9 @@ struct Clock {
 // first n_t slots of its region in buffer tpar[t], span after span, and its
 // cell starts are the Tvol + 1 entries tile_cs0(t) .. tile_cs0(t) + Tvol of
 // cs[tpar[t]] (the start of each span and the end of the tile's particles).
+// The two buffers of a field are one array of 2 nslots slots (buffer b from
+// slot b nslots), and cell starts hold absolute slots: a kernel reaches a
+// tile's particles through the buffer-0 pointers whichever buffer they are in.
 __host__ __device__ inline int64_t tile_cs0(const Geom& G, int64_t t) { return t * (int64_t)(G.Tvol + 1); }
 // Entry of the cell-start table of the span with key `key`.
 __host__ __device__ inline int64_t cs_index(const Geom& G, uint32_t key)
@@ -122,36 +125,41 @@ __device__ __forceinline__ int ring_bit(const Geom& G, uint32_t t, const int old
     return 3 * (idx[2] * ny + idx[1]) + idx[0];
 }
 
-// New key of particle k (slot k of buffer tp).  A particle that changes span
-// moves one count from its old span to its new one (most particles keep their
-// span and cost nothing here) and marks the tile it leaves and the tile it
-// enters as changed; one that enters another tile marks the ring part it
-// comes from.  Recycled particles go to the far list (they may jump anywhere)
-// and carry the flag bit.
+__device__ __forceinline__ void tile_origin(const Geom& G, int tile, int so[3]);
+
+// New key of particle k (absolute slot k), whose old key was okey (a span
+// of `tile`).  A particle that changes span moves one count from its old span
+// to its new one (most particles keep their span and cost nothing here) and
+// marks the tile it leaves and the tile it enters as changed; one that enters
+// another tile marks the ring part it comes from.  Recycled particles go to
+// the far list (they may jump anywhere) and carry the flag bit.
 __device__ __forceinline__ uint32_t record_key(const Geom& G, const Reorder& ro, Clock* clk, uint32_t key,
-                                               bool recycled, uint32_t k, int tile, const int old[3], int& err,
-                                               int tp)
+                                               bool recycled, uint32_t k, int tile, uint32_t okey, int& err)
 {
     const int lsh = G.tsh[0] + G.tsh[1] + G.tsh[2];
     const uint32_t nt = key >> lsh;
-    const int lo[3] = {old[0] & (G.T[0] - 1), old[1] & (G.T[1] - 1), old[2] & (G.T[2] - 1)};
-    const uint32_t okey = ((uint32_t)tile << lsh) | (uint32_t)((((lo[2] << G.tsh[1]) + lo[1]) << G.tsh[0]) | lo[0]);
     if (recycled || key != okey) {
         atomicAdd(&ro.count[key], 1u);
         atomicSub(&ro.count[okey], 1u);
         ro.dirty[tile] = 1u;
         ro.dirty[nt] = 1u;
-    }
-    if (recycled) {
-        const unsigned slot = atomicAdd(&clk->nfar, 1u);
-        if (slot < ro.far_cap) ro.far[slot] = make_uint2(key, k | ((uint32_t)tp << 31));
-        else err |= ERR_TILE;
-        return key | kFarFlag;
-    }
-    // a particle that enters another tile: mark the ring part it comes from
-    if (nt != (uint32_t)tile) {
-        const int bit = ring_bit(G, nt, old);
-        if (bit >= 0) atomicOr(&ro.ring[(int64_t)nt * ro.mwords + (bit >> 6)], 1ull << (bit & 63));
+        if (recycled) {
+            const unsigned slot = atomicAdd(&clk->nfar, 1u);
+            if (slot < ro.far_cap) ro.far[slot] = make_uint2(key, k);
+            else err |= ERR_TILE;
+            return key | kFarFlag;
+        }
+        // a particle that enters another tile: mark the ring part it comes from
+        if (nt != (uint32_t)tile) {
+            const uint32_t l = okey & ((uint32_t)G.Tvol - 1u);
+            int old[3];
+            tile_origin(G, tile, old);
+            old[0] += (int)(l & (uint32_t)(G.T[0] - 1));
+            old[1] += (int)((l >> G.tsh[0]) & (uint32_t)(G.T[1] - 1));
+            old[2] += (int)(l >> (G.tsh[0] + G.tsh[1]));
+            const int bit = ring_bit(G, nt, old);
+            if (bit >= 0) atomicOr(&ro.ring[(int64_t)nt * ro.mwords + (bit >> 6)], 1ull << (bit & 63));
+        }
     }
     return key;
 }
@@ -172,7 +180,7 @@ struct Particles {
 // The particle state seen by the tile kernels.
 template <class R>
 struct TileState {
-    Particles<R> pt[2];
+    Particles<R> pt;               // both buffers (absolute slots)
     uint32_t* cs[2];
     const uint8_t* tpar;           // buffer of each tile
 };
@@ -574,8 +582,7 @@ template <int D, int P, class R, class A>
 __global__ void __launch_bounds__(256) k_p2g(Geom G, TileState<R> ts, Grid<A, R> gr, Clock* clk)
 {
     const int t = blockIdx.x;
-    if (ts.tpar[t]) p2g_tile<D, P, R, A>(G, ts.pt[1], gr, ts.cs[1], clk, t);
-    else p2g_tile<D, P, R, A>(G, ts.pt[0], gr, ts.cs[0], clk, t);
+    p2g_tile<D, P, R, A>(G, ts.pt, gr, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
 }
 
 // ----------------------------------------------- grid update + G2P + P2G
@@ -711,16 +718,14 @@ template <int D, int P, class R, class A>
 __global__ void __launch_bounds__(256) k_grid_g2p(Geom G, TileState<R> ts, Grid<A, R> gr, Clock* clk)
 {
     const int t = blockIdx.x;
-    if (ts.tpar[t]) grid_g2p_tile<D, P, R, A>(G, ts.pt[1], gr, ts.cs[1], clk, t);
-    else grid_g2p_tile<D, P, R, A>(G, ts.pt[0], gr, ts.cs[0], clk, t);
+    grid_g2p_tile<D, P, R, A>(G, ts.pt, gr, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
 }
 
 // ------------------------------------ G2PD + particle update + move + key
 
 template <int D, int P, class R, class A>
 __device__ __forceinline__ void g2pd_tile(const Geom& G, const Particles<R>& pt, const Grid<A, R>& gr,
-                                          const uint32_t* cellstart, Clock* clk, const Reorder& ro, const int tile,
-                                          const int tp)
+                                          const uint32_t* cellstart, Clock* clk, const Reorder& ro, const int tile)
 {
     typedef Op<R> O;
     if (!clk->active) return;
@@ -883,8 +888,8 @@ __device__ __forceinline__ void g2pd_tile(const Geom& G, const Particles<R>& pt,
         int old[3] = {0, 0, 0};
 #pragma unroll
         for (int a = 0; a < D; ++a) old[a] = wrap_span(G, a, sx[a].c);
-        pt.key[k] = record_key(G, ro, clk, key_of<R>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, tile, old, err,
-                               tp);
+        pt.key[k] = record_key(G, ro, clk, key_of<R>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, tile,
+                               key_of<R>(G, old), err);
         pt.E[k] = En_s;
         pt.rho[k] = rn_s;
         pt.Q[k] = Qn_s;
@@ -906,8 +911,7 @@ template <int D, int P, class R, class A>
 __global__ void __launch_bounds__(256) k_g2pd(Geom G, TileState<R> ts, Grid<A, R> gr, Clock* clk, Reorder ro)
 {
     const int t = blockIdx.x;
-    if (ts.tpar[t]) g2pd_tile<D, P, R, A>(G, ts.pt[1], gr, ts.cs[1], clk, ro, t, 1);
-    else g2pd_tile<D, P, R, A>(G, ts.pt[0], gr, ts.cs[0], clk, ro, t, 0);
+    g2pd_tile<D, P, R, A>(G, ts.pt, gr, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, ro, t);
 }
 
 // ---------------------------------------------------------- time control
@@ -971,32 +975,26 @@ __global__ void k_tile_counts(Geom G, TileState<R> ts, uint32_t* counts)
     }
 }
 
-// Buffer and slot of the particle at position j of the key order; toff[t] is
-// the number of particles in the tiles before t (ntiles + 1 entries).
+// Slot of the particle at position j of the key order; toff[t] is the number
+// of particles in the tiles before t (ntiles + 1 entries).
 template <class R>
-__device__ __forceinline__ int order_slot(const Geom& G, const TileState<R>& ts, const uint32_t* toff, int64_t j,
-                                          uint32_t& slot)
+__device__ __forceinline__ uint32_t order_slot(const Geom& G, const TileState<R>& ts, const uint32_t* toff, int64_t j)
 {
     int lo = 0, hi = G.ntiles - 1;      // the last tile whose first position is <= j
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if ((int64_t)toff[mid] <= j) lo = mid; else hi = mid - 1;
     }
-    const int tp = ts.tpar[lo];
-    slot = ts.cs[tp][tile_cs0(G, lo)] + (uint32_t)(j - (int64_t)toff[lo]);
-    return tp;
+    return ts.cs[ts.tpar[lo]][tile_cs0(G, lo)] + (uint32_t)(j - (int64_t)toff[lo]);
 }
 
-// out[j] = the field (a0 in buffer 0, a1 in buffer 1) of the particle at
-// position j of the key order.
+// out[j] = the field a (both buffers) of the particle at position j of the
+// key order.
 template <class T, class R>
-__global__ void k_compact(Geom G, TileState<R> ts, const uint32_t* toff, const T* a0, const T* a1, T* out, int64_t n)
+__global__ void k_compact(Geom G, TileState<R> ts, const uint32_t* toff, const T* a, T* out, int64_t n)
 {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t q;
-        const int tp = order_slot(G, ts, toff, j, q);
-        out[j] = tp ? a1[q] : a0[q];
-    }
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        out[j] = a[order_slot(G, ts, toff, j)];
 }
 
 // Initial CFL maxima over the particle state (Vbar := V before the first step).
@@ -1007,8 +1005,8 @@ __global__ void k_cfl_init(Geom G, TileState<R> ts, const uint32_t* toff, int64_
     R vmax = (R)0, cmax = (R)0;
     const R gm1 = (R)(G.gamma - 1.0), gam = (R)G.gamma;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t k;
-        const Particles<R>& pt = ts.pt[order_slot(G, ts, toff, j, k)];
+        const uint32_t k = order_slot(G, ts, toff, j);
+        const Particles<R>& pt = ts.pt;
         R v2 = (R)0;
 #pragma unroll
         for (int a = 0; a < D; ++a) v2 = O::add(v2, O::mul(pt.v[a][k], pt.v[a][k]));
@@ -1086,8 +1084,8 @@ __global__ void __launch_bounds__(256) k_cons_partial(Geom G, TileState<R> ts, c
     __shared__ double sh[5][256];
     double s[5] = {0, 0, 0, 0, 0};
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t k;
-        const Particles<R>& pt = ts.pt[order_slot(G, ts, toff, j, k)];
+        const uint32_t k = order_slot(G, ts, toff, j);
+        const Particles<R>& pt = ts.pt;
         double M = (double)pt.M[k], v2 = 0.0;
 #pragma unroll
         for (int a = 0; a < D; ++a) {

@@ -77,19 +77,17 @@ __device__ __forceinline__ void copy_particle(const Particles<R>& in, const Part
     if (with_gen) out.gen[j] = gen;
 }
 
-// Copy kB particles per lane, slot q[u] of buffer b[u] -> slot j[u] of out,
-// where ok[u]: all loads first, so that 12 kB independent loads per lane are
-// in flight.
+// Copy kB particles per lane, slot q[u] -> slot j[u], where ok[u]: all loads
+// first, so that 12 kB independent loads per lane are in flight.
 template <int kB, class R>
-__device__ __forceinline__ void copy_batch(const Particles<R>* in, const Particles<R>& out, int D, const uint32_t* q,
-                                           const int* b, const uint32_t* j, const bool* ok, bool with_gen)
+__device__ __forceinline__ void copy_batch(const Particles<R>& s, const Particles<R>& out, int D, const uint32_t* q,
+                                           const uint32_t* j, const bool* ok, bool with_gen)
 {
     R xv[kB][6], M[kB], rho[kB], E[kB], Q[kB];
     uint32_t id[kB], gen[kB];
 #pragma unroll
     for (int u = 0; u < kB; ++u) {
         if (!ok[u]) continue;
-        const Particles<R>& s = in[b[u]];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
             if (a < D) { xv[u][a] = s.x[a][q[u]]; xv[u][3 + a] = s.v[a][q[u]]; }
@@ -118,7 +116,8 @@ __device__ __forceinline__ void copy_batch(const Particles<R>* in, const Particl
 // What one re-order pass needs of a simulation.
 template <class R>
 struct ReorderArgs {
-    Particles<R> pt[2];
+    Particles<R> pt;                // both buffers (absolute slots; buffer 1 from nslots)
+    uint32_t nslots;
     uint32_t* cs[2];
     const uint8_t* tpar_old;        // buffer of each tile during the step
     uint8_t* tpar_new;              // ... after the re-order
@@ -141,14 +140,14 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
     uint32_t* base = cnt + kReorderWarps * Tvol;          // next slot of each span
     uint32_t* endv = base + Tvol;                         // end of each span's stayers
     uint32_t* news = endv + Tvol;                         // new start of each span
-    uint32_t* list_q = news + Tvol;                       // compacted slots (bit 31: buffer)
-    uint32_t* ustart = list_q + kReorderCap;              // ranges as listed (bit 31: buffer)
+    uint32_t* list_q = news + Tvol;                       // compacted slots
+    uint32_t* ustart = list_q + kReorderCap;              // ranges as listed
     uint32_t* ulen = ustart + nrmax;
     uint32_t* sstart = ulen + nrmax;                      // ranges by old slot
     uint32_t* soff = sstart + nrmax;                      // exclusive prefix of lengths (nrmax + 1)
     uint32_t* wsum = soff + nrmax + 1;                    // per-warp totals (+1 spare)
     uint16_t* list_k = reinterpret_cast<uint16_t*>(wsum + kReorderWarps + 1);
-    uint2* farl = reinterpret_cast<uint2*>(list_k + kReorderCap);   // {local span, slot | buffer}, by id
+    uint2* farl = reinterpret_cast<uint2*>(list_k + kReorderCap);   // {local span, slot}, by id
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t K0 = (int64_t)t * Tvol;
@@ -170,8 +169,8 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
     }
     const int dst = relayout ? 1 : 1 - tp;
     const uint32_t* rb = relayout ? A.tbase_next : A.tbase;
-    const uint32_t rbeg = rb[t], rcap = rb[t + 1] - rb[t];
-    const Particles<R>& out = A.pt[dst];
+    const uint32_t rbeg = (dst ? A.nslots : 0u) + rb[t], rcap = rb[t + 1] - rb[t];
+    const uint32_t NS = A.nslots;
     int err = 0;
 
     // new span counts (old counts plus the step's changes) -> new starts
@@ -218,7 +217,8 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
         if ((e.x >> lsh) != (uint32_t)t) continue;
         const uint32_t at = atomicAdd(&s_nfar, 1u);
         if (at < (uint32_t)kReorderFarCap) {
-            farl[at] = make_uint2(e.x & lmask, relayout ? (e.y & 0x7fffffffu) : e.y);
+            // (a relayout reads every old particle from buffer 0)
+            farl[at] = make_uint2(e.x & lmask, relayout && e.y >= NS ? e.y - NS : e.y);
             atomicAdd(&endv[e.x & lmask], 1u);      // recycled arrivals per span (for now)
         } else {
             err |= ERR_TILE;
@@ -255,15 +255,12 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
     for (int w = tid; w < kReorderMaxRanges / 64; w += kReorderThreads)
         rbits[w] = w < mwords ? A.ro.ring[(int64_t)t * mwords + w] : 0ull;
     __syncthreads();
-    // old slot range of the spans a0..a1 of one row (one tile), in the
-    // buffer that tile's particles are in
+    // old slot range of the spans a0..a1 of one row (one tile)
     auto range = [&](const int a0[3], const int a1[3], uint32_t& b, uint32_t& l) {
         const uint32_t k0 = key_of<float>(G, a0), k1 = key_of<float>(G, a1);
-        const int src = relayout ? 0 : A.tpar_old[k0 >> lsh];
-        const uint32_t* cso = A.cs[src];
+        const uint32_t* cso = A.cs[relayout ? 0 : A.tpar_old[k0 >> lsh]];
         b = cso[cs_index(G, k0)];
         l = cso[cs_index(G, k1) + 1] - b;
-        b |= (uint32_t)src << 31;
     };
     // 1. old slot ranges of the tile's rows and of the ring parts entered
     for (int row = tid; row < nrows; row += kReorderThreads) {
@@ -292,9 +289,8 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
         }
     }
     __syncthreads();
-    // the non-empty ranges, ordered by (buffer, slot) -- within one buffer by
-    // old position, which is the old key order (one warp: typically the
-    // tile's own rows and a few ring parts)
+    // the non-empty ranges in old key order (one warp: typically the tile's
+    // own rows and a few ring parts)
     __shared__ int nr_used;
     if (warp == 0) {
         const uint32_t lt = (1u << lane) - 1u;
@@ -311,17 +307,16 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
             k += __popc(m);
         }
         __syncwarp();
-        // non-empty ranges are disjoint: their (buffer, start) pairs differ.
-        // Old key order across buffers: regions are in tile order in both
-        // buffers, so ordering by the slot alone (buffer bit dropped) is the
-        // old key order.
+        // non-empty ranges are disjoint.  Regions lie in tile order at the
+        // same places of both buffers, so the slot within its buffer gives
+        // the old key order
         for (int i = lane; i < k; i += 32) {
             const uint32_t si = ustart[i];
-            const uint32_t sv = si & 0x7fffffffu;
+            const uint32_t sv = si >= NS ? si - NS : si;
             int rank = 0;
             for (int j = 0; j < k; ++j) {
-                const uint32_t vj = ustart[j] & 0x7fffffffu;
-                rank += (vj < sv || (vj == sv && ustart[j] < si)) ? 1 : 0;
+                const uint32_t vj = ustart[j] >= NS ? ustart[j] - NS : ustart[j];
+                rank += (vj < sv) ? 1 : 0;
             }
             sstart[rank] = si;
             soff[rank] = ulen[i];    // length for now; prefix below
@@ -373,10 +368,10 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
                 } else {
                     while (soff[r + 1] <= c) ++r;
                 }
-                const uint32_t qb = sstart[r] + (c - soff[r]);      // bit 31 carried from the range
-                const uint32_t k = A.pt[qb >> 31].key[qb & 0x7fffffffu];
+                const uint32_t q = sstart[r] + (c - soff[r]);
+                const uint32_t k = A.pt.key[q];
                 hit = (k >> lsh) == (uint32_t)t;
-                myq[i] = qb;
+                myq[i] = q;
                 mykl[i] = k & lmask;
             }
             bal[i] = __ballot_sync(0xffffffffu, hit);
@@ -432,7 +427,6 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
         constexpr int kB = sizeof(R) == 4 ? 4 : 2;     // particles per lane per batch
         for (uint32_t j0 = wb; j0 < we; j0 += 32 * kB) {
             uint32_t qv[kB], pv[kB];
-            int bv[kB];
             bool okv[kB];
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
@@ -447,15 +441,13 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
                 const uint32_t pos = b0 + __popc(peers & lt);
                 okv[u] = valid && pos < endv[kl];
                 if (valid && !okv[u]) err |= ERR_TILE;
-                const uint32_t qb = valid ? list_q[j] : 0u;
-                qv[u] = qb & 0x7fffffffu;
-                bv[u] = (int)(qb >> 31);
+                qv[u] = valid ? list_q[j] : 0u;
                 pv[u] = pos;
                 __syncwarp();
                 if (valid && lane == leader) wc[kl] = b0 + __popc(peers);
                 __syncwarp();
             }
-            copy_batch<kB>(A.pt, out, D, qv, bv, pv, okv, with_gen);
+            copy_batch<kB>(A.pt, A.pt, D, qv, pv, okv, with_gen);
         }
         __syncthreads();
         for (int k = tid; k < kReorderWarps * Tvol; k += kReorderThreads) cnt[k] = 0u;
@@ -469,11 +461,11 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
         if (tid == 0) {
             for (uint32_t i = 1; i < nfar; ++i) {
                 const uint2 v = farl[i];
-                const uint32_t vid = A.pt[v.y >> 31].id[v.y & 0x7fffffffu];
+                const uint32_t vid = A.pt.id[v.y];
                 uint32_t j = i;
                 while (j > 0) {
                     const uint2 u = farl[j - 1];
-                    const uint32_t uid = A.pt[u.y >> 31].id[u.y & 0x7fffffffu];
+                    const uint32_t uid = A.pt.id[u.y];
                     if (u.x < v.x || (u.x == v.x && uid < vid)) break;
                     farl[j] = u;
                     --j;
@@ -490,7 +482,7 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
             while (first > 0 && farl[first - 1].x == v.x) --first;
             const uint32_t pos = endv[v.x] + (i - first);
             if (pos < (v.x + 1 < (uint32_t)Tvol ? news[v.x + 1] : rbeg + total))
-                copy_particle(A.pt[v.y >> 31], out, D, v.y & 0x7fffffffu, pos, true);
+                copy_particle(A.pt, A.pt, D, v.y, pos, true);
             else
                 err |= ERR_TILE;
         }
@@ -526,12 +518,12 @@ __device__ __forceinline__ void consolidate_tile(const Geom& G, const ReorderArg
 {
     if (A.tpar_old[t] != 1) return;
     const int64_t C0 = tile_cs0(G, t);
-    const uint32_t b = A.cs[1][C0], e = A.cs[1][C0 + G.Tvol];
+    const uint32_t b = A.cs[1][C0], e = A.cs[1][C0 + G.Tvol], NS = A.nslots;
     for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-        copy_particle(A.pt[1], A.pt[0], D, j, j, true);
-        A.pt[0].key[j] = A.pt[1].key[j];
+        copy_particle(A.pt, A.pt, D, j, j - NS, true);
+        A.pt.key[j - NS] = A.pt.key[j];
     }
-    for (int k = threadIdx.x; k <= G.Tvol; k += blockDim.x) A.cs[0][C0 + k] = A.cs[1][C0 + k];
+    for (int k = threadIdx.x; k <= G.Tvol; k += blockDim.x) A.cs[0][C0 + k] = A.cs[1][C0 + k] - NS;
 }
 
 template <int D, class R>
