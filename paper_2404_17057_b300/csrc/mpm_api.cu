@@ -266,7 +266,7 @@ struct Impl {
         if (kernel == 2 && kFast3) return (D == 3 ? 24 : 16) * W;
         if (kFast) {
             if (kernel == 0) return (1 + 2 * D) * W * sizeof(float);
-            return (K2Cfg<D>::kHeadFloats + tile_cs_words(G)) * sizeof(float) + 16 * W + D * W * sizeof(float);
+            return (K2Cfg<D>::kHeadFloats + tile_cs_words(G)) * sizeof(float) + 2 * D * W * sizeof(float);
         }
         if (kernel == 0) return (1 + 2 * D) * W * sizeof(A);
         if (kernel == 1) return align16(D * W * sizeof(R)) + D * W * sizeof(A);
@@ -395,7 +395,7 @@ struct Impl {
         k_consolidate<D, R><<<nb, kReorderThreads, 0, st>>>(G, a);
         k_relayout_bases<<<1, 1024, 0, st>>>(s->tcount, G.ntiles, s->tbase_next, s->clk);
         k_reorder<D, R><<<nb, kReorderThreads, reorder_smem(G), st>>>(G, a, 1);
-        k_reorder_done<<<nblk(G.ntiles), kThreads, 0, st>>>(G, a.ro, s->clk, s->tbase, s->tbase_next);
+        k_reorder_done<<<nblk(G.ntiles * 32), kThreads, 0, st>>>(G, a.ro, s->clk, s->tbase, s->tbase_next);
         s->launches += 5;
     }
     static FieldPtrs p2g_fields(const Grid<A, R>& gr)

@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(kScanThreads) kb_step_end(const BatchCommon* _
     const BatchCommon& d = c[r.prob];
     const int64_t b = (int64_t)r.tile * kScanTile;
     const Reorder ro = {d.count, nullptr, 0u, d.mwords, d.ring, d.dirty};
-    for (int64_t t = b + threadIdx.x; t < min(b + (int64_t)kScanTile, (int64_t)d.ntiles); t += blockDim.x)
-        reorder_done_tile(d.tvol, ro, d.clk, d.tbase, d.tbase_next, (int)t, d.ntiles);
+    for (int64_t t = b + (threadIdx.x >> 5); t < min(b + (int64_t)kScanTile, (int64_t)d.ntiles); t += blockDim.x >> 5)
+        reorder_done_tile(d.tvol, ro, d.clk, d.tbase, d.tbase_next, (int)t, d.ntiles, threadIdx.x & 31);
 }
 
 // ------------------------------------------------------------ per tile
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kG2PSpan2dThreads, 4)
 }
 
 template <int D, int P, bool PER>
-__global__ void __launch_bounds__(K2Cfg<D>::kThreads, 3)
+__global__ void __launch_bounds__(K2Cfg<D>::kThreads, 5)
     kb_grid_g2p_span(const BatchProb<float, float>* __restrict__ bp, const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(float, float)

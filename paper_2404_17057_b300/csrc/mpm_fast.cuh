@@ -194,6 +194,171 @@ __device__ __forceinline__ void flush_window(const Geom& G, const int so[3], con
 // sums go in with plain shared-memory adds.
 constexpr int kP2GThreads = 64;
 
+// 3D span columns: a lane walks the spans of one (x, y) column along z (rows
+// of 32 spans are z-major in a tile).  Its sums hold the three node layers of
+// the current span; after each span the lowest layer is complete, goes into
+// the window, and the two others move down.  GROUP 0 sums {m, mv_x, mv_y,
+// mv_z}, GROUP 1 {f_x, f_y, f_z}.
+template <int P, bool PER, int GROUP>
+__device__ __forceinline__ void p2g_zcol(const Geom& G, const Particles<float>& pt, const uint32_t* __restrict__ cs,
+                                         int64_t kb, const int so[3], const float lo[3], const float nper[3],
+                                         float ih, float gm1, float* sm, int lane)
+{
+    constexpr int NS = P + 1, NYZ = NS * NS, NN = NYZ * NS, L = NS * NS;
+    const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
+    const int tseg = G.T[0] < 32 ? G.T[0] : 32;
+    const int lxw = lane & (tseg - 1);
+    const int rpl = (G.T[0] * G.T[1]) >> 5;
+    for (int yb = 0; yb < rpl; ++yb) {
+        // GROUP 0: qa = {m, mv_x}, qb = {mv_y, mv_z}; GROUP 1: qa = {f_y, f_z}, qc = f_x
+        float2 qa[NN], qb[GROUP == 0 ? NN : 1];
+        float qc[GROUP == 0 ? 1 : NN];
+#pragma unroll
+        for (int i = 0; i < NN; ++i) {
+            qa[i] = f2(0.f, 0.f);
+            if (GROUP == 0) qb[i] = f2(0.f, 0.f); else qc[i] = 0.f;
+        }
+        for (int z = 0; z < G.T[2]; ++z) {
+            const int s = ((z * rpl + yb) << 5) + lane;
+            const uint32_t b = cs[kb + s], e = cs[kb + s + 1];
+            const int lx = s & (G.T[0] - 1);
+            const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
+            const int base = (z * W1 + ly) * W0 + lx;
+            const float cb0 = (float)(so[0] + lx - (P == 2 ? 1 : 0));
+            const float cb1 = (float)(so[1] + ly - (P == 2 ? 1 : 0));
+            const float cb2 = (float)(so[2] + z - (P == 2 ? 1 : 0));
+            if (GROUP == 0) {
+                float nx[3] = {0.f, 0.f, 0.f}, nv[3] = {0.f, 0.f, 0.f}, nM = 0.f;
+                if (b < e) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) { nx[a] = pt.x[a][b]; nv[a] = pt.v[a][b]; }
+                    nM = pt.M[b];
+                }
+                for (uint32_t k = b; k < e; ++k) {
+                    float x[3], v[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) { x[a] = nx[a]; v[a] = nv[a]; }
+                    const float M = nM;
+                    if (k + 1 < e) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) { nx[a] = pt.x[a][k + 1]; nv[a] = pt.v[a][k + 1]; }
+                        nM = pt.M[k + 1];
+                    }
+                    float w[3][3], dw[3][3];
+                    axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
+                    axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+                    axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
+                    float2 c0[NS], c1[NS];
+                    const float mv0 = M * v[0], mv1 = M * v[1], mv2 = M * v[2];
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) {
+                        const float wa = w[0][a];
+                        c0[a] = f2(M * wa, mv0 * wa);
+                        c1[a] = f2(mv1 * wa, mv2 * wa);
+                    }
+#pragma unroll
+                    for (int j = 0; j < NYZ; ++j) {
+                        const float yz = w[1][j % NS] * w[2][j / NS];
+                        const float2 yy = f2(yz, yz);
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) {
+                            const int i = j * NS + a;
+                            qa[i] = __ffma2_rn(c0[a], yy, qa[i]);
+                            if (GROUP == 0) qb[i] = __ffma2_rn(c1[a], yy, qb[i]);
+                        }
+                    }
+                }
+            } else {
+                float nx[3] = {0.f, 0.f, 0.f}, nM = 0.f, nr = 1.f, nE = 0.f, nQ = 0.f;
+                if (b < e) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) nx[a] = pt.x[a][b];
+                    nM = pt.M[b]; nr = pt.rho[b]; nE = pt.E[b]; nQ = pt.Q[b];
+                }
+                for (uint32_t k = b; k < e; ++k) {
+                    float x[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) x[a] = nx[a];
+                    const float M = nM, rho = nr, E = nE, Q = nQ;
+                    if (k + 1 < e) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) nx[a] = pt.x[a][k + 1];
+                        nM = pt.M[k + 1]; nr = pt.rho[k + 1]; nE = pt.E[k + 1]; nQ = pt.Q[k + 1];
+                    }
+                    float w[3][3], dw[3][3];
+                    axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
+                    axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+                    axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
+                    const float F = fmaf(gm1 * rho, E, Q) * __fdividef(M, rho) * ih;
+                    float Fx[NS], Fd[NS];
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) { Fx[a] = F * w[0][a]; Fd[a] = F * dw[0][a]; }
+#pragma unroll
+                    for (int j = 0; j < NYZ; ++j) {
+                        const int bb = j % NS, c = j / NS;
+                        const float yz = w[1][bb] * w[2][c];
+                        const float2 dd = f2(dw[1][bb] * w[2][c], w[1][bb] * dw[2][c]);
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) {
+                            const int i = j * NS + a;
+                            qa[i] = __ffma2_rn(f2(Fx[a], Fx[a]), dd, qa[i]);
+                            if (GROUP == 1) qc[i] = fmaf(Fd[a], yz, qc[i]);
+                        }
+                    }
+                }
+            }
+            // the completed node layers: the lowest, or all three after the
+            // column's last span
+            const bool last = z + 1 == G.T[2];
+#pragma unroll
+            for (int c = 0; c < NS; ++c) {
+                if (c > 0 && !last) break;
+#pragma unroll
+                for (int bb = 0; bb < NS; ++bb) {
+                    const int j = c * NS + bb;
+                    const int row = base - lxw + (c * W1 + bb) * W0;
+                    float v[NS];
+                    if (GROUP == 0) {
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) v[a] = qa[j * NS + a].x;
+                        xrow_rmw<NS>(sm + row, v, lxw, tseg);
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) v[a] = qa[j * NS + a].y;
+                        xrow_rmw<NS>(sm + W + row, v, lxw, tseg);
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) v[a] = qb[j * NS + a].x;
+                        xrow_rmw<NS>(sm + 2 * W + row, v, lxw, tseg);
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) v[a] = qb[j * NS + a].y;
+                        xrow_rmw<NS>(sm + 3 * W + row, v, lxw, tseg);
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) v[a] = qc[j * NS + a];
+                        xrow_rmw<NS>(sm + 4 * W + row, v, lxw, tseg);     // f_x
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) v[a] = qa[j * NS + a].x;
+                        xrow_rmw<NS>(sm + 5 * W + row, v, lxw, tseg);     // f_y
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) v[a] = qa[j * NS + a].y;
+                        xrow_rmw<NS>(sm + 6 * W + row, v, lxw, tseg);     // f_z
+                    }
+                }
+            }
+            if (last) break;
+#pragma unroll
+            for (int i = 0; i < NN; ++i) {
+                if (i + L < NN) {
+                    qa[i] = qa[i + L];
+                    if (GROUP == 0) qb[i] = qb[i + L]; else qc[i] = qc[i + L];
+                } else {
+                    qa[i] = f2(0.f, 0.f);
+                    if (GROUP == 0) qb[i] = f2(0.f, 0.f); else qc[i] = 0.f;
+                }
+            }
+        }
+    }
+}
+
 template <int D, int P, bool PER>
 __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<float>& pt, const FieldPtrs& out,
                                               const uint32_t* __restrict__ cs, Clock* clk, const int tile)
@@ -217,6 +382,13 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int group = warp & 1;
+    if constexpr (D == 3) {
+        if (group == 0) p2g_zcol<P, PER, 0>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
+        else p2g_zcol<P, PER, 1>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
+        __syncthreads();
+        flush_window<D, P>(G, so, sm, NF, out);
+        return;
+    }
     const int nrows = G.Tvol >> 5;
     for (int r = 0; r < nrows; ++r) {
         const int s = (r << 5) + lane;
@@ -691,23 +863,24 @@ __global__ void __launch_bounds__(kG2PSpan2dThreads, 4) k_grid_g2p_span2d(Geom G
 
 // ----------------------------------------- K2: grid update + G2P + P2G
 //
-// The tile's particles are staged row chunk by row chunk (32 spans, at most
-// kCap particles) into shared memory by bulk copies, double-buffered.  Per
-// chunk, phase (i): one thread per particle gathers A = G2P(f/m) from the
-// window (lanes of a warp mostly share a span, so node records are
-// broadcast), forms V' = V + dt A, stores it (coalesced) and into the stage;
-// phase (ii): warp d (d < dim) owns the momentum field mv2_d: its lanes own
-// the row's spans, sum M V'_d phi over their particles in registers and add
-// the row's sums into the window with plain shared-memory adds.
+// One warp per velocity component d.  The tile's particles are staged row
+// chunk by row chunk (32 spans, at most kCap particles) into shared memory by
+// bulk copies, kStages deep.  A lane owns one span of the row and keeps the
+// values of f_d/m (after the grid BC) at the span's (p+1)^d support nodes in
+// registers; for each of its particles it gathers A_d = G2P(f_d/m), forms
+// V'_d = V_d + dt A_d, writes it back into the stage and sums M V'_d phi into
+// registers.  A completed row's sums go into the warp's own window of mv2_d
+// with plain shared-memory adds.  After each chunk the block copies the
+// chunk's V' to global memory (coalesced) and takes the largest |V'|.
 template <int D>
 struct K2Cfg {
-    static constexpr int kThreads = 128;
+    static constexpr int kThreads = 32 * D;
     static constexpr int kFields = 2 * D + 1;      // x[D], v[D], M
     static constexpr int kCap = 256;               // particles per chunk
     static constexpr int kPitch = kCap + 8;        // staged floats per field (16-byte multiple)
-    static constexpr int kStageFloats = 2 * kFields * kPitch;
-    static constexpr int kWeightFloats = 3 * D * kPitch;    // 1D weights of the chunk's particles
-    static constexpr int kHeadFloats = kStageFloats + kWeightFloats + 4;   // + two mbarriers
+    static constexpr int kStages = 2;
+    static constexpr int kStageFloats = kStages * kFields * kPitch;
+    static constexpr int kHeadFloats = kStageFloats + 8;   // + the stages' mbarriers (32 bytes)
 };
 
 // Tile cell starts kept in shared memory (Tvol + 1 words, rounded to 4).
@@ -764,11 +937,10 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
     constexpr int NS = P + 1, NYZ = (D == 3) ? NS * NS : NS, NN = NYZ * NS;
     const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
     float* stage = sm;
-    float* sw = sm + C::kStageFloats;          // [axis][node][particle] weights of the current chunk
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + C::kStageFloats + C::kWeightFloats);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + C::kStageFloats);
     uint32_t* tcs = reinterpret_cast<uint32_t*>(sm + C::kHeadFloats);
-    float4* sA = reinterpret_cast<float4*>(sm + C::kHeadFloats + tile_cs_words(G));   // W records: f/m after BC
-    float* s2 = reinterpret_cast<float*>(sA + W);                                       // D x W: momentum P2G
+    float* sA = sm + C::kHeadFloats + tile_cs_words(G);     // D x W: f/m after BC
+    float* s2 = sA + D * W;                                  // D x W: momentum P2G
     int so[3];
     tile_origin(G, tile, so);
     const float dt = (float)clk->dt_cur;
@@ -783,168 +955,161 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
             node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
         }
         const float im = m != 0.f ? __frcp_rn(m) : 0.f;
-        sA[i] = make_float4(f[0] * im, f[1] * im, D == 3 ? f[2] * im : 0.f, 0.f);
 #pragma unroll
-        for (int a = 0; a < D; ++a) s2[a * W + i] = 0.f;
+        for (int a = 0; a < D; ++a) {
+            sA[a * W + i] = f[a] * im;
+            s2[a * W + i] = 0.f;
+        }
     }
     for (int i = threadIdx.x; i <= G.Tvol; i += blockDim.x) tcs[i] = cs[kb + i];
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
+#pragma unroll
+        for (int q = 0; q < C::kStages; ++q) mbar_init(bar + q, 1);
         mbar_init_fence();
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nrows = G.Tvol >> 5;
-    const int tseg = G.T[0] < 32 ? G.T[0] : 32;
-    const int lxw = lane & (tseg - 1);
     const bool producer = threadIdx.x == 0;
+    const float ih = (float)G.inv_h;
+    float lo[3], nper[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (float)G.lo[a];
+        nper[a] = G.per[a] ? (float)G.n[a] : 3.0e38f;
+    }
     RowChunk c = next_chunk(tcs, nrows, RowChunk{-1, 0u, 0u, 0u, false}, C::kCap);
     RowChunk pc = c;
     int issued = 0;
     if (producer) {
-        for (int s = 0; s < 2 && pc.valid; ++s) {
-            k2_stage<D>(pc, pt, stage + s * C::kFields * C::kPitch, bar + s);
+        for (int q = 0; q < C::kStages && pc.valid; ++q) {
+            k2_stage<D>(pc, pt, stage + q * C::kFields * C::kPitch, bar + q);
             pc = next_chunk(tcs, nrows, pc, C::kCap);
             ++issued;
         }
     }
-    // phase (ii) state of this lane (warps d < D)
-    float acc[NN];
+    const float* sAd = sA + warp * W;
+    float* s2d = s2 + warp * W;
+    float Aw[NN], acc[NN];
     uint32_t sb = 0, se = 0;
     int base = 0;
+    float cb[3] = {0.f, 0.f, 0.f};
     float vmax = 0.f;
-    int err = 0, fail = 0, i = 0;
+    int fail = 0, i = 0;
     for (; c.valid; ++i) {
-        const int st = i & 1;
-        if (!mbar_wait(bar + st, (uint32_t)(i >> 1) & 1u)) fail = 1;
+        const int st = i % C::kStages;
+        if (!mbar_wait(bar + st, (uint32_t)(i / C::kStages) & 1u)) fail = 1;
         float* sg = stage + st * C::kFields * C::kPitch;
         const uint32_t a0 = c.lo & ~3u;
-        // (i) one thread per particle: V' = V + dt G2P(f/m)
-        for (uint32_t k = c.lo + threadIdx.x; k < c.hi; k += blockDim.x) {
-            const uint32_t j = k - a0;
-            float x[3], w[3][3], dw[3][3];
-            int l[3] = {0, 0, 0};
-            bool ok = true;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                x[a] = sg[a * C::kPitch + j];
-                float xi;
-                const int cc = span_of<float, P>(G, a, x[a], xi);
-                weights1d<P>(__fsub_rn(xi, (float)(cc - (P == 2 ? 1 : 0))), w[a], dw[a]);
-                l[a] = wrap_span(G, a, cc) - so[a];
-                ok = ok && l[a] >= 0 && l[a] < G.T[a];
-            }
-            // weights for the momentum P2G of phase (ii) (zero: no contribution)
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-#pragma unroll
-                for (int q = 0; q < NS; ++q) sw[(a * 3 + q) * C::kPitch + j] = ok ? w[a][q] : 0.f;
-            if (!ok) { err = 1; continue; }
-            const int nb = (l[2] * W1 + l[1]) * W0 + l[0];
-            float A0 = 0.f, A1 = 0.f, A2 = 0.f;
+        if (c.lo == tcs[c.r << 5]) {
+            // a new row: the lane's span, its f_d/m values, zero sums
+            const int s = (c.r << 5) + lane;
+            sb = tcs[s];
+            se = tcs[s + 1];
+            const int lx = s & (G.T[0] - 1);
+            const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
+            const int lz = s >> (G.tsh[0] + G.tsh[1]);
+            base = (lz * W1 + ly) * W0 + lx;
+            cb[0] = (float)(so[0] + lx - (P == 2 ? 1 : 0));
+            cb[1] = (float)(so[1] + ly - (P == 2 ? 1 : 0));
+            cb[2] = (float)(so[2] + lz - (P == 2 ? 1 : 0));
 #pragma unroll
             for (int jj = 0; jj < NYZ; ++jj) {
-                const int bb = D == 3 ? jj % NS : jj, cz = D == 3 ? jj / NS : 0;
-                const float yz = D == 3 ? w[1][bb] * w[2][cz] : w[1][bb];
-                const int row = nb + (cz * W1 + bb) * W0;
-                float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+                const int row = base + ((D == 3 ? jj / NS : 0) * W1 + (D == 3 ? jj % NS : jj)) * W0;
 #pragma unroll
                 for (int a = 0; a < NS; ++a) {
-                    const float4 q = sA[row + a];
-                    x0 = fmaf(w[0][a], q.x, x0);
-                    x1 = fmaf(w[0][a], q.y, x1);
-                    x2 = fmaf(w[0][a], q.z, x2);
+                    Aw[jj * NS + a] = sAd[row + a];
+                    acc[jj * NS + a] = 0.f;
                 }
-                A0 = fmaf(yz, x0, A0);
-                A1 = fmaf(yz, x1, A1);
-                A2 = fmaf(yz, x2, A2);
             }
-            const float A[3] = {A0, A1, A2};
+        }
+        const uint32_t kb0 = max(sb, c.lo), kb1 = min(se, c.hi);
+        const uint32_t cnt = kb1 > kb0 ? kb1 - kb0 : 0u;
+        // lanes start at different particles of their spans: with 8 particles
+        // a span, the 32 lanes then read 32 different banks
+        const uint32_t rot = cnt ? ((uint32_t)lane >> 2) % cnt : 0u;
+        for (uint32_t ii = 0; ii < cnt; ++ii) {
+            const uint32_t kk = ii + rot;
+            const uint32_t j = kb0 - a0 + (kk >= cnt ? kk - cnt : kk);
+            float w[3][3], dw[3][3];
+#pragma unroll
+            for (int a = 0; a < D; ++a) axis_known<P, PER>(sg[a * C::kPitch + j], lo[a], ih, cb[a], nper[a], w[a], dw[a]);
+            float yz[NYZ];
+#pragma unroll
+            for (int jj = 0; jj < NYZ; ++jj) yz[jj] = D == 3 ? w[1][jj % NS] * w[2][jj / NS] : w[1][jj];
+            // A_d = sum over the support of phi f_d/m, x first
+            float A = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < NYZ; ++jj) {
+                float t = 0.f;
+#pragma unroll
+                for (int a = 0; a < NS; ++a) t = fmaf(w[0][a], Aw[jj * NS + a], t);
+                A = fmaf(yz[jj], t, A);
+            }
+            float* vp = sg + (D + warp) * C::kPitch + j;
+            const float vn = fmaf(dt, A, *vp);
+            *vp = vn;
+            const float mv = sg[2 * D * C::kPitch + j] * vn;
+            float cm[NS];
+#pragma unroll
+            for (int a = 0; a < NS; ++a) cm[a] = mv * w[0][a];
+#pragma unroll
+            for (int jj = 0; jj < NYZ; ++jj)
+#pragma unroll
+                for (int a = 0; a < NS; ++a) acc[jj * NS + a] = fmaf(cm[a], yz[jj], acc[jj * NS + a]);
+        }
+        if (c.hi == c.re) {
+            // the row is complete: node lx + a of each window row gets acc of
+            // span lx, in NS phases (each lane a different node in a phase)
+#pragma unroll
+            for (int a = 0; a < NS; ++a) {
+                __syncwarp();
+#pragma unroll
+                for (int jj = 0; jj < NYZ; ++jj)
+                    s2d[base + ((D == 3 ? jj / NS : 0) * W1 + (D == 3 ? jj % NS : jj)) * W0 + a] += acc[jj * NS + a];
+            }
+            __syncwarp();
+        }
+        // V' of the chunk is complete in the stage; order the generic
+        // accesses to the stages before later bulk copies into them
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (block_bar_or(fail)) { fail = 1; break; }
+        // the previous chunk's stage is free (every thread passed its
+        // write-back before this barrier): refill it
+        if (producer && i >= 1 && pc.valid) {
+            const int q = (i - 1) % C::kStages;
+            k2_stage<D>(pc, pt, stage + q * C::kFields * C::kPitch, bar + q);
+            pc = next_chunk(tcs, nrows, pc, C::kCap);
+            ++issued;
+        }
+        // write the chunk's V' back, coalesced
+        for (uint32_t k = c.lo + threadIdx.x; k < c.hi; k += blockDim.x) {
+            const uint32_t j = k - a0;
             float v2 = 0.f;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                const float vn = fmaf(dt, A[a], sg[(D + a) * C::kPitch + j]);
-                sg[(D + a) * C::kPitch + j] = vn;
+                const float vn = sg[(D + a) * C::kPitch + j];
                 pt.v[a][k] = vn;
                 v2 = fmaf(vn, vn, v2);
             }
             vmax = fmaxf(vmax, v2);
         }
-        // V' was written into the stage by generic stores; order them before
-        // the bulk copy that will later refill this stage
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        // (ii) warp d: P2G of M V'_d over the row's spans, one span per lane
-        if (warp < D) {
-            if (c.lo == tcs[c.r << 5]) {
-                const int s = (c.r << 5) + lane;
-                sb = tcs[s];
-                se = tcs[s + 1];
-                const int lx = s & (G.T[0] - 1);
-                const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
-                const int lz = s >> (G.tsh[0] + G.tsh[1]);
-                base = (lz * W1 + ly) * W0 + lx;
-#pragma unroll
-                for (int q = 0; q < NN; ++q) acc[q] = 0.f;
-            }
-            const uint32_t kb0 = max(sb, c.lo), kb1 = min(se, c.hi);
-            const uint32_t cnt = kb1 > kb0 ? kb1 - kb0 : 0u;
-            const uint32_t rot = cnt ? ((uint32_t)lane >> 2) % cnt : 0u;
-            for (uint32_t ii = 0; ii < cnt; ++ii) {
-                const uint32_t kk = ii + rot;
-                const uint32_t j = kb0 - a0 + (kk >= cnt ? kk - cnt : kk);
-                float w[3][3];
-#pragma unroll
-                for (int a = 0; a < D; ++a)
-#pragma unroll
-                    for (int q = 0; q < NS; ++q) w[a][q] = sw[(a * 3 + q) * C::kPitch + j];
-                const float mv = sg[2 * D * C::kPitch + j] * sg[(D + warp) * C::kPitch + j];
-                float cm[NS];
-#pragma unroll
-                for (int a = 0; a < NS; ++a) cm[a] = mv * w[0][a];
-#pragma unroll
-                for (int jj = 0; jj < NYZ; ++jj) {
-                    const float yz = D == 3 ? w[1][jj % NS] * w[2][jj / NS] : w[1][jj];
-#pragma unroll
-                    for (int a = 0; a < NS; ++a) acc[jj * NS + a] = fmaf(cm[a], yz, acc[jj * NS + a]);
-                }
-            }
-            if (c.hi == c.re) {
-                // the row is complete: add its sums (x-neighbours summed first)
-#pragma unroll
-                for (int jj = 0; jj < NYZ; ++jj) {
-                    const int row = base - lxw + ((D == 3 ? jj / NS : 0) * W1 + (D == 3 ? jj % NS : jj)) * W0;
-                    float v[NS];
-#pragma unroll
-                    for (int a = 0; a < NS; ++a) v[a] = acc[jj * NS + a];
-                    xrow_rmw<NS>(s2 + warp * W + row, v, lxw, tseg);
-                }
-            }
-        }
-        // the stage is free once every warp is done with it
-        if (block_bar_or(fail)) { fail = 1; break; }
-        if (producer && pc.valid) {
-            k2_stage<D>(pc, pt, stage + st * C::kFields * C::kPitch, bar + st);
-            pc = next_chunk(tcs, nrows, pc, C::kCap);
-            ++issued;
-        }
         c = next_chunk(tcs, nrows, c, C::kCap);
     }
     if (fail && producer) {
         // drain the copies still in flight before the block's memory is reused
-        for (int j = i; j < issued; ++j) mbar_wait(bar + (j & 1), (uint32_t)(j >> 1) & 1u);
+        for (int q = i; q < issued; ++q) mbar_wait(bar + (q % C::kStages), (uint32_t)(q / C::kStages) & 1u);
     }
     vmax = warp_max(vmax);
     if (lane == 0) atomic_max_nonneg(&clk->vmax_bits, (double)sqrtf(vmax));
-    if (err || fail) atomicOr(&clk->err, (err ? ERR_TILE : 0) | (fail ? ERR_TIMEOUT : 0));
+    if (fail) atomicOr(&clk->err, ERR_TIMEOUT);
     __syncthreads();
     if (fail) return;
     flush_window<D, P>(G, so, s2, D, out);
 }
 
 template <int D, int P, bool PER>
-__global__ void __launch_bounds__(K2Cfg<D>::kThreads, 4) k_grid_g2p_span(Geom G, TileState<float> ts,
+__global__ void __launch_bounds__(K2Cfg<D>::kThreads, 5) k_grid_g2p_span(Geom G, TileState<float> ts,
                                                                          Grid<float, float> gr, FieldPtrs out,
                                                                          Clock* clk,
                                                                          const uint32_t* __restrict__ tiles)

@@ -561,18 +561,19 @@ __global__ void __launch_bounds__(1024) k_relayout_bases(const uint32_t* tcount,
 }
 
 // End of the re-order: clear the changed tiles' marks, install the regions of
-// a relayout.
+// a relayout.  One warp per tile (a changed tile clears Tvol counts).
 __device__ __forceinline__ void reorder_done_tile(int tvol, const Reorder& ro, Clock* clk, uint32_t* tbase,
-                                                  const uint32_t* tbase_next, int t, int ntiles)
+                                                  const uint32_t* tbase_next, int t, int ntiles, int lane)
 {
     // only a changed tile has count changes and ring marks
     if (ro.dirty[t]) {
-        for (int w = 0; w < ro.mwords; ++w) ro.ring[(int64_t)t * ro.mwords + w] = 0ull;
+        for (int w = lane; w < ro.mwords; w += 32) ro.ring[(int64_t)t * ro.mwords + w] = 0ull;
         uint4* c4 = reinterpret_cast<uint4*>(ro.count + (int64_t)t * tvol);
-        for (int k = 0; k < tvol / 4; ++k) c4[k] = make_uint4(0u, 0u, 0u, 0u);
-        ro.dirty[t] = 0u;
+        for (int k = lane; k < tvol / 4; k += 32) c4[k] = make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();                       // every lane has read the mark
+        if (lane == 0) ro.dirty[t] = 0u;
     }
-    if (clk->overflow) {
+    if (lane == 0 && clk->overflow) {
         tbase[t] = tbase_next[t];
         if (t == ntiles - 1) tbase[ntiles] = tbase_next[ntiles];
         if (t == 0) clk->relayouts += 1;
@@ -581,8 +582,10 @@ __device__ __forceinline__ void reorder_done_tile(int tvol, const Reorder& ro, C
 
 __global__ void k_reorder_done(Geom G, Reorder ro, Clock* clk, uint32_t* tbase, const uint32_t* tbase_next)
 {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G.ntiles; t += gridDim.x * blockDim.x)
-        reorder_done_tile(G.Tvol, ro, clk, tbase, tbase_next, t, G.ntiles);
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = w0; t < G.ntiles; t += nw)
+        reorder_done_tile(G.Tvol, ro, clk, tbase, tbase_next, (int)t, G.ntiles, threadIdx.x & 31);
 }
 
 // Initial layout: the particles of a compact key order (cell starts cc[key],
