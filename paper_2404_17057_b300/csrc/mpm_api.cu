@@ -390,7 +390,7 @@ struct Impl {
     {
         const Geom& G = s->G;
         const ReorderArgs<R> a = rargs(s, s->cur);
-        const unsigned nb = (unsigned)std::min<int64_t>(G.ntiles, (int64_t)s->sms * 3);
+        const unsigned nb = (unsigned)std::min<int64_t>(G.ntiles, (int64_t)s->sms * kReorderBlocksPerSM);
         k_reorder<D, R><<<nb, kReorderThreads, reorder_smem(G), st>>>(G, a, 0);
         k_consolidate<D, R><<<nb, kReorderThreads, 0, st>>>(G, a);
         k_relayout_bases<<<1, 1024, 0, st>>>(s->tcount, G.ntiles, s->tbase_next, s->clk);

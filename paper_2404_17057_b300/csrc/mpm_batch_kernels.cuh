@@ -207,7 +207,7 @@ __device__ __forceinline__ void batch_reorder_args(const BatchProb<R, A>& p, int
 // mode 0: the member's changed tiles; mode 1: its relayout (if a tile
 // overflowed)
 template <int D, class R, class A>
-__global__ void __launch_bounds__(kReorderThreads, 3) kb_reorder(const BatchProb<R, A>* __restrict__ bp,
+__global__ void __launch_bounds__(kReorderThreads, kReorderBlocksPerSM) kb_reorder(const BatchProb<R, A>* __restrict__ bp,
                                                                  const TileRef* __restrict__ tl, int mode)
 {
     MPM_BATCH_PROLOGUE(R, A)

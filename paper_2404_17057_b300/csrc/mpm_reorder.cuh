@@ -35,13 +35,16 @@
 
 namespace mpm {
 
-constexpr int kReorderThreads = 256;
+constexpr int kReorderThreads = 128;
 constexpr int kReorderWarps = kReorderThreads / 32;
 constexpr int kReorderItems = 8;                                  // keys per thread per chunk
 constexpr int kReorderChunk = kReorderThreads * kReorderItems;
-constexpr int kReorderCap = 6144;                                 // compacted particles per flush
+constexpr int kReorderCap = 1024;                                 // compacted particles per flush
 constexpr int kReorderMaxRanges = 1024;
-constexpr int kReorderFarCap = 1024;                              // recycled arrivals per tile
+constexpr int kReorderFarCap = 512;                               // recycled arrivals per tile
+// Resident re-order blocks per SM: a tile's re-order is a chain of short
+// dependent phases, so many small blocks hide each other's latency.
+constexpr int kReorderBlocksPerSM = 8;
 
 // Region of a tile with n particles: room for twice as many plus 64, in
 // multiples of 32 slots (128-byte aligned starts in single precision).
@@ -78,7 +81,7 @@ __device__ __forceinline__ void copy_particle(const Particles<R>& in, const Part
 }
 
 // Copy kB particles per lane, slot q[u] -> slot j[u], where ok[u]: all loads
-// first, so that 12 kB independent loads per lane are in flight.
+// first, so that up to 12 kB independent loads per lane are in flight.
 template <int kB, class R>
 __device__ __forceinline__ void copy_batch(const Particles<R>& s, const Particles<R>& out, int D, const uint32_t* q,
                                            const uint32_t* j, const bool* ok, bool with_gen)
@@ -424,7 +427,7 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
             base[k] = run;
         }
         __syncthreads();
-        constexpr int kB = sizeof(R) == 4 ? 4 : 2;     // particles per lane per batch
+        constexpr int kB = 2;                          // particles per lane per batch
         for (uint32_t j0 = wb; j0 < we; j0 += 32 * kB) {
             uint32_t qv[kB], pv[kB];
             bool okv[kB];
@@ -501,7 +504,7 @@ __device__ __forceinline__ void reorder_tile(const Geom& G, const ReorderArgs<R>
 
 // Pass `mode` over the tiles of one simulation (persistent CTAs).
 template <int D, class R>
-__global__ void __launch_bounds__(kReorderThreads, 3) k_reorder(Geom G, ReorderArgs<R> A, int mode)
+__global__ void __launch_bounds__(kReorderThreads, kReorderBlocksPerSM) k_reorder(Geom G, ReorderArgs<R> A, int mode)
 {
     if (mode == 1 && !A.clk->overflow) return;
     for (int t = blockIdx.x; t < G.ntiles; t += gridDim.x) {
