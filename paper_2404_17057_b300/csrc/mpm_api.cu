@@ -178,7 +178,7 @@ struct Vtbl {
     // batched execution: descriptor of a member, stage launches of a group
     size_t bdesc_size;
     void (*bdesc_fill)(const mpm_sim* s, void* out);
-    void (*blaunch)(int stage, const void* desc, const TileRef* tl, int ntl, size_t smem, int per, cudaStream_t st);
+    void (*blaunch)(int stage, const void* desc, const TileRef* tl, int ntl, size_t smem, int flags, cudaStream_t st);
     cudaError_t (*bset_smem)(const size_t smem[4]);
 };
 
@@ -294,10 +294,11 @@ struct Impl {
         else e = allow((const void*)k_g2pd<D, P, R, A>, smem(G, 2));
         if (e != cudaSuccess) return e;
         if constexpr (kFast) {
-            const void* f[4] = {(const void*)k_p2g_span<D, P, true>, (const void*)k_p2g_span<D, P, false>,
+            const void* f[6] = {(const void*)k_p2g_span<D, P, true, true>, (const void*)k_p2g_span<D, P, false, true>,
+                                (const void*)k_p2g_span<D, P, true, false>, (const void*)k_p2g_span<D, P, false, false>,
                                 (const void*)k_grid_g2p_span<D, P, true>, (const void*)k_grid_g2p_span<D, P, false>};
-            const size_t z[4] = {smem(G, 0), smem(G, 0), smem(G, 1), smem(G, 1)};
-            for (int i = 0; i < 4; ++i)
+            const size_t z[6] = {smem(G, 0), smem(G, 0), smem(G, 0), smem(G, 0), smem(G, 1), smem(G, 1)};
+            for (int i = 0; i < 6; ++i)
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
             return cudaSuccess;
         } else {
@@ -326,8 +327,11 @@ struct Impl {
                     const uint32_t* tl = colour_tiles(s, c);
                     const unsigned nb = colour_blocks(s, c);
                     if (nb == 0) continue;
-                    if (per) k_p2g_span<D, P, true><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
-                    else k_p2g_span<D, P, false><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
+                    const bool col = p2g_columns(G);
+                    if (per && col) k_p2g_span<D, P, true, true><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
+                    else if (col) k_p2g_span<D, P, false, true><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
+                    else if (per) k_p2g_span<D, P, true, false><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
+                    else k_p2g_span<D, P, false, false><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
                 }
                 s->launches += ncolours(s) - 1;
             } else if (kSpan2d && span2d(s)) {
@@ -439,9 +443,11 @@ struct Impl {
         memcpy(out, &d, sizeof d);
     }
     // stage 0: P2G, 1: grid + G2P + P2G, 2: G2PD + update, 3: re-order of
-    // the changed tiles, 4 and 5: relayout (consolidation, rebuild)
-    static void blaunch(int stage, const void* dv, const TileRef* tl, int ntl, size_t sm, int per, cudaStream_t st)
+    // the changed tiles, 4 and 5: relayout (consolidation, rebuild).
+    // flags: 1 = a periodic axis, 2 = P2G walks span columns (p2g_columns)
+    static void blaunch(int stage, const void* dv, const TileRef* tl, int ntl, size_t sm, int flags, cudaStream_t st)
     {
+        const bool per = (flags & 1) != 0;
         const BatchProb<R, A>* d = static_cast<const BatchProb<R, A>*>(dv);
         if (ntl <= 0) return;
         if (stage == 3 || stage == 5) {
@@ -459,8 +465,11 @@ struct Impl {
         }
         if constexpr (kFast) {
             if (stage == 0) {
-                if (per) kb_p2g_span<D, P, true><<<ntl, kP2GThreads, sm, st>>>(d, tl);
-                else kb_p2g_span<D, P, false><<<ntl, kP2GThreads, sm, st>>>(d, tl);
+                const bool col = (flags & 2) != 0;
+                if (per && col) kb_p2g_span<D, P, true, true><<<ntl, kP2GThreads, sm, st>>>(d, tl);
+                else if (col) kb_p2g_span<D, P, false, true><<<ntl, kP2GThreads, sm, st>>>(d, tl);
+                else if (per) kb_p2g_span<D, P, true, false><<<ntl, kP2GThreads, sm, st>>>(d, tl);
+                else kb_p2g_span<D, P, false, false><<<ntl, kP2GThreads, sm, st>>>(d, tl);
             } else {
                 if (per) kb_grid_g2p_span<D, P, true><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
                 else kb_grid_g2p_span<D, P, false><<<ntl, K2Cfg<D>::kThreads, sm, st>>>(d, tl);
@@ -496,10 +505,11 @@ struct Impl {
         else e = allow((const void*)kb_g2pd<D, P, R, A>, sm[2]);
         if (e != cudaSuccess) return e;
         if constexpr (kFast) {
-            const void* f[4] = {(const void*)kb_p2g_span<D, P, true>, (const void*)kb_p2g_span<D, P, false>,
+            const void* f[6] = {(const void*)kb_p2g_span<D, P, true, true>, (const void*)kb_p2g_span<D, P, false, true>,
+                                (const void*)kb_p2g_span<D, P, true, false>, (const void*)kb_p2g_span<D, P, false, false>,
                                 (const void*)kb_grid_g2p_span<D, P, true>, (const void*)kb_grid_g2p_span<D, P, false>};
-            const size_t z[4] = {sm[0], sm[0], sm[1], sm[1]};
-            for (int i = 0; i < 4; ++i)
+            const size_t z[6] = {sm[0], sm[0], sm[0], sm[0], sm[1], sm[1]};
+            for (int i = 0; i < 6; ++i)
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
             return cudaSuccess;
         } else {

@@ -17,7 +17,7 @@ namespace {
 
 struct BatchGroup {
     const Vtbl* vt;
-    int per;
+    int per;           // blaunch flags: 1 = a periodic axis, 2 = P2G span columns
     std::vector<int> members;      // indices into mpm_batch::members
     size_t smem[4];
     size_t desc_off, tl_off;
@@ -116,7 +116,7 @@ mpm_status batch_build(mpm_batch* b)
     // groups of members that share the kernel variant
     for (int i = 0; i < n; ++i) {
         const mpm_sim* s = b->members[i];
-        const int per = (s->G.per[0] | s->G.per[1] | s->G.per[2]) ? 1 : 0;
+        const int per = ((s->G.per[0] | s->G.per[1] | s->G.per[2]) ? 1 : 0) | (p2g_columns(s->G) ? 2 : 0);
         BatchGroup* g = nullptr;
         for (auto& h : b->groups)
             if (h.vt == s->vt && h.per == per) g = &h;

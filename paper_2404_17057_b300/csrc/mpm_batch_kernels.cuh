@@ -147,12 +147,12 @@ __global__ void __launch_bounds__(256) kb_g2pd(const BatchProb<R, A>* __restrict
     g2pd_tile<D, P, R, A>(p.G, p.pt, p.gr, csp, p.clk, p.ro, r.tile);
 }
 
-template <int D, int P, bool PER>
+template <int D, int P, bool PER, bool COL>
 __global__ void __launch_bounds__(kP2GThreads, 6) kb_p2g_span(const BatchProb<float, float>* __restrict__ bp,
                                                               const TileRef* __restrict__ tl)
 {
     MPM_BATCH_PROLOGUE(float, float)
-    p2g_span_tile<D, P, PER>(p.G, p.pt, p.p2g_out, csp, p.clk, r.tile);
+    p2g_span_tile<D, P, PER, COL>(p.G, p.pt, p.p2g_out, csp, p.clk, r.tile);
 }
 
 template <int P, class R, class A>

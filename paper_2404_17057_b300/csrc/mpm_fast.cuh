@@ -359,7 +359,12 @@ __device__ __forceinline__ void p2g_zcol(const Geom& G, const Particles<float>& 
     }
 }
 
-template <int D, int P, bool PER>
+__host__ __device__ inline bool p2g_columns(const Geom& G) { return G.dim == 3 && G.T[0] * G.T[1] >= 32; }
+
+// COL: 3D tiles whose z-layers hold whole rows of 32 spans walk span columns
+// (p2g_zcol); the others walk rows.  Separate instantiations keep each
+// kernel's registers to its own path.
+template <int D, int P, bool PER, bool COL>
 __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<float>& pt, const FieldPtrs& out,
                                               const uint32_t* __restrict__ cs, Clock* clk, const int tile)
 {
@@ -382,7 +387,7 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int group = warp & 1;
-    if constexpr (D == 3) {
+    if constexpr (D == 3 && COL) {
         if (group == 0) p2g_zcol<P, PER, 0>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
         else p2g_zcol<P, PER, 1>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
         __syncthreads();
@@ -557,12 +562,12 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
 
 // tiles: the tiles of one colour pass (block b runs tiles[b]), or NULL (block
 // b runs tile b)
-template <int D, int P, bool PER>
+template <int D, int P, bool PER, bool COL>
 __global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, TileState<float> ts, FieldPtrs out, Clock* clk,
                                                               const uint32_t* __restrict__ tiles)
 {
     const int t = tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x;
-    p2g_span_tile<D, P, PER>(G, ts.pt, out, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
+    p2g_span_tile<D, P, PER, COL>(G, ts.pt, out, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
 }
 
 // ------------------------------- 2D span-per-lane kernels, 64-bit sums

@@ -137,6 +137,10 @@ P2G_CASES = [
     (3, 1, [10, 9, 11], ["wall"] * 6, (0, 0, 0)),
     (2, 2, [160, 60], ["wall"] * 4, (32, 1, 0)),
     (2, 1, [160, 64], ["periodic"] * 2 + ["inflow", "outflow"], (32, 1, 0)),
+    # 3D tiles whose z-layer holds fewer than 32 spans (FP32 P2G walks rows,
+    # not span columns), and exactly 32 (two-span columns, 8-span x-rows)
+    (3, 2, [13, 11, 9], ["wall"] * 6, (4, 4, 8)),
+    (3, 2, [20, 12, 10], ["periodic"] * 2 + ["wall"] * 4, (8, 4, 2)),
 ]
 
 
