@@ -661,6 +661,8 @@ mpm_status make_geom(const mpm_config* c, Geom* G, std::string* why)
         G->lo[a] = c->origin[a];
         G->hi[a] = c->origin[a] + c->n[a] * c->h;
     }
+    G->inv_w[0] = 1.0f / (float)G->W[0];
+    G->inv_w[1] = 1.0f / (float)G->W[1];
     for (int a = 0; a < 3; ++a) {
         tvol *= G->T[a];
         wvol *= G->W[a];

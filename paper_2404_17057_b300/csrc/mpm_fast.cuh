@@ -206,8 +206,6 @@ __device__ __forceinline__ void p2g_zcol(const Geom& G, const Particles<float>& 
 {
     constexpr int NS = P + 1, NYZ = NS * NS, NN = NYZ * NS, L = NS * NS;
     const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
-    const int tseg = G.T[0] < 32 ? G.T[0] : 32;
-    const int lxw = lane & (tseg - 1);
     const int rpl = (G.T[0] * G.T[1]) >> 5;
     for (int yb = 0; yb < rpl; ++yb) {
         // GROUP 0: qa = {m, mv_x}, qb = {mv_y, mv_z}; GROUP 1: qa = {f_y, f_z}, qc = f_x
@@ -307,43 +305,36 @@ __device__ __forceinline__ void p2g_zcol(const Geom& G, const Particles<float>& 
                     }
                 }
             }
-            // the completed node layers: the lowest, or all three after the
-            // column's last span
+            // the completed node layers (the lowest, or all three after the
+            // column's last span) go into the window in NS phases: in phase a
+            // lane lx adds its sums of node lx + a of each row, so the lanes
+            // of a phase write different nodes
             const bool last = z + 1 == G.T[2];
+            float* sp = sm + base;
 #pragma unroll
-            for (int c = 0; c < NS; ++c) {
-                if (c > 0 && !last) break;
+            for (int a = 0; a < NS; ++a) {
+                __syncwarp();
 #pragma unroll
-                for (int bb = 0; bb < NS; ++bb) {
-                    const int j = c * NS + bb;
-                    const int row = base - lxw + (c * W1 + bb) * W0;
-                    float v[NS];
-                    if (GROUP == 0) {
+                for (int c = 0; c < NS; ++c) {
+                    if (c > 0 && !last) break;
 #pragma unroll
-                        for (int a = 0; a < NS; ++a) v[a] = qa[j * NS + a].x;
-                        xrow_rmw<NS>(sm + row, v, lxw, tseg);
-#pragma unroll
-                        for (int a = 0; a < NS; ++a) v[a] = qa[j * NS + a].y;
-                        xrow_rmw<NS>(sm + W + row, v, lxw, tseg);
-#pragma unroll
-                        for (int a = 0; a < NS; ++a) v[a] = qb[j * NS + a].x;
-                        xrow_rmw<NS>(sm + 2 * W + row, v, lxw, tseg);
-#pragma unroll
-                        for (int a = 0; a < NS; ++a) v[a] = qb[j * NS + a].y;
-                        xrow_rmw<NS>(sm + 3 * W + row, v, lxw, tseg);
-                    } else {
-#pragma unroll
-                        for (int a = 0; a < NS; ++a) v[a] = qc[j * NS + a];
-                        xrow_rmw<NS>(sm + 4 * W + row, v, lxw, tseg);     // f_x
-#pragma unroll
-                        for (int a = 0; a < NS; ++a) v[a] = qa[j * NS + a].x;
-                        xrow_rmw<NS>(sm + 5 * W + row, v, lxw, tseg);     // f_y
-#pragma unroll
-                        for (int a = 0; a < NS; ++a) v[a] = qa[j * NS + a].y;
-                        xrow_rmw<NS>(sm + 6 * W + row, v, lxw, tseg);     // f_z
+                    for (int bb = 0; bb < NS; ++bb) {
+                        const int i = (c * NS + bb) * NS + a;
+                        float* r = sp + (c * W1 + bb) * W0 + a;
+                        if (GROUP == 0) {
+                            r[0] += qa[i].x;
+                            r[W] += qa[i].y;
+                            r[2 * W] += qb[i].x;
+                            r[3 * W] += qb[i].y;
+                        } else {
+                            r[4 * W] += qc[i];          // f_x
+                            r[5 * W] += qa[i].x;        // f_y
+                            r[6 * W] += qa[i].y;        // f_z
+                        }
                     }
                 }
             }
+            __syncwarp();
             if (last) break;
 #pragma unroll
             for (int i = 0; i < NN; ++i) {
@@ -949,6 +940,7 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
     int so[3];
     tile_origin(G, tile, so);
     const float dt = (float)clk->dt_cur;
+    const bool bc = window_has_bc(G, gr.mask, so);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         int idx[3];
         const int64_t node = slot_node<P>(G, so, i, idx);
@@ -957,7 +949,7 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
             m = gr.m[node];
 #pragma unroll
             for (int a = 0; a < D; ++a) f[a] = gr.f[a][node];
-            node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
+            if (bc) node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
         }
         const float im = m != 0.f ? __frcp_rn(m) : 0.f;
 #pragma unroll
@@ -995,7 +987,13 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
     }
     const float* sAd = sA + warp * W;
     float* s2d = s2 + warp * W;
-    float Aw[NN], acc[NN];
+    // f_d/m and the M V'_d sums of the span's nodes, node rows jj (y, z)
+    // paired for packed FMAs: rows 2q and 2q+1 in AwP[q][a] / accP[q][a],
+    // the last row of an odd count (quadratic basis) in AwT / accT
+    constexpr int NP = NYZ / 2;
+    constexpr bool ODD = (NYZ & 1) != 0;
+    float2 AwP[NP][NS], accP[NP][NS];
+    float AwT[NS], accT[NS];
     uint32_t sb = 0, se = 0;
     int base = 0;
     float cb[3] = {0.f, 0.f, 0.f};
@@ -1023,8 +1021,10 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
                 const int row = base + ((D == 3 ? jj / NS : 0) * W1 + (D == 3 ? jj % NS : jj)) * W0;
 #pragma unroll
                 for (int a = 0; a < NS; ++a) {
-                    Aw[jj * NS + a] = sAd[row + a];
-                    acc[jj * NS + a] = 0.f;
+                    const float v = sAd[row + a];
+                    if (ODD && jj == NYZ - 1) { AwT[a] = v; accT[a] = 0.f; }
+                    else if (jj & 1) { AwP[jj >> 1][a].y = v; accP[jj >> 1][a].y = 0.f; }
+                    else { AwP[jj >> 1][a].x = v; accP[jj >> 1][a].x = 0.f; }
                 }
             }
         }
@@ -1039,29 +1039,40 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
             float w[3][3], dw[3][3];
 #pragma unroll
             for (int a = 0; a < D; ++a) axis_known<P, PER>(sg[a * C::kPitch + j], lo[a], ih, cb[a], nper[a], w[a], dw[a]);
-            float yz[NYZ];
+            float2 yzP[NP];
 #pragma unroll
-            for (int jj = 0; jj < NYZ; ++jj) yz[jj] = D == 3 ? w[1][jj % NS] * w[2][jj / NS] : w[1][jj];
-            // A_d = sum over the support of phi f_d/m, x first
-            float A = 0.f;
-#pragma unroll
-            for (int jj = 0; jj < NYZ; ++jj) {
-                float t = 0.f;
-#pragma unroll
-                for (int a = 0; a < NS; ++a) t = fmaf(w[0][a], Aw[jj * NS + a], t);
-                A = fmaf(yz[jj], t, A);
+            for (int q = 0; q < NP; ++q) {
+                const int j0 = 2 * q, j1 = 2 * q + 1;
+                yzP[q] = D == 3 ? f2(w[1][j0 % NS] * w[2][j0 / NS], w[1][j1 % NS] * w[2][j1 / NS])
+                                : f2(w[1][j0], w[1][j1]);
             }
+            const float yzT = !ODD ? 0.f : D == 3 ? w[1][NS - 1] * w[2][NS - 1] : w[1][NYZ - 1];
+            // A_d = sum over the support of phi f_d/m, x first
+            float2 AP = f2(0.f, 0.f);
+            float tT = 0.f;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                float2 t = f2(0.f, 0.f);
+#pragma unroll
+                for (int a = 0; a < NS; ++a) t = __ffma2_rn(f2(w[0][a], w[0][a]), AwP[q][a], t);
+                AP = __ffma2_rn(yzP[q], t, AP);
+            }
+            if (ODD) {
+#pragma unroll
+                for (int a = 0; a < NS; ++a) tT = fmaf(w[0][a], AwT[a], tT);
+            }
+            const float A = ODD ? fmaf(yzT, tT, AP.x + AP.y) : AP.x + AP.y;
             float* vp = sg + (D + warp) * C::kPitch + j;
             const float vn = fmaf(dt, A, *vp);
             *vp = vn;
             const float mv = sg[2 * D * C::kPitch + j] * vn;
-            float cm[NS];
 #pragma unroll
-            for (int a = 0; a < NS; ++a) cm[a] = mv * w[0][a];
+            for (int a = 0; a < NS; ++a) {
+                const float cm = mv * w[0][a];
 #pragma unroll
-            for (int jj = 0; jj < NYZ; ++jj)
-#pragma unroll
-                for (int a = 0; a < NS; ++a) acc[jj * NS + a] = fmaf(cm[a], yz[jj], acc[jj * NS + a]);
+                for (int q = 0; q < NP; ++q) accP[q][a] = __ffma2_rn(f2(cm, cm), yzP[q], accP[q][a]);
+                if (ODD) accT[a] = fmaf(cm, yzT, accT[a]);
+            }
         }
         if (c.hi == c.re) {
             // the row is complete: node lx + a of each window row gets acc of
@@ -1071,7 +1082,8 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
                 __syncwarp();
 #pragma unroll
                 for (int jj = 0; jj < NYZ; ++jj)
-                    s2d[base + ((D == 3 ? jj / NS : 0) * W1 + (D == 3 ? jj % NS : jj)) * W0 + a] += acc[jj * NS + a];
+                    s2d[base + ((D == 3 ? jj / NS : 0) * W1 + (D == 3 ? jj % NS : jj)) * W0 + a] +=
+                        (ODD && jj == NYZ - 1) ? accT[a] : ((jj & 1) ? accP[jj >> 1][a].y : accP[jj >> 1][a].x);
             }
             __syncwarp();
         }

@@ -46,6 +46,7 @@ struct Geom {
     uint64_t seed;
     float qscale[3];                // fixed point: 2^32 / unit (mass, momentum, force)
     float dqscale[3];               // unit / 2^32
+    float inv_w[2];                 // 1 / W[0], 1 / W[1] (window slot decoding)
 };
 
 struct Clock {
@@ -346,14 +347,20 @@ __device__ __forceinline__ void tile_origin(const Geom& G, int tile, int so[3])
     so[2] = tz * G.T[2];
 }
 
+// w / d for 0 <= w < 2^21 from the float reciprocal of d: (w + 1/2) / d lies
+// at least 1/(2d) from an integer, and the two float roundings move it by
+// less than 2^-22 (w + 1/2) / d, which is smaller.
+__device__ __forceinline__ int div_small(int w, float inv_d) { return (int)(((float)w + 0.5f) * inv_d); }
+
 // Storage index of window slot w of the tile whose first span is so[], or -1.
 template <int P>
 __device__ __forceinline__ int64_t slot_node(const Geom& G, const int so[3], int w, int idx[3])
 {
     int ws[3];
-    ws[0] = w % G.W[0];
-    ws[1] = (w / G.W[0]) % G.W[1];
-    ws[2] = w / (G.W[0] * G.W[1]);
+    const int q = div_small(w, G.inv_w[0]);
+    ws[0] = w - q * G.W[0];
+    ws[2] = div_small(q, G.inv_w[1]);
+    ws[1] = q - ws[2] * G.W[1];
     for (int a = 0; a < 3; ++a) {
         if (a >= G.dim) { idx[a] = 0; continue; }
         int i = so[a] + ws[a];
