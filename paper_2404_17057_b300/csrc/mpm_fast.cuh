@@ -133,11 +133,15 @@ __device__ __forceinline__ void flush_window(const Geom& G, const int so[3], con
     const int nch = (W0 + 3) >> 2;
     const int nrow = W1 * W2;
     const bool vec = !G.per[0] && (G.T[0] % 4 == 0);
+    // t < 7 * 66^2 * 17 < 2^21: exact quotients from float reciprocals
+    const float inch = 1.0f / (float)nch, inrow = 1.0f / (float)nrow;
     for (int t = threadIdx.x; t < nf * nrow * nch; t += blockDim.x) {
-        const int q = t % nch;
-        const int r = (t / nch) % nrow;
-        const int f = t / (nch * nrow);
-        const int wy = r % W1, wz = r / W1;
+        const int tq = div_small(t, inch);
+        const int q = t - tq * nch;
+        const int f = div_small(tq, inrow);
+        const int r = tq - f * nrow;
+        const int wz = div_small(r, G.inv_w[1]);
+        const int wy = r - wz * W1;
         int iy = so[1] + wy, iz = D == 3 ? so[2] + wz : 0;
         if (G.per[1]) {
             iy -= (P == 2 ? 1 : 0);
@@ -1032,7 +1036,8 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
         const uint32_t cnt = kb1 > kb0 ? kb1 - kb0 : 0u;
         // lanes start at different particles of their spans: with 8 particles
         // a span, the 32 lanes then read 32 different banks
-        const uint32_t rot = cnt ? ((uint32_t)lane >> 2) % cnt : 0u;
+        uint32_t rot = cnt ? (uint32_t)lane >> 2 : 0u;     // (lane / 4) mod cnt
+        while (rot >= cnt && cnt) rot -= cnt;
         for (uint32_t ii = 0; ii < cnt; ++ii) {
             const uint32_t kk = ii + rot;
             const uint32_t j = kb0 - a0 + (kk >= cnt ? kk - cnt : kk);

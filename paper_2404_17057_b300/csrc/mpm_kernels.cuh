@@ -285,8 +285,14 @@ __device__ __forceinline__ int span_of(const Geom& G, int a, R x, R& xi)
 __device__ __forceinline__ int wrap_span(const Geom& G, int a, int c)
 {
     if (!G.per[a]) return c;
-    int r = c % G.n[a];
-    return r < 0 ? r + G.n[a] : r;
+    const int n = G.n[a];
+    // spans of positions in [lo, hi] and one span beyond wrap by one period
+    int r = c >= n ? c - n : (c < 0 ? c + n : c);
+    if ((unsigned)r >= (unsigned)n) {
+        r = c % n;
+        if (r < 0) r += n;
+    }
+    return r;
 }
 
 template <class R, int P>
