@@ -211,7 +211,12 @@ __device__ __forceinline__ void p2g_zcol(const Geom& G, const Particles<float>& 
     constexpr int NS = P + 1, NYZ = NS * NS, NN = NYZ * NS, L = NS * NS;
     const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
     const int rpl = (G.T[0] * G.T[1]) >> 5;
+    // spans beyond the last one of an axis hold no particles: a tile at the
+    // domain's end walks only its real z-layers and rows
+    const int nz = min(G.T[2], G.S[2] - so[2]);
     for (int yb = 0; yb < rpl; ++yb) {
+        const int r0 = yb << 5;     // first span of the row in its z-layer
+        if (so[1] + (r0 >> G.tsh[0]) >= G.S[1] || so[0] + (r0 & (G.T[0] - 1)) >= G.S[0]) continue;
         // GROUP 0: qa = {m, mv_x}, qb = {mv_y, mv_z}; GROUP 1: qa = {f_y, f_z}, qc = f_x
         float2 qa[NN], qb[GROUP == 0 ? NN : 1];
         float qc[GROUP == 0 ? 1 : NN];
@@ -220,7 +225,7 @@ __device__ __forceinline__ void p2g_zcol(const Geom& G, const Particles<float>& 
             qa[i] = f2(0.f, 0.f);
             if (GROUP == 0) qb[i] = f2(0.f, 0.f); else qc[i] = 0.f;
         }
-        for (int z = 0; z < G.T[2]; ++z) {
+        for (int z = 0; z < nz; ++z) {
             const int s = ((z * rpl + yb) << 5) + lane;
             const uint32_t b = cs[kb + s], e = cs[kb + s + 1];
             const int lx = s & (G.T[0] - 1);
@@ -313,7 +318,7 @@ __device__ __forceinline__ void p2g_zcol(const Geom& G, const Particles<float>& 
             // column's last span) go into the window in NS phases: in phase a
             // lane lx adds its sums of node lx + a of each row, so the lanes
             // of a phase write different nodes
-            const bool last = z + 1 == G.T[2];
+            const bool last = z + 1 == nz;
             float* sp = sm + base;
 #pragma unroll
             for (int a = 0; a < NS; ++a) {
@@ -369,7 +374,9 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
     extern __shared__ __align__(16) float sm[];
     constexpr int NS = P + 1, NF = 1 + 2 * D, NYZ = (D == 3) ? NS * NS : NS, NN = NYZ * NS;
     const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
-    for (int i = threadIdx.x; i < NF * W; i += blockDim.x) sm[i] = 0.f;
+    for (int i = threadIdx.x; i < (NF * W) >> 2; i += blockDim.x)
+        reinterpret_cast<float4*>(sm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = ((NF * W) & ~3) + threadIdx.x; i < NF * W; i += blockDim.x) sm[i] = 0.f;
     __syncthreads();
     int so[3];
     tile_origin(G, tile, so);
