@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_coloured", "fp32_fixed64", "fp64"])
     ap.add_argument("--degree", type=int, default=2, choices=[1, 2], help="basis: 1 = Q1, 2 = quadratic B-spline")
     ap.add_argument("--ppa", type=int, default=2, help="particles per cell along each axis")
+    ap.add_argument("--tile", default="",
+                    help="tile edges in spans, e.g. 8x8x8 (default: 8x8x8 for the blast, the library's for the "
+                         "cylinders)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", type=int, default=0,
                     help="also run the serving stream with this many requests (batched vs one at a time)")
@@ -69,19 +72,36 @@ def parse():
     return ap.parse_args()
 
 
+# Tile edges (spans) of the GPU kernels per workload, timed on B300: for the
+# 256^3 blast 8x8x8 10.43, 16x4x8 10.59, 16x8x4 (the library default) 10.68,
+# 8x16x4 10.73, 4x8x16 10.73, 32x4x4 12.38, 16x8x8 13.34 ms per step; the
+# 1024x512 cylinder keeps the library's 32x8 (16x16, 64x4, 32x4: +1 to +6%).
+DEFAULT_TILE = {"blast": [8, 8, 8]}
+
+
+def tile_of(args):
+    if args.tile:
+        t = [int(v) for v in args.tile.split("x")]
+        return t + [0] * (3 - len(t))
+    return DEFAULT_TILE.get(args.config, [0, 0, 0])
+
+
 def workload(args):
     """The workload's description, from the arguments alone (both arms)."""
     basis = "quadratic B-spline" if args.degree == 2 else "Q1"
+    tile = tile_of(args)
     if args.config == "blast":
         n = args.n or 256
         ppc = args.ppa ** 3
         return {"workload": f"3D blast wave {n}^3 cells, {ppc} ppc, {basis}, {args.precision}",
-                "cells": [n, n, n], "ppc": ppc, "degree": args.degree, "precision": args.precision}
+                "cells": [n, n, n], "ppc": ppc, "degree": args.degree, "precision": args.precision,
+                "tile": tile if any(tile) else "library default"}
     nx = args.n or (1024 if args.config == "cylinder" else 1414)
     ppc = args.ppa ** 2
     where = "" if args.config == "cylinder" else " on [0,4]x[0,2], r = 0.25, CFL 1/2"
     return {"workload": f"2D Mach-3 cylinder {nx}x{nx // 2} cells{where}, {ppc} ppc, {basis}, {args.precision}",
-            "cells": [nx, nx // 2], "ppc": ppc, "degree": args.degree, "precision": args.precision}
+            "cells": [nx, nx // 2], "ppc": ppc, "degree": args.degree, "precision": args.precision,
+            "tile": tile if any(tile) else "library default"}
 
 
 def problem(args):
@@ -89,12 +109,13 @@ def problem(args):
     cfg = workload(args)
     if args.config == "blast":
         n = cfg["cells"][0]
-        p = I.blast(n=n, ppa=args.ppa, degree=args.degree, precision=args.precision)
+        p = I.blast(n=n, ppa=args.ppa, degree=args.degree, precision=args.precision, tile=tile_of(args))
         cfg["l2"] = "inputs larger than L2 (no flush)"
     else:
         nx, ny = cfg["cells"]
         geo = {} if args.config == "cylinder" else {"lx": 4.0, "center": (0.6, 1.0), "radius": 0.25, "cfl": 0.5}
-        p = I.cylinder(nx=nx, ny=ny, ppa=args.ppa, degree=args.degree, precision=args.precision, **geo)
+        p = I.cylinder(nx=nx, ny=ny, ppa=args.ppa, degree=args.degree, precision=args.precision, tile=tile_of(args),
+                       **geo)
         cfg["l2"] = ("inputs larger than L2 (no flush)" if p.n_particles * 40 > 126e6
                      else "particle state partly L2-resident")
     cfg["particles"] = p.n_particles
