@@ -941,7 +941,7 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
     const int64_t kb = tile_cs0(G, tile);
     if (cs[kb] == cs[kb + G.Tvol]) return;
     extern __shared__ __align__(16) float sm[];
-    constexpr int NS = P + 1, NYZ = (D == 3) ? NS * NS : NS, NN = NYZ * NS;
+    constexpr int NS = P + 1, NYZ = (D == 3) ? NS * NS : NS;
     const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
     float* stage = sm;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + C::kStageFloats);
