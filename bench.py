@@ -199,13 +199,14 @@ class ClockSampler:
 
 # DRAM bytes per particle of the step kernels, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch each) of the
-# 128^3 blast, FP32, degree 2, divided by its 16,777,216 particles.  Traffic
-# grows with the particle count (same tiles, same ppc), so a full 256^3 launch
-# moves 8x those bytes.  Valid only for the kernel sources with this digest.
+# 128^3 blast, FP32, degree 2, 8x8x8 tiles, second step, divided by its
+# 16,777,216 particles.  Traffic grows with the particle count (same tiles,
+# same ppc), so a full 256^3 launch moves 8x those bytes.  Valid only for the
+# kernel sources with this digest.
 MEASURED_TRAFFIC = {
-    "sources": "c5f82dc8f4c49763",
-    "config": ("blast", 3, 2, "fp32", 2),
-    "bytes_per_particle": {"p2g": 49.49, "grid_g2p": 44.89, "g2pd": 55.25, "reorder": 92.87},
+    "sources": "1b1b4f8b37f7fbcd",
+    "config": ("blast", 3, 2, "fp32", 2, (8, 8, 8)),
+    "bytes_per_particle": {"p2g": 49.59, "grid_g2p": 45.58, "g2pd": 54.03, "reorder": 0.044},
 }
 
 
@@ -225,11 +226,12 @@ def sources_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str, config: str, dim: int, degree: int, precision: str, ppa: int, n_p: int):
+def measured_traffic(kernel: str, config: str, dim: int, degree: int, precision: str, ppa: int, n_p: int,
+                     tile=(0, 0, 0)):
     """DRAM bytes of one launch of `kernel`, or None when the counters were
     taken on other kernel sources or another kind of workload."""
     t = MEASURED_TRAFFIC
-    if t["config"] != (config, dim, degree, precision, ppa) or sources_digest() != t["sources"]:
+    if t["config"] != (config, dim, degree, precision, ppa, tuple(tile)) or sources_digest() != t["sources"]:
         return None
     return t["bytes_per_particle"][kernel] * n_p
 
@@ -483,7 +485,7 @@ def main():
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
                      "frac": ach / hbm, "peak_source": which,
                      "traffic": measured_traffic(dom, args.config, dim, int(p.cfg["degree"]), args.precision,
-                                                 args.ppa, n_p),
+                                                 args.ppa, n_p, tile_of(args)),
                      "k1_k2_k3_gbs": k123_gbs, "k1_k2_k3_frac": k123_gbs / hbm,
                      "k1_k2_k3_frac_nominal_7.7TB": k123_gbs / NOMINAL_HBM},
         "phase_ms_per_step": {"p2g": per_launch_ms["p2g"], "grid_g2p": per_launch_ms["grid_g2p"],
