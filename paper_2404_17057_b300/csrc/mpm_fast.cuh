@@ -359,7 +359,152 @@ __device__ __forceinline__ void p2g_zcol(const Geom& G, const Particles<float>& 
     }
 }
 
-__host__ __device__ inline bool p2g_columns(const Geom& G) { return G.dim == 3 && G.T[0] * G.T[1] >= 32; }
+
+// 2D span columns: a lane walks the spans of one x along y (rows of 32 spans
+// are x-rows of a tile at least 32 spans wide).  Its sums hold the three node
+// rows of the current span; after each span the lowest row is complete and
+// goes into the window in NS phases, the two others move down.  GROUP 0 sums
+// {m, mv_x, mv_y}, GROUP 1 {f_x, f_y}.
+template <int P, bool PER, int GROUP>
+__device__ __forceinline__ void p2g_ycol(const Geom& G, const Particles<float>& pt, const uint32_t* __restrict__ cs,
+                                         int64_t kb, const int so[3], const float lo[3], const float nper[3],
+                                         float ih, float gm1, float* sm, int lane)
+{
+    constexpr int NS = P + 1, NN = NS * NS, L = NS;
+    const int W = G.Wvol, W0 = G.W[0];
+    const int rpl = G.T[0] >> 5;                       // rows of 32 spans per y-line
+    const int ny = min(G.T[1], G.S[1] - so[1]);        // real y-lines of the tile
+    for (int xb = 0; xb < rpl; ++xb) {
+        if (so[0] + (xb << 5) >= G.S[0]) continue;
+        // GROUP 0: qa = {m, mv_x}, qc = mv_y; GROUP 1: qa = {f_x, f_y}
+        float2 qa[NN];
+        float qc[GROUP == 0 ? NN : 1];
+#pragma unroll
+        for (int i = 0; i < NN; ++i) {
+            qa[i] = f2(0.f, 0.f);
+            if (GROUP == 0) qc[i] = 0.f;
+        }
+        for (int y = 0; y < ny; ++y) {
+            const int s = ((y * rpl + xb) << 5) + lane;
+            const uint32_t b = cs[kb + s], e = cs[kb + s + 1];
+            const int lx = s & (G.T[0] - 1);
+            const int base = y * W0 + lx;
+            const float cb0 = (float)(so[0] + lx - (P == 2 ? 1 : 0));
+            const float cb1 = (float)(so[1] + y - (P == 2 ? 1 : 0));
+            if (GROUP == 0) {
+                float nx[2] = {0.f, 0.f}, nv[2] = {0.f, 0.f}, nM = 0.f;
+                if (b < e) {
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) { nx[a] = pt.x[a][b]; nv[a] = pt.v[a][b]; }
+                    nM = pt.M[b];
+                }
+                for (uint32_t k = b; k < e; ++k) {
+                    float x[2], v[2];
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) { x[a] = nx[a]; v[a] = nv[a]; }
+                    const float M = nM;
+                    if (k + 1 < e) {
+#pragma unroll
+                        for (int a = 0; a < 2; ++a) { nx[a] = pt.x[a][k + 1]; nv[a] = pt.v[a][k + 1]; }
+                        nM = pt.M[k + 1];
+                    }
+                    float w[2][3], dw[2][3];
+                    axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
+                    axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+                    const float mv0 = M * v[0], mv1 = M * v[1];
+                    float2 c0[NS];
+                    float c3[NS];
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) {
+                        const float wa = w[0][a];
+                        c0[a] = f2(M * wa, mv0 * wa);
+                        c3[a] = mv1 * wa;
+                    }
+#pragma unroll
+                    for (int j = 0; j < NS; ++j) {
+                        const float yj = w[1][j];
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) {
+                            qa[j * NS + a] = __ffma2_rn(c0[a], f2(yj, yj), qa[j * NS + a]);
+                            qc[j * NS + a] = fmaf(c3[a], yj, qc[j * NS + a]);
+                        }
+                    }
+                }
+            } else {
+                float nx[2] = {0.f, 0.f}, nM = 0.f, nr = 1.f, nE = 0.f, nQ = 0.f;
+                if (b < e) {
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) nx[a] = pt.x[a][b];
+                    nM = pt.M[b]; nr = pt.rho[b]; nE = pt.E[b]; nQ = pt.Q[b];
+                }
+                for (uint32_t k = b; k < e; ++k) {
+                    float x[2];
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) x[a] = nx[a];
+                    const float M = nM, rho = nr, E = nE, Q = nQ;
+                    if (k + 1 < e) {
+#pragma unroll
+                        for (int a = 0; a < 2; ++a) nx[a] = pt.x[a][k + 1];
+                        nM = pt.M[k + 1]; nr = pt.rho[k + 1]; nE = pt.E[k + 1]; nQ = pt.Q[k + 1];
+                    }
+                    float w[2][3], dw[2][3];
+                    axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
+                    axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+                    const float F = fmaf(gm1 * rho, E, Q) * __fdividef(M, rho) * ih;
+                    float2 cf[NS];
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) cf[a] = f2(F * dw[0][a], F * w[0][a]);
+#pragma unroll
+                    for (int j = 0; j < NS; ++j) {
+                        const float2 yd = f2(w[1][j], dw[1][j]);
+#pragma unroll
+                        for (int a = 0; a < NS; ++a) qa[j * NS + a] = __ffma2_rn(cf[a], yd, qa[j * NS + a]);
+                    }
+                }
+            }
+            // the completed node rows (the lowest, or all after the column's
+            // last span) into the window in NS phases: in phase a lane lx
+            // adds node lx + a, so the lanes of a phase write different nodes
+            const bool last = y + 1 == ny;
+            float* sp = sm + base;
+#pragma unroll
+            for (int a = 0; a < NS; ++a) {
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < NS; ++j) {
+                    if (j > 0 && !last) break;
+                    const int i = j * NS + a;
+                    float* r = sp + j * W0 + a;
+                    if (GROUP == 0) {
+                        r[0] += qa[i].x;
+                        r[W] += qa[i].y;
+                        r[2 * W] += qc[i];
+                    } else {
+                        r[3 * W] += qa[i].x;        // f_x
+                        r[4 * W] += qa[i].y;        // f_y
+                    }
+                }
+            }
+            __syncwarp();
+            if (last) break;
+#pragma unroll
+            for (int i = 0; i < NN; ++i) {
+                if (i + L < NN) {
+                    qa[i] = qa[i + L];
+                    if (GROUP == 0) qc[i] = qc[i + L];
+                } else {
+                    qa[i] = f2(0.f, 0.f);
+                    if (GROUP == 0) qc[i] = 0.f;
+                }
+            }
+        }
+    }
+}
+
+__host__ __device__ inline bool p2g_columns(const Geom& G)
+{
+    return G.dim == 3 ? G.T[0] * G.T[1] >= 32 : G.T[0] >= 32;
+}
 
 // COL: 3D tiles whose z-layers hold whole rows of 32 spans walk span columns
 // (p2g_zcol); the others walk rows.  Separate instantiations keep each
@@ -389,9 +534,14 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int group = warp & 1;
-    if constexpr (D == 3 && COL) {
-        if (group == 0) p2g_zcol<P, PER, 0>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
-        else p2g_zcol<P, PER, 1>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
+    if constexpr (COL) {
+        if constexpr (D == 3) {
+            if (group == 0) p2g_zcol<P, PER, 0>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
+            else p2g_zcol<P, PER, 1>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
+        } else {
+            if (group == 0) p2g_ycol<P, PER, 0>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
+            else p2g_ycol<P, PER, 1>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
+        }
         __syncthreads();
         flush_window<D, P>(G, so, sm, NF, out);
         return;
