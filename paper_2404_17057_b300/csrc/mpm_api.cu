@@ -300,6 +300,15 @@ struct Impl {
             const size_t z[6] = {smem(G, 0), smem(G, 0), smem(G, 0), smem(G, 0), smem(G, 1), smem(G, 1)};
             for (int i = 0; i < 6; ++i)
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
+            if constexpr (D == 3 && P == 2) {
+                const void* g[4] = {(const void*)k_p2g_span<3, 2, true, true, 8, 8, 8>,
+                                    (const void*)k_p2g_span<3, 2, false, true, 8, 8, 8>,
+                                    (const void*)k_p2g_span<3, 2, true, true, 16, 8, 4>,
+                                    (const void*)k_p2g_span<3, 2, false, true, 16, 8, 4>};
+                const int st = static_tile(G);
+                for (int i = 0; i < 2 && st > 0; ++i)
+                    if ((e = allow(g[2 * (st - 1) + i], smem(G, 0))) != cudaSuccess) return e;
+            }
             return cudaSuccess;
         } else {
             if constexpr (kSpan2d) {
@@ -328,6 +337,19 @@ struct Impl {
                     const unsigned nb = colour_blocks(s, c);
                     if (nb == 0) continue;
                     const bool col = p2g_columns(G);
+                    if constexpr (D == 3 && P == 2) {
+                        // compile-time tile edges for the common shapes
+                        const int shape = static_tile(G);
+                        if (shape == 1 && per)
+                            k_p2g_span<3, 2, true, true, 8, 8, 8><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
+                        else if (shape == 1)
+                            k_p2g_span<3, 2, false, true, 8, 8, 8><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
+                        else if (shape == 2 && per)
+                            k_p2g_span<3, 2, true, true, 16, 8, 4><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
+                        else if (shape == 2)
+                            k_p2g_span<3, 2, false, true, 16, 8, 4><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
+                        if (shape > 0) continue;
+                    }
                     if (per && col) k_p2g_span<D, P, true, true><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
                     else if (col) k_p2g_span<D, P, false, true><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);
                     else if (per) k_p2g_span<D, P, true, false><<<nb, kP2GThreads, smem(G, 0), st>>>(G, ts, o, s->clk, tl);

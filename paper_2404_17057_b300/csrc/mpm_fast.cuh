@@ -96,9 +96,12 @@ __device__ __forceinline__ void sh_add(long long* p, long long v)
 }
 
 // ATOMIC: rows that other warps may update at the same time.
+// Without ATOMIC the call starts with a warp barrier: lanes of different row
+// segments (different y) reach the same node row in different calls.
 template <int NS, class T, bool ATOMIC = false>
 __device__ __forceinline__ void xrow_rmw(T* row, const T* v, int lx, int T0)
 {
+    if constexpr (!ATOMIC) __syncwarp();
     T s = v[0];
 #pragma unroll
     for (int a = 1; a < NS; ++a) {
@@ -125,23 +128,39 @@ struct FieldPtrs {
 // Add a tile's shared-memory window (nf fields of W floats) into global node
 // rows.  Rows are padded to a multiple of 4 nodes and tiles start on a
 // multiple of 4 spans, so x-chunks of 4 nodes are 16-byte aligned.
-template <int D, int P>
+// TX, TY, TZ > 0: the tile edges as compile-time constants (3D); the
+// chunk, row and field of a thread's item then come from integer divisions
+// by constants.
+template <int D, int P, int TX = 0, int TY = 0, int TZ = 0>
 __device__ __forceinline__ void flush_window(const Geom& G, const int so[3], const float* sm, int nf,
                                              const FieldPtrs& dst)
 {
-    const int W0 = G.W[0], W1 = G.W[1], W2 = G.W[2], W = G.Wvol;
-    const int nch = (W0 + 3) >> 2;
-    const int nrow = W1 * W2;
-    const bool vec = !G.per[0] && (G.T[0] % 4 == 0);
+    constexpr bool ST = TX > 0;
+    static_assert(!ST || (D == 3 && TX % 4 == 0), "static windows: 3D tiles of a multiple of 4 spans in x");
+    constexpr int SW0 = TX + P, SW1 = TY + P, SW2 = TZ + P, SNCH = (SW0 + 3) / 4;
+    const int W0 = ST ? SW0 : G.W[0], W1 = ST ? SW1 : G.W[1];
+    const int W = ST ? SW0 * SW1 * SW2 : G.Wvol;
+    const int nch = ST ? SNCH : (W0 + 3) >> 2;
+    const int nrow = ST ? SW1 * SW2 : W1 * G.W[2];
+    const bool vec = !G.per[0] && (ST || G.T[0] % 4 == 0);
     // t < 7 * 66^2 * 17 < 2^21: exact quotients from float reciprocals
     const float inch = 1.0f / (float)nch, inrow = 1.0f / (float)nrow;
     for (int t = threadIdx.x; t < nf * nrow * nch; t += blockDim.x) {
-        const int tq = div_small(t, inch);
-        const int q = t - tq * nch;
-        const int f = div_small(tq, inrow);
-        const int r = tq - f * nrow;
-        const int wz = div_small(r, G.inv_w[1]);
-        const int wy = r - wz * W1;
+        int q, f, wy, wz;
+        if constexpr (ST) {
+            const unsigned tq = (unsigned)t / SNCH, r = tq % (SW1 * SW2);
+            q = (int)((unsigned)t - tq * SNCH);
+            f = (int)(tq / (SW1 * SW2));
+            wz = (int)(r / SW1);
+            wy = (int)(r - (unsigned)wz * SW1);
+        } else {
+            const int tq = div_small(t, inch);
+            q = t - tq * nch;
+            f = div_small(tq, inrow);
+            const int r = tq - f * nrow;
+            wz = div_small(r, G.inv_w[1]);
+            wy = r - wz * W1;
+        }
         int iy = so[1] + wy, iz = D == 3 ? so[2] + wz : 0;
         if (G.per[1]) {
             iy -= (P == 2 ? 1 : 0);
@@ -200,160 +219,223 @@ constexpr int kP2GThreads = 64;
 
 // 3D span columns: a lane walks the spans of one (x, y) column along z (rows
 // of 32 spans are z-major in a tile).  Its sums hold the three node layers of
-// the current span; after each span the lowest layer is complete, goes into
-// the window, and the two others move down.  GROUP 0 sums {m, mv_x, mv_y,
-// mv_z}, GROUP 1 {f_x, f_y, f_z}.
-template <int P, bool PER, int GROUP>
+// the current span; after each span the lowest layer is complete and goes
+// into the window, the two others become the lower layers of the next span
+// and the completed one, cleared, its top layer.  The layers rotate through
+// NS register slots: layer c of span z is slot (z + c) mod NS, and the walk
+// is unrolled by NS spans so that every slot index is a constant (no sums
+// move between registers).  GROUP 0 sums {m, mv_x, mv_y, mv_z}, GROUP 1
+// {f_x, f_y, f_z}.  TX, TY, TZ > 0: the tile edges as compile-time constants
+// (window offsets become immediates); 0: read from the geometry.
+__host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v >> 1); }
+
+template <int P, int GROUP>
+struct ZcolSums {
+    static constexpr int NS = P + 1, L = NS * NS;
+    // GROUP 0: qa = {m, mv_x}, qb = {mv_y, mv_z}; GROUP 1: qa = {f_y, f_z}, qc = f_x
+    float2 qa[NS][L];
+    float2 qb[GROUP == 0 ? NS : 1][GROUP == 0 ? L : 1];
+    float qc[GROUP == 0 ? 1 : NS][GROUP == 0 ? 1 : L];
+    __device__ __forceinline__ void clear(int s)
+    {
+#pragma unroll
+        for (int n = 0; n < L; ++n) {
+            qa[s][n] = f2(0.f, 0.f);
+            if constexpr (GROUP == 0) qb[s][n] = f2(0.f, 0.f); else qc[s][n] = 0.f;
+        }
+    }
+};
+
+// One span of a column: its particles into the sums (slot rotation U), then
+// the completed layers into the window.  Returns whether it was the
+// column's last span.
+template <int U, int P, bool PER, int GROUP, int TX, int TY, int TZ>
+__device__ __forceinline__ bool zcol_span(const Geom& G, const Particles<float>& pt, const uint32_t* __restrict__ cs,
+                                          int64_t kb, const int so[3], const float lo[3], const float nper[3],
+                                          float ih, float gm1, float* sm, int lane, int yb, int rpl, int z, int nz,
+                                          ZcolSums<P, GROUP>& S)
+{
+    constexpr int NS = P + 1;
+    constexpr bool ST = TX > 0;
+    const int T0 = ST ? TX : G.T[0], T1 = ST ? TY : G.T[1];
+    const int sh0 = ST ? clog2(TX) : G.tsh[0];
+    const int W0 = ST ? TX + P : G.W[0], W1 = ST ? TY + P : G.W[1];
+    const int W = ST ? (TX + P) * (TY + P) * (TZ + P) : G.Wvol;
+    // a warp row of 32 spans: for tiles narrower than 32 spans, the y-rows
+    // yb, yb + rpl, .. of the z-layer (lanes of different rows are rpl rows
+    // apart); otherwise 32 consecutive spans of one x-row
+    int lx, ly;
+    if (T0 >= 32) {
+        const int s0 = ((z * rpl + yb) << 5) + lane;
+        lx = s0 & (T0 - 1);
+        ly = (s0 >> sh0) & (T1 - 1);
+    } else {
+        lx = lane & (T0 - 1);
+        ly = (lane >> sh0) * rpl + yb;
+    }
+    const int s = ((z * T1 + ly) << sh0) + lx;
+    const uint32_t b = cs[kb + s], e = cs[kb + s + 1];
+    const int base = (z * W1 + ly) * W0 + lx;
+    const float cb0 = (float)(so[0] + lx - (P == 2 ? 1 : 0));
+    const float cb1 = (float)(so[1] + ly - (P == 2 ? 1 : 0));
+    const float cb2 = (float)(so[2] + z - (P == 2 ? 1 : 0));
+    if constexpr (GROUP == 0) {
+        float nx[3] = {0.f, 0.f, 0.f}, nv[3] = {0.f, 0.f, 0.f}, nM = 0.f;
+        if (b < e) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { nx[a] = pt.x[a][b]; nv[a] = pt.v[a][b]; }
+            nM = pt.M[b];
+        }
+        for (uint32_t k = b; k < e; ++k) {
+            float x[3], v[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { x[a] = nx[a]; v[a] = nv[a]; }
+            const float M = nM;
+            if (k + 1 < e) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) { nx[a] = pt.x[a][k + 1]; nv[a] = pt.v[a][k + 1]; }
+                nM = pt.M[k + 1];
+            }
+            float w[3][3], dw[3][3];
+            axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
+            axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+            axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
+            float2 c0[NS], c1[NS];
+            const float mv0 = M * v[0], mv1 = M * v[1], mv2 = M * v[2];
+#pragma unroll
+            for (int a = 0; a < NS; ++a) {
+                const float wa = w[0][a];
+                c0[a] = f2(M * wa, mv0 * wa);
+                c1[a] = f2(mv1 * wa, mv2 * wa);
+            }
+#pragma unroll
+            for (int c = 0; c < NS; ++c) {
+#pragma unroll
+                for (int bb = 0; bb < NS; ++bb) {
+                    const float yz = w[1][bb] * w[2][c];
+                    const float2 yy = f2(yz, yz);
+                    const int sl = (U + c) % NS;
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) {
+                        S.qa[sl][bb * NS + a] = __ffma2_rn(c0[a], yy, S.qa[sl][bb * NS + a]);
+                        S.qb[sl][bb * NS + a] = __ffma2_rn(c1[a], yy, S.qb[sl][bb * NS + a]);
+                    }
+                }
+            }
+        }
+    } else {
+        float nx[3] = {0.f, 0.f, 0.f}, nM = 0.f, nr = 1.f, nE = 0.f, nQ = 0.f;
+        if (b < e) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) nx[a] = pt.x[a][b];
+            nM = pt.M[b]; nr = pt.rho[b]; nE = pt.E[b]; nQ = pt.Q[b];
+        }
+        for (uint32_t k = b; k < e; ++k) {
+            float x[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) x[a] = nx[a];
+            const float M = nM, rho = nr, E = nE, Q = nQ;
+            if (k + 1 < e) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) nx[a] = pt.x[a][k + 1];
+                nM = pt.M[k + 1]; nr = pt.rho[k + 1]; nE = pt.E[k + 1]; nQ = pt.Q[k + 1];
+            }
+            float w[3][3], dw[3][3];
+            axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
+            axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+            axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
+            const float F = fmaf(gm1 * rho, E, Q) * __fdividef(M, rho) * ih;
+            float Fx[NS], Fd[NS];
+#pragma unroll
+            for (int a = 0; a < NS; ++a) { Fx[a] = F * w[0][a]; Fd[a] = F * dw[0][a]; }
+#pragma unroll
+            for (int c = 0; c < NS; ++c) {
+#pragma unroll
+                for (int bb = 0; bb < NS; ++bb) {
+                    const float yz = w[1][bb] * w[2][c];
+                    const float2 dd = f2(dw[1][bb] * w[2][c], w[1][bb] * dw[2][c]);
+                    const int sl = (U + c) % NS;
+#pragma unroll
+                    for (int a = 0; a < NS; ++a) {
+                        S.qa[sl][bb * NS + a] = __ffma2_rn(f2(Fx[a], Fx[a]), dd, S.qa[sl][bb * NS + a]);
+                        S.qc[sl][bb * NS + a] = fmaf(Fd[a], yz, S.qc[sl][bb * NS + a]);
+                    }
+                }
+            }
+        }
+    }
+    // the completed node layers (the lowest, or all three after the column's
+    // last span) go into the window in phases: in phase (a, g) lane (lx, ly)
+    // adds its sums of the nodes (lx + a, ly + bb) with bb / ystep = g.  Lanes
+    // of one y-row then write different nodes; lanes of two y-rows (rpl rows
+    // apart, or adjacent when a warp row is one x-row) can meet only when
+    // their bb differ by a multiple of that distance, which never happens
+    // within one group.  A warp barrier separates the phases.
+    const bool last = z + 1 == nz;
+    float* sp = sm + base;
+    const int ystep = T0 >= 32 ? NS : rpl;
+#pragma unroll
+    for (int a = 0; a < NS; ++a) {
+#pragma unroll
+        for (int g = 0; g < NS; ++g) {
+            if (g * ystep >= NS) break;
+            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < NS; ++c) {
+                if (c > 0 && !last) break;
+                const int sl = (U + c) % NS;
+#pragma unroll
+                for (int bb = 0; bb < NS; ++bb) {
+                    if (bb / ystep != g) continue;
+                    const int n = bb * NS + a;
+                    float* r = sp + (c * W1 + bb) * W0 + a;
+                    if constexpr (GROUP == 0) {
+                        r[0] += S.qa[sl][n].x;
+                        r[W] += S.qa[sl][n].y;
+                        r[2 * W] += S.qb[sl][n].x;
+                        r[3 * W] += S.qb[sl][n].y;
+                    } else {
+                        r[4 * W] += S.qc[sl][n];          // f_x
+                        r[5 * W] += S.qa[sl][n].x;        // f_y
+                        r[6 * W] += S.qa[sl][n].y;        // f_z
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (!last) S.clear(U % NS);
+    return last;
+}
+
+template <int P, bool PER, int GROUP, int TX, int TY, int TZ>
 __device__ __forceinline__ void p2g_zcol(const Geom& G, const Particles<float>& pt, const uint32_t* __restrict__ cs,
                                          int64_t kb, const int so[3], const float lo[3], const float nper[3],
                                          float ih, float gm1, float* sm, int lane)
 {
-    constexpr int NS = P + 1, NYZ = NS * NS, NN = NYZ * NS, L = NS * NS;
-    const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
-    const int rpl = (G.T[0] * G.T[1]) >> 5;
+    constexpr int NS = P + 1;
+    constexpr bool ST = TX > 0;
+    const int T0 = ST ? TX : G.T[0], T1 = ST ? TY : G.T[1], T2 = ST ? TZ : G.T[2];
+    const int sh0 = ST ? clog2(TX) : G.tsh[0];
+    const int rpl = (T0 * T1) >> 5;
     // spans beyond the last one of an axis hold no particles: a tile at the
     // domain's end walks only its real z-layers and rows
-    const int nz = min(G.T[2], G.S[2] - so[2]);
+    const int nz = min(T2, G.S[2] - so[2]);
     for (int yb = 0; yb < rpl; ++yb) {
-        const int r0 = yb << 5;     // first span of the row in its z-layer
-        if (so[1] + (r0 >> G.tsh[0]) >= G.S[1] || so[0] + (r0 & (G.T[0] - 1)) >= G.S[0]) continue;
-        // GROUP 0: qa = {m, mv_x}, qb = {mv_y, mv_z}; GROUP 1: qa = {f_y, f_z}, qc = f_x
-        float2 qa[NN], qb[GROUP == 0 ? NN : 1];
-        float qc[GROUP == 0 ? 1 : NN];
+        // the warp row's first span in its z-layer (its lowest y-row)
+        const int r0 = T0 >= 32 ? yb << 5 : yb << sh0;
+        if (so[1] + (r0 >> sh0) >= G.S[1] || so[0] + (r0 & (T0 - 1)) >= G.S[0]) continue;
+        ZcolSums<P, GROUP> S;
 #pragma unroll
-        for (int i = 0; i < NN; ++i) {
-            qa[i] = f2(0.f, 0.f);
-            if (GROUP == 0) qb[i] = f2(0.f, 0.f); else qc[i] = 0.f;
-        }
-        for (int z = 0; z < nz; ++z) {
-            const int s = ((z * rpl + yb) << 5) + lane;
-            const uint32_t b = cs[kb + s], e = cs[kb + s + 1];
-            const int lx = s & (G.T[0] - 1);
-            const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
-            const int base = (z * W1 + ly) * W0 + lx;
-            const float cb0 = (float)(so[0] + lx - (P == 2 ? 1 : 0));
-            const float cb1 = (float)(so[1] + ly - (P == 2 ? 1 : 0));
-            const float cb2 = (float)(so[2] + z - (P == 2 ? 1 : 0));
-            if (GROUP == 0) {
-                float nx[3] = {0.f, 0.f, 0.f}, nv[3] = {0.f, 0.f, 0.f}, nM = 0.f;
-                if (b < e) {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) { nx[a] = pt.x[a][b]; nv[a] = pt.v[a][b]; }
-                    nM = pt.M[b];
-                }
-                for (uint32_t k = b; k < e; ++k) {
-                    float x[3], v[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) { x[a] = nx[a]; v[a] = nv[a]; }
-                    const float M = nM;
-                    if (k + 1 < e) {
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) { nx[a] = pt.x[a][k + 1]; nv[a] = pt.v[a][k + 1]; }
-                        nM = pt.M[k + 1];
-                    }
-                    float w[3][3], dw[3][3];
-                    axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
-                    axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
-                    axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
-                    float2 c0[NS], c1[NS];
-                    const float mv0 = M * v[0], mv1 = M * v[1], mv2 = M * v[2];
-#pragma unroll
-                    for (int a = 0; a < NS; ++a) {
-                        const float wa = w[0][a];
-                        c0[a] = f2(M * wa, mv0 * wa);
-                        c1[a] = f2(mv1 * wa, mv2 * wa);
-                    }
-#pragma unroll
-                    for (int j = 0; j < NYZ; ++j) {
-                        const float yz = w[1][j % NS] * w[2][j / NS];
-                        const float2 yy = f2(yz, yz);
-#pragma unroll
-                        for (int a = 0; a < NS; ++a) {
-                            const int i = j * NS + a;
-                            qa[i] = __ffma2_rn(c0[a], yy, qa[i]);
-                            if (GROUP == 0) qb[i] = __ffma2_rn(c1[a], yy, qb[i]);
-                        }
-                    }
-                }
-            } else {
-                float nx[3] = {0.f, 0.f, 0.f}, nM = 0.f, nr = 1.f, nE = 0.f, nQ = 0.f;
-                if (b < e) {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) nx[a] = pt.x[a][b];
-                    nM = pt.M[b]; nr = pt.rho[b]; nE = pt.E[b]; nQ = pt.Q[b];
-                }
-                for (uint32_t k = b; k < e; ++k) {
-                    float x[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) x[a] = nx[a];
-                    const float M = nM, rho = nr, E = nE, Q = nQ;
-                    if (k + 1 < e) {
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) nx[a] = pt.x[a][k + 1];
-                        nM = pt.M[k + 1]; nr = pt.rho[k + 1]; nE = pt.E[k + 1]; nQ = pt.Q[k + 1];
-                    }
-                    float w[3][3], dw[3][3];
-                    axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
-                    axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
-                    axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
-                    const float F = fmaf(gm1 * rho, E, Q) * __fdividef(M, rho) * ih;
-                    float Fx[NS], Fd[NS];
-#pragma unroll
-                    for (int a = 0; a < NS; ++a) { Fx[a] = F * w[0][a]; Fd[a] = F * dw[0][a]; }
-#pragma unroll
-                    for (int j = 0; j < NYZ; ++j) {
-                        const int bb = j % NS, c = j / NS;
-                        const float yz = w[1][bb] * w[2][c];
-                        const float2 dd = f2(dw[1][bb] * w[2][c], w[1][bb] * dw[2][c]);
-#pragma unroll
-                        for (int a = 0; a < NS; ++a) {
-                            const int i = j * NS + a;
-                            qa[i] = __ffma2_rn(f2(Fx[a], Fx[a]), dd, qa[i]);
-                            if (GROUP == 1) qc[i] = fmaf(Fd[a], yz, qc[i]);
-                        }
-                    }
-                }
-            }
-            // the completed node layers (the lowest, or all three after the
-            // column's last span) go into the window in NS phases: in phase a
-            // lane lx adds its sums of node lx + a of each row, so the lanes
-            // of a phase write different nodes
-            const bool last = z + 1 == nz;
-            float* sp = sm + base;
-#pragma unroll
-            for (int a = 0; a < NS; ++a) {
-                __syncwarp();
-#pragma unroll
-                for (int c = 0; c < NS; ++c) {
-                    if (c > 0 && !last) break;
-#pragma unroll
-                    for (int bb = 0; bb < NS; ++bb) {
-                        const int i = (c * NS + bb) * NS + a;
-                        float* r = sp + (c * W1 + bb) * W0 + a;
-                        if (GROUP == 0) {
-                            r[0] += qa[i].x;
-                            r[W] += qa[i].y;
-                            r[2 * W] += qb[i].x;
-                            r[3 * W] += qb[i].y;
-                        } else {
-                            r[4 * W] += qc[i];          // f_x
-                            r[5 * W] += qa[i].x;        // f_y
-                            r[6 * W] += qa[i].y;        // f_z
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-            if (last) break;
-#pragma unroll
-            for (int i = 0; i < NN; ++i) {
-                if (i + L < NN) {
-                    qa[i] = qa[i + L];
-                    if (GROUP == 0) qb[i] = qb[i + L]; else qc[i] = qc[i + L];
-                } else {
-                    qa[i] = f2(0.f, 0.f);
-                    if (GROUP == 0) qb[i] = f2(0.f, 0.f); else qc[i] = 0.f;
-                }
+        for (int sl = 0; sl < NS; ++sl) S.clear(sl);
+        for (int z = 0; z < nz; z += NS) {
+            if (zcol_span<0, P, PER, GROUP, TX, TY, TZ>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane, yb, rpl, z,
+                                                       nz, S)) break;
+            if (zcol_span<1, P, PER, GROUP, TX, TY, TZ>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane, yb, rpl,
+                                                       z + 1, nz, S)) break;
+            if constexpr (NS == 3) {
+                if (zcol_span<2, P, PER, GROUP, TX, TY, TZ>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane, yb,
+                                                           rpl, z + 2, nz, S)) break;
             }
         }
     }
@@ -509,16 +591,20 @@ __host__ __device__ inline bool p2g_columns(const Geom& G)
 // COL: 3D tiles whose z-layers hold whole rows of 32 spans walk span columns
 // (p2g_zcol); the others walk rows.  Separate instantiations keep each
 // kernel's registers to its own path.
-template <int D, int P, bool PER, bool COL>
+// TX, TY, TZ > 0 (3D span columns only): the tile edges as compile-time
+// constants.
+template <int D, int P, bool PER, bool COL, int TX = 0, int TY = 0, int TZ = 0>
 __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<float>& pt, const FieldPtrs& out,
                                               const uint32_t* __restrict__ cs, Clock* clk, const int tile)
 {
     if (!clk->active) return;
+    constexpr bool ST = TX > 0;
+    static_assert(!ST || (D == 3 && COL), "static tiles: 3D span columns");
     const int64_t kb = tile_cs0(G, tile);
-    if (cs[kb] == cs[kb + G.Tvol]) return;
+    if (cs[kb] == cs[kb + (ST ? TX * TY * TZ : G.Tvol)]) return;
     extern __shared__ __align__(16) float sm[];
     constexpr int NS = P + 1, NF = 1 + 2 * D, NYZ = (D == 3) ? NS * NS : NS, NN = NYZ * NS;
-    const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
+    const int W = ST ? (TX + P) * (TY + P) * (TZ + P) : G.Wvol, W0 = G.W[0], W1 = G.W[1];
     for (int i = threadIdx.x; i < (NF * W) >> 2; i += blockDim.x)
         reinterpret_cast<float4*>(sm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = ((NF * W) & ~3) + threadIdx.x; i < NF * W; i += blockDim.x) sm[i] = 0.f;
@@ -536,14 +622,14 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
     const int group = warp & 1;
     if constexpr (COL) {
         if constexpr (D == 3) {
-            if (group == 0) p2g_zcol<P, PER, 0>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
-            else p2g_zcol<P, PER, 1>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
+            if (group == 0) p2g_zcol<P, PER, 0, TX, TY, TZ>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
+            else p2g_zcol<P, PER, 1, TX, TY, TZ>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
         } else {
             if (group == 0) p2g_ycol<P, PER, 0>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
             else p2g_ycol<P, PER, 1>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane);
         }
         __syncthreads();
-        flush_window<D, P>(G, so, sm, NF, out);
+        flush_window<D, P, TX, TY, TZ>(G, so, sm, NF, out);
         return;
     }
     const int nrows = G.Tvol >> 5;
@@ -714,12 +800,23 @@ __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<flo
 
 // tiles: the tiles of one colour pass (block b runs tiles[b]), or NULL (block
 // b runs tile b)
-template <int D, int P, bool PER, bool COL>
+template <int D, int P, bool PER, bool COL, int TX = 0, int TY = 0, int TZ = 0>
 __global__ void __launch_bounds__(kP2GThreads, 6) k_p2g_span(Geom G, TileState<float> ts, FieldPtrs out, Clock* clk,
                                                               const uint32_t* __restrict__ tiles)
 {
     const int t = tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x;
-    p2g_span_tile<D, P, PER, COL>(G, ts.pt, out, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
+    p2g_span_tile<D, P, PER, COL, TX, TY, TZ>(G, ts.pt, out, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
+}
+
+// Tile shapes with compile-time variants of the 3D degree-2 FP32 span
+// kernels: 1 = 8 x 8 x 8 spans, 2 = 16 x 8 x 4; 0 = none (edges read from the
+// geometry).
+__host__ __device__ inline int static_tile(const Geom& G)
+{
+    if (G.dim != 3 || G.p != 2) return 0;
+    if (G.T[0] == 8 && G.T[1] == 8 && G.T[2] == 8) return 1;
+    if (G.T[0] == 16 && G.T[1] == 8 && G.T[2] == 4) return 2;
+    return 0;
 }
 
 // ------------------------------- 2D span-per-lane kernels, 64-bit sums
@@ -1237,15 +1334,23 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
             }
         }
         if (c.hi == c.re) {
-            // the row is complete: node lx + a of each window row gets acc of
-            // span lx, in NS phases (each lane a different node in a phase)
+            // the row is complete: node (lx + a, ly + bb) of each window layer
+            // gets acc of span (lx, ly), in NS x NS phases (a, bb).  A row of
+            // 32 spans may cover several y-rows of the tile, and lanes
+            // (lx, ly) and (lx, ly + 1) add to the same node in phases (a, 1)
+            // and (a, 0): the warp barrier between phases orders them
 #pragma unroll
             for (int a = 0; a < NS; ++a) {
-                __syncwarp();
 #pragma unroll
-                for (int jj = 0; jj < NYZ; ++jj)
-                    s2d[base + ((D == 3 ? jj / NS : 0) * W1 + (D == 3 ? jj % NS : jj)) * W0 + a] +=
-                        (ODD && jj == NYZ - 1) ? accT[a] : ((jj & 1) ? accP[jj >> 1][a].y : accP[jj >> 1][a].x);
+                for (int bb = 0; bb < (D == 3 ? NS : NYZ); ++bb) {
+                    __syncwarp();
+#pragma unroll
+                    for (int c = 0; c < (D == 3 ? NS : 1); ++c) {
+                        const int jj = D == 3 ? c * NS + bb : bb;
+                        s2d[base + (c * W1 + bb) * W0 + a] +=
+                            (ODD && jj == NYZ - 1) ? accT[a] : ((jj & 1) ? accP[jj >> 1][a].y : accP[jj >> 1][a].x);
+                    }
+                }
             }
             __syncwarp();
         }

@@ -141,6 +141,10 @@ P2G_CASES = [
     # not span columns), and exactly 32 (two-span columns, 8-span x-rows)
     (3, 2, [13, 11, 9], ["wall"] * 6, (4, 4, 8)),
     (3, 2, [20, 12, 10], ["periodic"] * 2 + ["wall"] * 4, (8, 4, 2)),
+    # 8 x 8 x 8 tiles: the FP32 P2G with compile-time tile edges, ragged in
+    # every axis (the last z-tile walks one or two spans), periodic and walls
+    (3, 2, [21, 13, 9], ["periodic"] * 2 + ["wall"] * 4, (8, 8, 8)),
+    (3, 2, [17, 24, 26], ["wall"] * 4 + ["periodic"] * 2, (8, 8, 8)),
 ]
 
 
@@ -358,9 +362,10 @@ def test_span_kernel_cylinder_matches_oracle(precision, steps, tol):
     g.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32_coloured"])
-def test_fp32_blast_3d_100_steps_within_target(precision):
-    p = f32(I.blast(n=16, precision=precision))
+@pytest.mark.parametrize("precision,tile", [("fp32", [0, 0, 0]), ("fp32_coloured", [0, 0, 0]),
+                                            ("fp32", [8, 8, 8])])
+def test_fp32_blast_3d_100_steps_within_target(precision, tile):
+    p = f32(I.blast(n=16, precision=precision, tile=tile))
     g, o = gpu_sim(p), oracle_sim(p)
     g.step(100)
     o.step(100)
