@@ -293,6 +293,12 @@ struct Impl {
         if constexpr (kFast3) e = allow((const void*)k_g2pd_fast<D, P, A>, smem(G, 2));
         else e = allow((const void*)k_g2pd<D, P, R, A>, smem(G, 2));
         if (e != cudaSuccess) return e;
+        if constexpr (kFast3 && D == 3 && P == 2) {
+            const int shape = static_tile(G);
+            if (shape == 1) e = allow((const void*)k_g2pd_fast<3, 2, A, 8, 8, 8>, smem(G, 2));
+            if (shape == 2) e = allow((const void*)k_g2pd_fast<3, 2, A, 16, 8, 4>, smem(G, 2));
+            if (e != cudaSuccess) return e;
+        }
         if constexpr (kFast) {
             const void* f[6] = {(const void*)k_p2g_span<D, P, true, true>, (const void*)k_p2g_span<D, P, false, true>,
                                 (const void*)k_p2g_span<D, P, true, false>, (const void*)k_p2g_span<D, P, false, false>,
@@ -301,13 +307,17 @@ struct Impl {
             for (int i = 0; i < 6; ++i)
                 if ((e = allow(f[i], z[i])) != cudaSuccess) return e;
             if constexpr (D == 3 && P == 2) {
-                const void* g[4] = {(const void*)k_p2g_span<3, 2, true, true, 8, 8, 8>,
+                const void* g[8] = {(const void*)k_p2g_span<3, 2, true, true, 8, 8, 8>,
                                     (const void*)k_p2g_span<3, 2, false, true, 8, 8, 8>,
+                                    (const void*)k_grid_g2p_span<3, 2, true, 8, 8, 8>,
+                                    (const void*)k_grid_g2p_span<3, 2, false, 8, 8, 8>,
                                     (const void*)k_p2g_span<3, 2, true, true, 16, 8, 4>,
-                                    (const void*)k_p2g_span<3, 2, false, true, 16, 8, 4>};
+                                    (const void*)k_p2g_span<3, 2, false, true, 16, 8, 4>,
+                                    (const void*)k_grid_g2p_span<3, 2, true, 16, 8, 4>,
+                                    (const void*)k_grid_g2p_span<3, 2, false, 16, 8, 4>};
                 const int st = static_tile(G);
-                for (int i = 0; i < 2 && st > 0; ++i)
-                    if ((e = allow(g[2 * (st - 1) + i], smem(G, 0))) != cudaSuccess) return e;
+                for (int i = 0; i < 4 && st > 0; ++i)
+                    if ((e = allow(g[4 * (st - 1) + i], smem(G, i < 2 ? 0 : 1))) != cudaSuccess) return e;
             }
             return cudaSuccess;
         } else {
@@ -371,6 +381,20 @@ struct Impl {
                     const uint32_t* tl = colour_tiles(s, c);
                     const unsigned nb = colour_blocks(s, c);
                     if (nb == 0) continue;
+                    if constexpr (D == 3 && P == 2) {
+                        // compile-time tile edges for the common shapes
+                        const int shape = static_tile(G);
+                        const unsigned nt = K2Cfg<3>::kThreads;
+                        if (shape == 1 && per)
+                            k_grid_g2p_span<3, 2, true, 8, 8, 8><<<nb, nt, smem(G, 1), st>>>(G, ts, gr, o, s->clk, tl);
+                        else if (shape == 1)
+                            k_grid_g2p_span<3, 2, false, 8, 8, 8><<<nb, nt, smem(G, 1), st>>>(G, ts, gr, o, s->clk, tl);
+                        else if (shape == 2 && per)
+                            k_grid_g2p_span<3, 2, true, 16, 8, 4><<<nb, nt, smem(G, 1), st>>>(G, ts, gr, o, s->clk, tl);
+                        else if (shape == 2)
+                            k_grid_g2p_span<3, 2, false, 16, 8, 4><<<nb, nt, smem(G, 1), st>>>(G, ts, gr, o, s->clk, tl);
+                        if (shape > 0) continue;
+                    }
                     if (per)
                         k_grid_g2p_span<D, P, true><<<nb, K2Cfg<D>::kThreads, smem(G, 1), st>>>(G, ts, gr, o, s->clk,
                                                                                                 tl);
@@ -387,10 +411,21 @@ struct Impl {
             s->launches += 1;
         }
         if (which & 4) {
-            if constexpr (kFast3)
-                k_g2pd_fast<D, P, A><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
-            else
-                k_g2pd<D, P, R, A><<<G.ntiles, kThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
+            int shape = 0;
+            if constexpr (kFast3 && D == 3 && P == 2) {
+                // compile-time tile edges for the common shapes
+                shape = static_tile(G);
+                if (shape == 1)
+                    k_g2pd_fast<3, 2, A, 8, 8, 8><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
+                else if (shape == 2)
+                    k_g2pd_fast<3, 2, A, 16, 8, 4><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
+            }
+            if (shape == 0) {
+                if constexpr (kFast3)
+                    k_g2pd_fast<D, P, A><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
+                else
+                    k_g2pd<D, P, R, A><<<G.ntiles, kThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
+            }
             s->launches += 1;
         }
     }

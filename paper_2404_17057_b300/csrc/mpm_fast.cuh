@@ -1178,22 +1178,29 @@ __device__ __forceinline__ void k2_stage(const RowChunk& c, const Particles<floa
     }
 }
 
-template <int D, int P, bool PER>
+// TX, TY, TZ > 0 (3D): the tile edges as compile-time constants.
+template <int D, int P, bool PER, int TX = 0, int TY = 0, int TZ = 0>
 __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particles<float>& pt,
                                                    const Grid<float, float>& gr, const FieldPtrs& out,
                                                    const uint32_t* __restrict__ cs, Clock* clk, const int tile)
 {
     typedef K2Cfg<D> C;
+    constexpr bool ST = TX > 0;
+    static_assert(!ST || D == 3, "static tiles: 3D");
     if (!clk->active) return;
+    const int Tvol = ST ? TX * TY * TZ : G.Tvol;
     const int64_t kb = tile_cs0(G, tile);
-    if (cs[kb] == cs[kb + G.Tvol]) return;
+    if (cs[kb] == cs[kb + Tvol]) return;
     extern __shared__ __align__(16) float sm[];
     constexpr int NS = P + 1, NYZ = (D == 3) ? NS * NS : NS;
-    const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
+    const int W = ST ? (TX + P) * (TY + P) * (TZ + P) : G.Wvol;
+    const int W0 = ST ? TX + P : G.W[0], W1 = ST ? TY + P : G.W[1];
+    const int T0 = ST ? TX : G.T[0], T1 = ST ? TY : G.T[1];
+    const int sh0 = ST ? clog2(TX) : G.tsh[0], sh1 = ST ? clog2(TY) : G.tsh[1];
     float* stage = sm;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + C::kStageFloats);
     uint32_t* tcs = reinterpret_cast<uint32_t*>(sm + C::kHeadFloats);
-    float* sA = sm + C::kHeadFloats + tile_cs_words(G);     // D x W: f/m after BC
+    float* sA = sm + C::kHeadFloats + ((Tvol + 1 + 3) & ~3);  // D x W: f/m after BC
     float* s2 = sA + D * W;                                  // D x W: momentum P2G
     int so[3];
     tile_origin(G, tile, so);
@@ -1201,7 +1208,7 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
     const bool bc = window_has_bc(G, gr.mask, so);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         int idx[3];
-        const int64_t node = slot_node<P>(G, so, i, idx);
+        const int64_t node = slot_node<P, TX, TY>(G, so, i, idx);
         float f[3] = {0.f, 0.f, 0.f}, m = 0.f;
         if (node >= 0) {
             m = gr.m[node];
@@ -1216,7 +1223,7 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
             s2[a * W + i] = 0.f;
         }
     }
-    for (int i = threadIdx.x; i <= G.Tvol; i += blockDim.x) tcs[i] = cs[kb + i];
+    for (int i = threadIdx.x; i <= Tvol; i += blockDim.x) tcs[i] = cs[kb + i];
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < C::kStages; ++q) mbar_init(bar + q, 1);
@@ -1224,7 +1231,7 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nrows = G.Tvol >> 5;
+    const int nrows = Tvol >> 5;
     const bool producer = threadIdx.x == 0;
     const float ih = (float)G.inv_h;
     float lo[3], nper[3];
@@ -1267,9 +1274,9 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
             const int s = (c.r << 5) + lane;
             sb = tcs[s];
             se = tcs[s + 1];
-            const int lx = s & (G.T[0] - 1);
-            const int ly = (s >> G.tsh[0]) & (G.T[1] - 1);
-            const int lz = s >> (G.tsh[0] + G.tsh[1]);
+            const int lx = s & (T0 - 1);
+            const int ly = (s >> sh0) & (T1 - 1);
+            const int lz = s >> (sh0 + sh1);
             base = (lz * W1 + ly) * W0 + lx;
             cb[0] = (float)(so[0] + lx - (P == 2 ? 1 : 0));
             cb[1] = (float)(so[1] + ly - (P == 2 ? 1 : 0));
@@ -1389,17 +1396,17 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
     if (fail) atomicOr(&clk->err, ERR_TIMEOUT);
     __syncthreads();
     if (fail) return;
-    flush_window<D, P>(G, so, s2, D, out);
+    flush_window<D, P, TX, TY, TZ>(G, so, s2, D, out);
 }
 
-template <int D, int P, bool PER>
+template <int D, int P, bool PER, int TX = 0, int TY = 0, int TZ = 0>
 __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 5) k_grid_g2p_span(Geom G, TileState<float> ts,
                                                                          Grid<float, float> gr, FieldPtrs out,
                                                                          Clock* clk,
                                                                          const uint32_t* __restrict__ tiles)
 {
     const int t = tiles ? (int)tiles[blockIdx.x] : (int)blockIdx.x;
-    grid_g2p_span_tile<D, P, PER>(G, ts.pt, gr, out, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
+    grid_g2p_span_tile<D, P, PER, TX, TY, TZ>(G, ts.pt, gr, out, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, t);
 }
 
 // ------------------------------- K3: G2PD + particle update + move + key
@@ -1412,26 +1419,32 @@ template <int D>
 constexpr int g2pd_blocks() { return D == 3 ? 4 : 5; }
 
 // A: grid accumulator type (float, or int64 fixed point read back as float).
-template <int D, int P, class A>
+// TX, TY, TZ > 0 (3D): the tile edges as compile-time constants.
+template <int D, int P, class A, int TX = 0, int TY = 0, int TZ = 0>
 __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<float>& pt, const Grid<A, float>& gr,
                                                const uint32_t* __restrict__ cs, Clock* clk, const Reorder& ro,
                                                const int tile)
 {
+    constexpr bool ST = TX > 0;
+    static_assert(!ST || D == 3, "static tiles: 3D");
     if (!clk->active) return;
     const uint32_t beg = cs[tile_cs0(G, tile)];
-    const uint32_t end = cs[tile_cs0(G, tile) + G.Tvol];
+    const uint32_t end = cs[tile_cs0(G, tile) + (ST ? TX * TY * TZ : G.Tvol)];
     if (beg == end) return;
     // per node: 3D {Vb_x, Vb_y, Vb_z, V2_y} + {V2_x, V2_z}; 2D {Vb_x, Vb_y, V2_x, V2_y}
     extern __shared__ __align__(16) float4 sn[];
     constexpr int NS = P + 1;
-    const int W = G.Wvol, W0 = G.W[0], W1 = G.W[1];
+    const int W = ST ? (TX + P) * (TY + P) * (TZ + P) : G.Wvol;
+    const int W0 = ST ? TX + P : G.W[0], W1 = ST ? TY + P : G.W[1];
+    const int Ta[3] = {ST ? TX : G.T[0], ST ? TY : G.T[1], ST ? TZ : G.T[2]};
+    const int sh0 = ST ? clog2(TX) : G.tsh[0], sh1 = ST ? clog2(TY) : G.tsh[1], sh2 = ST ? clog2(TZ) : G.tsh[2];
     int so[3];
     tile_origin(G, tile, so);
     const float dt = (float)clk->dt_cur;
     const bool bc = window_has_bc(G, gr.mask, so);
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
         int idx[3];
-        const int64_t node = slot_node<P>(G, so, i, idx);
+        const int64_t node = slot_node<P, TX, TY>(G, so, i, idx);
         float mv[3] = {0.f, 0.f, 0.f}, f[3] = {0.f, 0.f, 0.f}, m2[3] = {0.f, 0.f, 0.f}, m = 0.f;
         if (node >= 0) {
             m = Acc<A>::to_real(gr.m[node], G.dqscale[0]);
@@ -1495,13 +1508,13 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
             csp[a] = c;
             weights1d<P>(__fsub_rn(xi, (float)(c - (P == 2 ? 1 : 0))), w[a], dw[a]);
             l[a] = wrap_span(G, a, c) - so[a];
-            ok = ok && l[a] >= 0 && l[a] < G.T[a];
+            ok = ok && l[a] >= 0 && l[a] < Ta[a];
         }
         if (!ok) { err |= ERR_TILE; continue; }
         const int base = (l[2] * W1 + l[1]) * W0 + l[0];
         // the particle's old key (its span in this tile)
-        const uint32_t okey = ((uint32_t)tile << (G.tsh[0] + G.tsh[1] + G.tsh[2])) |
-                              (uint32_t)((((l[2] << G.tsh[1]) + l[1]) << G.tsh[0]) | l[0]);
+        const uint32_t okey = ((uint32_t)tile << (sh0 + sh1 + sh2)) |
+                              (uint32_t)((((l[2] << sh1) + l[1]) << sh0) | l[0]);
         // Vbar = G2P(mv'/m); div V = trace of G2PD(mv2/m), summed x first,
         // then y, then z, two sums per packed FMA
         const float2* sn2 = reinterpret_cast<const float2*>(sn + W);
@@ -1659,12 +1672,12 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
     }
 }
 
-template <int D, int P, class A>
+template <int D, int P, class A, int TX = 0, int TY = 0, int TZ = 0>
 __global__ void __launch_bounds__(kG2PDThreads, g2pd_blocks<D>()) k_g2pd_fast(Geom G, TileState<float> ts,
                                                                          Grid<A, float> gr, Clock* clk, Reorder ro)
 {
     const int t = blockIdx.x;
-    g2pd_fast_tile<D, P, A>(G, ts.pt, gr, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, ro, t);
+    g2pd_fast_tile<D, P, A, TX, TY, TZ>(G, ts.pt, gr, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, ro, t);
 }
 
 }  // namespace mpm

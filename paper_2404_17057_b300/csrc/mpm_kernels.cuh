@@ -359,14 +359,24 @@ __device__ __forceinline__ void tile_origin(const Geom& G, int tile, int so[3])
 __device__ __forceinline__ int div_small(int w, float inv_d) { return (int)(((float)w + 0.5f) * inv_d); }
 
 // Storage index of window slot w of the tile whose first span is so[], or -1.
-template <int P>
+// TX, TY > 0: the tile edges as compile-time constants (slot decoded by
+// integer division by constants).
+template <int P, int TX = 0, int TY = 0>
 __device__ __forceinline__ int64_t slot_node(const Geom& G, const int so[3], int w, int idx[3])
 {
     int ws[3];
-    const int q = div_small(w, G.inv_w[0]);
-    ws[0] = w - q * G.W[0];
-    ws[2] = div_small(q, G.inv_w[1]);
-    ws[1] = q - ws[2] * G.W[1];
+    if constexpr (TX > 0) {
+        constexpr unsigned W0 = TX + P, W1 = TY + P;
+        const unsigned q = (unsigned)w / W0, q2 = q / W1;
+        ws[0] = (int)((unsigned)w - q * W0);
+        ws[2] = (int)q2;
+        ws[1] = (int)(q - q2 * W1);
+    } else {
+        const int q = div_small(w, G.inv_w[0]);
+        ws[0] = w - q * G.W[0];
+        ws[2] = div_small(q, G.inv_w[1]);
+        ws[1] = q - ws[2] * G.W[1];
+    }
     for (int a = 0; a < 3; ++a) {
         if (a >= G.dim) { idx[a] = 0; continue; }
         int i = so[a] + ws[a];
