@@ -1414,9 +1414,10 @@ __global__ void __launch_bounds__(K2Cfg<D>::kThreads, 5) k_grid_g2p_span(Geom G,
 constexpr int kG2PDThreads = 128;
 // resident blocks: in 3D four, 128 registers a thread (five blocks at 96
 // registers spill in the particle loop: 3.41 against 3.32 ms on the 256^3
-// blast); in 2D five (93 registers, no spills)
-template <int D>
-constexpr int g2pd_blocks() { return D == 3 ? 4 : 5; }
+// blast), five for the compile-time tiles, whose constant window offsets fit
+// 96 registers (2.97 against 3.10 ms); in 2D five (93 registers, no spills)
+template <int D, bool ST = false>
+constexpr int g2pd_blocks() { return D == 3 && !ST ? 4 : 5; }
 
 // A: grid accumulator type (float, or int64 fixed point read back as float).
 // TX, TY, TZ > 0 (3D): the tile edges as compile-time constants.
@@ -1673,7 +1674,7 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
 }
 
 template <int D, int P, class A, int TX = 0, int TY = 0, int TZ = 0>
-__global__ void __launch_bounds__(kG2PDThreads, g2pd_blocks<D>()) k_g2pd_fast(Geom G, TileState<float> ts,
+__global__ void __launch_bounds__(kG2PDThreads, g2pd_blocks<D, (TX > 0)>()) k_g2pd_fast(Geom G, TileState<float> ts,
                                                                          Grid<A, float> gr, Clock* clk, Reorder ro)
 {
     const int t = blockIdx.x;
