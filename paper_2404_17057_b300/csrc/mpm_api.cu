@@ -459,21 +459,15 @@ struct Impl {
         k_reorder_done<<<nblk(G.ntiles * 32), kThreads, 0, st>>>(G, a.ro, s->clk, s->tbase, s->tbase_next);
         s->launches += 5;
     }
+    // m, mv[D], f[D] (P2G) and mv2[D] (grid + G2P + P2G) are consecutive
+    // arrays of nnode_p nodes in the grid allocation (grid_view)
     static FieldPtrs p2g_fields(const Grid<A, R>& gr)
     {
-        FieldPtrs o = {};
-        o.p[0] = (float*)gr.m;
-        for (int a = 0; a < D; ++a) {
-            o.p[1 + a] = (float*)gr.mv[a];
-            o.p[1 + D + a] = (float*)gr.f[a];
-        }
-        return o;
+        return FieldPtrs{(float*)gr.m, (int64_t)(gr.mv[0] - gr.m)};
     }
     static FieldPtrs g2p_fields(const Grid<A, R>& gr)
     {
-        FieldPtrs o = {};
-        for (int a = 0; a < D; ++a) o.p[a] = (float*)gr.mv2[a];
-        return o;
+        return FieldPtrs{(float*)gr.mv2[0], (int64_t)(gr.mv2[1] - gr.mv2[0])};
     }
     static void bdesc_fill(const mpm_sim* s, void* out)
     {

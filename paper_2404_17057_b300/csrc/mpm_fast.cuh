@@ -121,8 +121,11 @@ __device__ __forceinline__ void xrow_rmw(T* row, const T* v, int lx, int T0)
     }
 }
 
+// Grid fields a kernel adds into: field f at p0 + f * stride (the fields of
+// one kind are consecutive arrays of one allocation).
 struct FieldPtrs {
-    float* p[7];
+    float* p0;
+    int64_t stride;
 };
 
 // Add a tile's shared-memory window (nf fields of W floats) into global node
@@ -179,7 +182,7 @@ __device__ __forceinline__ void flush_window(const Geom& G, const int so[3], con
             }
         }
         const float* src = sm + f * W + (wz * W1 + wy) * W0;
-        float* row = dst.p[f] + ((int64_t)iz * G.N[1] + iy) * G.pitch;
+        float* row = dst.p0 + f * dst.stride + ((int64_t)iz * G.N[1] + iy) * G.pitch;
         const int x0 = 4 * q;
         if (vec) {
             const int gx = so[0] + x0;
