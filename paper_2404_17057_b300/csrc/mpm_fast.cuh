@@ -223,12 +223,11 @@ constexpr int kP2GThreads = 64;
 // 3D span columns: a lane walks the spans of one (x, y) column along z (rows
 // of 32 spans are z-major in a tile).  Its sums hold the three node layers of
 // the current span; after each span the lowest layer is complete and goes
-// into the window, the two others become the lower layers of the next span
-// and the completed one, cleared, its top layer.  The layers rotate through
-// NS register slots: layer c of span z is slot (z + c) mod NS, and the walk
-// is unrolled by NS spans so that every slot index is a constant (no sums
-// move between registers).  GROUP 0 sums {m, mv_x, mv_y, mv_z}, GROUP 1
-// {f_x, f_y, f_z}.  TX, TY, TZ > 0: the tile edges as compile-time constants
+// into the window, the two others move down and the top one starts at zero.
+// (Rotating the layers through register slots instead of moving them, with
+// the walk unrolled by three spans, was slower: three copies of the particle
+// loop miss the instruction cache.)  GROUP 0 sums {m, mv_x, mv_y, mv_z},
+// GROUP 1 {f_x, f_y, f_z}.  TX, TY, TZ > 0: the tile edges as compile-time constants
 // (window offsets become immediates); 0: read from the geometry.
 __host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v >> 1); }
 
@@ -249,10 +248,10 @@ struct ZcolSums {
     }
 };
 
-// One span of a column: its particles into the sums (slot rotation U), then
-// the completed layers into the window.  Returns whether it was the
+// One span of a column: its particles into the sums (layer c in slot c),
+// then the completed layers into the window.  Returns whether it was the
 // column's last span.
-template <int U, int P, bool PER, int GROUP, int TX, int TY, int TZ>
+template <int P, bool PER, int GROUP, int TX, int TY, int TZ>
 __device__ __forceinline__ bool zcol_span(const Geom& G, const Particles<float>& pt, const uint32_t* __restrict__ cs,
                                           int64_t kb, const int so[3], const float lo[3], const float nper[3],
                                           float ih, float gm1, float* sm, int lane, int yb, int rpl, int z, int nz,
@@ -317,7 +316,7 @@ __device__ __forceinline__ bool zcol_span(const Geom& G, const Particles<float>&
                 for (int bb = 0; bb < NS; ++bb) {
                     const float yz = w[1][bb] * w[2][c];
                     const float2 yy = f2(yz, yz);
-                    const int sl = (U + c) % NS;
+                    const int sl = c;
 #pragma unroll
                     for (int a = 0; a < NS; ++a) {
                         S.qa[sl][bb * NS + a] = __ffma2_rn(c0[a], yy, S.qa[sl][bb * NS + a]);
@@ -357,7 +356,7 @@ __device__ __forceinline__ bool zcol_span(const Geom& G, const Particles<float>&
                 for (int bb = 0; bb < NS; ++bb) {
                     const float yz = w[1][bb] * w[2][c];
                     const float2 dd = f2(dw[1][bb] * w[2][c], w[1][bb] * dw[2][c]);
-                    const int sl = (U + c) % NS;
+                    const int sl = c;
 #pragma unroll
                     for (int a = 0; a < NS; ++a) {
                         S.qa[sl][bb * NS + a] = __ffma2_rn(f2(Fx[a], Fx[a]), dd, S.qa[sl][bb * NS + a]);
@@ -386,7 +385,7 @@ __device__ __forceinline__ bool zcol_span(const Geom& G, const Particles<float>&
 #pragma unroll
             for (int c = 0; c < NS; ++c) {
                 if (c > 0 && !last) break;
-                const int sl = (U + c) % NS;
+                const int sl = c;
 #pragma unroll
                 for (int bb = 0; bb < NS; ++bb) {
                     if (bb / ystep != g) continue;
@@ -407,7 +406,6 @@ __device__ __forceinline__ bool zcol_span(const Geom& G, const Particles<float>&
         }
     }
     __syncwarp();
-    if (!last) S.clear(U % NS);
     return last;
 }
 
@@ -431,15 +429,19 @@ __device__ __forceinline__ void p2g_zcol(const Geom& G, const Particles<float>& 
         ZcolSums<P, GROUP> S;
 #pragma unroll
         for (int sl = 0; sl < NS; ++sl) S.clear(sl);
-        for (int z = 0; z < nz; z += NS) {
-            if (zcol_span<0, P, PER, GROUP, TX, TY, TZ>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane, yb, rpl, z,
-                                                       nz, S)) break;
-            if (zcol_span<1, P, PER, GROUP, TX, TY, TZ>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane, yb, rpl,
-                                                       z + 1, nz, S)) break;
-            if constexpr (NS == 3) {
-                if (zcol_span<2, P, PER, GROUP, TX, TY, TZ>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane, yb,
-                                                           rpl, z + 2, nz, S)) break;
+        for (int z = 0; z < nz; ++z) {
+            if (zcol_span<P, PER, GROUP, TX, TY, TZ>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane, yb, rpl, z, nz,
+                                                    S)) break;
+            // the layers move down; the new top layer starts at zero
+#pragma unroll
+            for (int sl = 0; sl + 1 < NS; ++sl) {
+#pragma unroll
+                for (int n = 0; n < NS * NS; ++n) {
+                    S.qa[sl][n] = S.qa[sl + 1][n];
+                    if constexpr (GROUP == 0) S.qb[sl][n] = S.qb[sl + 1][n]; else S.qc[sl][n] = S.qc[sl + 1][n];
+                }
             }
+            S.clear(NS - 1);
         }
     }
 }
