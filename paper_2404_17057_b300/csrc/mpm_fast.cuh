@@ -1480,7 +1480,9 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
     __syncthreads();
     const float gm1 = (float)(G.gamma - 1.0), gam = (float)G.gamma, ih = (float)G.inv_h, hh = (float)G.h;
     const float c0 = (float)G.c0, c1 = (float)G.c1;
-    float vmax = 0.f, cmax = 0.f;
+    // squares of the largest speeds; sqrt is monotonic and correctly rounded,
+    // so the root of the largest square is the largest root
+    float vmax2 = 0.f, cmax2 = 0.f;
     int err = 0;
     // the next particle's state is loaded while this one is processed
     float px[3] = {0.f, 0.f, 0.f}, prho = 0.f, pE = 0.f, pQ = 0.f;
@@ -1583,11 +1585,12 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
         const float rn = __fdividef(rho, den);
         const float Pn = gm1 * rn * En;
         const float c2 = gam * gm1 * En;       // gamma P / rho with P = (gamma - 1) rho e
-        const float cs = sqrtf(c2 > 0.f ? c2 : 0.f);
+        const float c2p = c2 > 0.f ? c2 : 0.f;
         float Qn = 0.f;
         if (dv < 0.f) {
             // eq. muart: von Neumann-Richtmyer and Landshoff terms, both
             // proportional to the density
+            const float cs = sqrtf(c2p);
             const float t1 = hh * dv;
             Qn = rn * (c0 * t1 * t1 - c1 * hh * cs * dv);
         }
@@ -1595,23 +1598,24 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
         // step ix: move with Vbar; step x: wrap / hold / recycle; new key
         float xn[3] = {0.f, 0.f, 0.f}, vb2 = 0.f;
         int cn[3] = {0, 0, 0};
-        bool out = false, fin = isfinite(En) && isfinite(rn) && isfinite(Qn);
+        bool out = false;
+        // x - x is 0 for a finite x and NaN otherwise
+        float fz = __fadd_rn(__fadd_rn(__fsub_rn(En, En), __fsub_rn(rn, rn)), __fsub_rn(Qn, Qn));
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             xn[a] = __fadd_rn(x[a], __fmul_rn(dt, vb[a]));
             vb2 = fmaf(vb[a], vb[a], vb2);
-            fin = fin && isfinite(xn[a]);
+            fz = __fadd_rn(fz, __fsub_rn(xn[a], xn[a]));
             float xi;
             cn[a] = span_of<float, P>(G, a, xn[a], xi);
-            const int d = cn[a] - csp[a];
-            if (d < -1 || d > 1) err |= ERR_CFL;
+            if ((unsigned)(cn[a] - csp[a] + 1) > 2u) err |= ERR_CFL;    // more than one span
             if (!G.per[a]) {
                 if (xn[a] < (float)G.lo[a] && G.bc[2 * a] == 3) out = true;
                 if (xn[a] >= (float)G.hi[a] && G.bc[2 * a + 1] == 3) out = true;
             }
         }
-        if (!fin) { err |= ERR_NONFINITE; continue; }
-        float En_s = En, rn_s = rn, Qn_s = Qn, cpart = cs;
+        if (!(fz == 0.f)) { err |= ERR_NONFINITE; continue; }
+        float En_s = En, rn_s = rn, Qn_s = Qn, cpart2 = c2p;
         int sp[3] = {0, 0, 0};
         if (out && G.inflow_face >= 0) {
             const uint32_t gk = pt.gen[k];
@@ -1638,8 +1642,8 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
             rn_s = (float)G.inflow_rho;
             Qn_s = 0.f;
             const float ci2 = gam * gm1 * En_s;
-            cpart = sqrtf(ci2 > 0.f ? ci2 : 0.f);
-            vmax = fmaxf(vmax, sqrtf(vin2));
+            cpart2 = ci2 > 0.f ? ci2 : 0.f;
+            vmax2 = fmaxf(vmax2, vin2);
         } else {
 #pragma unroll
             for (int a = 0; a < D; ++a) {
@@ -1664,11 +1668,11 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
         pt.E[k] = En_s;
         pt.rho[k] = rn_s;
         pt.Q[k] = Qn_s;
-        vmax = fmaxf(vmax, sqrtf(vb2));
-        cmax = fmaxf(cmax, cpart);
+        vmax2 = fmaxf(vmax2, vb2);
+        cmax2 = fmaxf(cmax2, cpart2);
     }
-    vmax = warp_max(vmax);
-    cmax = warp_max(cmax);
+    const float vmax = sqrtf(warp_max(vmax2));
+    const float cmax = sqrtf(warp_max(cmax2));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) err |= __shfl_xor_sync(0xffffffffu, err, o);
     if ((threadIdx.x & 31) == 0) {
