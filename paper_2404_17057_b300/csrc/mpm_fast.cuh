@@ -66,6 +66,41 @@ __device__ __forceinline__ bool axis_known(float x, float lo, float ih, float cb
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// axis_known for two axes at once (the x and y axes of a particle) in packed
+// f32x2 arithmetic, with the same IEEE operations per axis: x - lo as
+// x + (-lo), 1.5 - fx as fx (-1) + 1.5 (one rounding), and 0.75 - (fx - 1)^2
+// as (fx - 1)(1 - fx) + 0.75 (one rounding; 1 - fx is -(fx - 1) exactly).
+template <int P, bool PER>
+__device__ __forceinline__ void axes2_known(float2 x, float2 nlo, float2 ih2, float2 ncb, float n0, float n1,
+                                            float* wa, float* wb, float* dwa, float* dwb)
+{
+    float2 fx = __fadd2_rn(__fmul2_rn(__fadd2_rn(x, nlo), ih2), ncb);
+    if (PER && P == 2) {
+        if (fx.x > 0.5f * n0 + 0.75f) fx.x -= n0;
+        if (fx.y > 0.5f * n1 + 0.75f) fx.y -= n1;
+    }
+    if constexpr (P == 2) {
+        const float2 m1 = f2(-1.f, -1.f), hf = f2(0.5f, 0.5f);
+        const float2 t0 = __ffma2_rn(fx, m1, f2(1.5f, 1.5f));
+        const float2 t1 = __fadd2_rn(fx, m1);
+        const float2 u1 = __ffma2_rn(fx, m1, f2(1.f, 1.f));
+        const float2 t2 = __fadd2_rn(fx, f2(-0.5f, -0.5f));
+        const float2 w0 = __fmul2_rn(__fmul2_rn(hf, t0), t0);
+        const float2 w1 = __ffma2_rn(t1, u1, f2(0.75f, 0.75f));
+        const float2 w2 = __fmul2_rn(__fmul2_rn(hf, t2), t2);
+        wa[0] = w0.x; wa[1] = w1.x; wa[2] = w2.x;
+        wb[0] = w0.y; wb[1] = w1.y; wb[2] = w2.y;
+        dwa[0] = -t0.x; dwa[1] = 2.0f * u1.x; dwa[2] = t2.x;
+        dwb[0] = -t0.y; dwb[1] = 2.0f * u1.y; dwb[2] = t2.y;
+    } else {
+        const float2 u = __ffma2_rn(fx, f2(-1.f, -1.f), f2(1.f, 1.f));
+        wa[0] = u.x; wa[1] = fx.x;
+        wb[0] = u.y; wb[1] = fx.y;
+        dwa[0] = -1.f; dwa[1] = 1.f;
+        dwb[0] = -1.f; dwb[1] = 1.f;
+    }
+}
+
 // Add one node row of a span's contributions into the shared window with the
 // neighbouring spans of the same x-row summed first.  Lane = span x in its
 // row segment of T0 lanes (lx); v[a] = contribution to window node lx + a.
@@ -248,6 +283,29 @@ struct ZcolSums {
     }
 };
 
+// The next particle of a column walk, loaded one particle ahead: the next of
+// the same span, or, after a span's last particle, the first of the next
+// span up the column (have: loaded).  GROUP 0 keeps {x, v, M}, GROUP 1
+// {x, M, rho, E, Q} (u = rho, E, Q).
+struct ZcolNext {
+    float x[3], u[3], M;
+    bool have;
+};
+
+template <int GROUP>
+__device__ __forceinline__ void zcol_load(const Particles<float>& pt, uint32_t k, ZcolNext& N)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) N.x[a] = pt.x[a][k];
+    N.M = pt.M[k];
+    if constexpr (GROUP == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) N.u[a] = pt.v[a][k];
+    } else {
+        N.u[0] = pt.rho[k]; N.u[1] = pt.E[k]; N.u[2] = pt.Q[k];
+    }
+}
+
 // One span of a column: its particles into the sums (layer c in slot c),
 // then the completed layers into the window.  Returns whether it was the
 // column's last span.
@@ -255,7 +313,7 @@ template <int P, bool PER, int GROUP, int TX, int TY, int TZ>
 __device__ __forceinline__ bool zcol_span(const Geom& G, const Particles<float>& pt, const uint32_t* __restrict__ cs,
                                           int64_t kb, const int so[3], const float lo[3], const float nper[3],
                                           float ih, float gm1, float* sm, int lane, int yb, int rpl, int z, int nz,
-                                          ZcolSums<P, GROUP>& S)
+                                          ZcolSums<P, GROUP>& S, ZcolNext& N)
 {
     constexpr int NS = P + 1;
     constexpr bool ST = TX > 0;
@@ -278,29 +336,23 @@ __device__ __forceinline__ bool zcol_span(const Geom& G, const Particles<float>&
     const int s = ((z * T1 + ly) << sh0) + lx;
     const uint32_t b = cs[kb + s], e = cs[kb + s + 1];
     const int base = (z * W1 + ly) * W0 + lx;
+    const int sn = s + T0 * T1;                 // the next span up the column
+    const bool up = z + 1 < nz;
+    const uint32_t nb = up ? cs[kb + sn] : 0u, ne = up ? cs[kb + sn + 1] : 0u;
     const float cb0 = (float)(so[0] + lx - (P == 2 ? 1 : 0));
     const float cb1 = (float)(so[1] + ly - (P == 2 ? 1 : 0));
     const float cb2 = (float)(so[2] + z - (P == 2 ? 1 : 0));
     if constexpr (GROUP == 0) {
-        float nx[3] = {0.f, 0.f, 0.f}, nv[3] = {0.f, 0.f, 0.f}, nM = 0.f;
-        if (b < e) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) { nx[a] = pt.x[a][b]; nv[a] = pt.v[a][b]; }
-            nM = pt.M[b];
-        }
+        if (!N.have && b < e) zcol_load<0>(pt, b, N);
         for (uint32_t k = b; k < e; ++k) {
             float x[3], v[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) { x[a] = nx[a]; v[a] = nv[a]; }
-            const float M = nM;
-            if (k + 1 < e) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) { nx[a] = pt.x[a][k + 1]; nv[a] = pt.v[a][k + 1]; }
-                nM = pt.M[k + 1];
-            }
+            for (int a = 0; a < 3; ++a) { x[a] = N.x[a]; v[a] = N.u[a]; }
+            const float M = N.M;
+            if (k + 1 < e) zcol_load<0>(pt, k + 1, N);
             float w[3][3], dw[3][3];
-            axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
-            axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+            axes2_known<P, PER>(f2(x[0], x[1]), f2(-lo[0], -lo[1]), f2(ih, ih), f2(-cb0, -cb1), nper[0], nper[1],
+                                w[0], w[1], dw[0], dw[1]);
             axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
             float2 c0[NS], c1[NS];
             const float mv0 = M * v[0], mv1 = M * v[1], mv2 = M * v[2];
@@ -326,25 +378,16 @@ __device__ __forceinline__ bool zcol_span(const Geom& G, const Particles<float>&
             }
         }
     } else {
-        float nx[3] = {0.f, 0.f, 0.f}, nM = 0.f, nr = 1.f, nE = 0.f, nQ = 0.f;
-        if (b < e) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) nx[a] = pt.x[a][b];
-            nM = pt.M[b]; nr = pt.rho[b]; nE = pt.E[b]; nQ = pt.Q[b];
-        }
+        if (!N.have && b < e) zcol_load<1>(pt, b, N);
         for (uint32_t k = b; k < e; ++k) {
             float x[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) x[a] = nx[a];
-            const float M = nM, rho = nr, E = nE, Q = nQ;
-            if (k + 1 < e) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) nx[a] = pt.x[a][k + 1];
-                nM = pt.M[k + 1]; nr = pt.rho[k + 1]; nE = pt.E[k + 1]; nQ = pt.Q[k + 1];
-            }
+            for (int a = 0; a < 3; ++a) x[a] = N.x[a];
+            const float M = N.M, rho = N.u[0], E = N.u[1], Q = N.u[2];
+            if (k + 1 < e) zcol_load<1>(pt, k + 1, N);
             float w[3][3], dw[3][3];
-            axis_known<P, PER>(x[0], lo[0], ih, cb0, nper[0], w[0], dw[0]);
-            axis_known<P, PER>(x[1], lo[1], ih, cb1, nper[1], w[1], dw[1]);
+            axes2_known<P, PER>(f2(x[0], x[1]), f2(-lo[0], -lo[1]), f2(ih, ih), f2(-cb0, -cb1), nper[0], nper[1],
+                                w[0], w[1], dw[0], dw[1]);
             axis_known<P, PER>(x[2], lo[2], ih, cb2, nper[2], w[2], dw[2]);
             const float F = fmaf(gm1 * rho, E, Q) * __fdividef(M, rho) * ih;
             float Fx[NS], Fd[NS];
@@ -366,6 +409,10 @@ __device__ __forceinline__ bool zcol_span(const Geom& G, const Particles<float>&
             }
         }
     }
+    // the first particle of the next span up the column, loaded before this
+    // span's layer adds
+    N.have = nb < ne;
+    if (N.have) zcol_load<GROUP>(pt, nb, N);
     // the completed node layers (the lowest, or all three after the column's
     // last span) go into the window in phases: in phase (a, g) lane (lx, ly)
     // adds its sums of the nodes (lx + a, ly + bb) with bb / ystep = g.  Lanes
@@ -429,9 +476,11 @@ __device__ __forceinline__ void p2g_zcol(const Geom& G, const Particles<float>& 
         ZcolSums<P, GROUP> S;
 #pragma unroll
         for (int sl = 0; sl < NS; ++sl) S.clear(sl);
+        ZcolNext N;
+        N.have = false;
         for (int z = 0; z < nz; ++z) {
             if (zcol_span<P, PER, GROUP, TX, TY, TZ>(G, pt, cs, kb, so, lo, nper, ih, gm1, sm, lane, yb, rpl, z, nz,
-                                                    S)) break;
+                                                    S, N)) break;
             // the layers move down; the new top layer starts at zero
 #pragma unroll
             for (int sl = 0; sl + 1 < NS; ++sl) {
