@@ -295,8 +295,13 @@ struct Impl {
         if (e != cudaSuccess) return e;
         if constexpr (kFast3 && D == 3 && P == 2) {
             const int shape = static_tile(G);
-            if (shape == 1) e = allow((const void*)k_g2pd_fast<3, 2, A, 8, 8, 8>, smem(G, 2));
-            if (shape == 2) e = allow((const void*)k_g2pd_fast<3, 2, A, 16, 8, 4>, smem(G, 2));
+            const bool wl = all_walls(G);
+            if (shape == 1)
+                e = allow(wl ? (const void*)k_g2pd_fast<3, 2, A, 8, 8, 8, true> : (const void*)k_g2pd_fast<3, 2, A, 8, 8, 8>,
+                          smem(G, 2));
+            if (shape == 2)
+                e = allow(wl ? (const void*)k_g2pd_fast<3, 2, A, 16, 8, 4, true> : (const void*)k_g2pd_fast<3, 2, A, 16, 8, 4>,
+                          smem(G, 2));
             if (e != cudaSuccess) return e;
         }
         if constexpr (kFast) {
@@ -415,8 +420,13 @@ struct Impl {
             if constexpr (kFast3 && D == 3 && P == 2) {
                 // compile-time tile edges for the common shapes
                 shape = static_tile(G);
-                if (shape == 1)
+                const bool wl = all_walls(G);
+                if (shape == 1 && wl)
+                    k_g2pd_fast<3, 2, A, 8, 8, 8, true><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
+                else if (shape == 1)
                     k_g2pd_fast<3, 2, A, 8, 8, 8><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
+                else if (shape == 2 && wl)
+                    k_g2pd_fast<3, 2, A, 16, 8, 4, true><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
                 else if (shape == 2)
                     k_g2pd_fast<3, 2, A, 16, 8, 4><<<G.ntiles, kG2PDThreads, smem(G, 2), st>>>(G, ts, gr, s->clk, ro);
             }

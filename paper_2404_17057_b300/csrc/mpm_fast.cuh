@@ -1260,24 +1260,71 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
     tile_origin(G, tile, so);
     const float dt = (float)clk->dt_cur;
     const bool bc = window_has_bc(G, gr.mask, so);
-    for (int i = threadIdx.x; i < W; i += blockDim.x) {
-        int idx[3];
-        const int64_t node = slot_node<P, TX, TY>(G, so, i, idx);
-        float f[3] = {0.f, 0.f, 0.f}, m = 0.f;
-        if (node >= 0) {
-            m = gr.m[node];
+    if constexpr (ST) {
+        // compile-time tiles: the window's m (into the first field of s2) and
+        // f (into sA) and the span starts arrive by asynchronous copies, all
+        // of a thread's in flight at once; then each thread applies the BC to
+        // its own nodes and forms f/m in place
+        constexpr int WS = (TX + P) * (TY + P) * (TZ + P), NT = C::kThreads, NI = (WS + NT - 1) / NT;
 #pragma unroll
-            for (int a = 0; a < D; ++a) f[a] = gr.f[a][node];
-            if (bc) node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
-        }
-        const float im = m != 0.f ? __frcp_rn(m) : 0.f;
+        for (int q = 0; q < NI; ++q) {
+            const int i = (int)threadIdx.x + q * NT;
+            if (i < WS) {
+                int idx[3];
+                const int64_t node = slot_node<P, TX, TY>(G, so, i, idx);
+                if (node >= 0) {
+                    cp_async4(s2 + i, gr.m + node);
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            sA[a * W + i] = f[a] * im;
-            s2[a * W + i] = 0.f;
+                    for (int a = 0; a < D; ++a) cp_async4(sA + a * W + i, gr.f[a] + node);
+                } else {
+                    s2[i] = 0.f;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) sA[a * W + i] = 0.f;
+                }
+            }
         }
+        for (int i = threadIdx.x; i <= Tvol; i += blockDim.x) cp_async4(tcs + i, cs + kb + i);
+        cp_async_wait_all();
+#pragma unroll
+        for (int q = 0; q < NI; ++q) {
+            const int i = (int)threadIdx.x + q * NT;
+            if (i < WS) {
+                float f[3] = {0.f, 0.f, 0.f}, m = s2[i];
+#pragma unroll
+                for (int a = 0; a < D; ++a) f[a] = sA[a * W + i];
+                if (bc) {
+                    int idx[3];
+                    const int64_t node = slot_node<P, TX, TY>(G, so, i, idx);
+                    if (node >= 0) node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
+                }
+                const float im = m != 0.f ? __frcp_rn(m) : 0.f;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    sA[a * W + i] = f[a] * im;
+                    s2[a * W + i] = 0.f;
+                }
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < W; i += blockDim.x) {
+            int idx[3];
+            const int64_t node = slot_node<P, TX, TY>(G, so, i, idx);
+            float f[3] = {0.f, 0.f, 0.f}, m = 0.f;
+            if (node >= 0) {
+                m = gr.m[node];
+#pragma unroll
+                for (int a = 0; a < D; ++a) f[a] = gr.f[a][node];
+                if (bc) node_bc<float, D>(G, gr.mask, gr.nrm, node, idx, m, f, 1);
+            }
+            const float im = m != 0.f ? __frcp_rn(m) : 0.f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                sA[a * W + i] = f[a] * im;
+                s2[a * W + i] = 0.f;
+            }
+        }
+        for (int i = threadIdx.x; i <= Tvol; i += blockDim.x) tcs[i] = cs[kb + i];
     }
-    for (int i = threadIdx.x; i <= Tvol; i += blockDim.x) tcs[i] = cs[kb + i];
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < C::kStages; ++q) mbar_init(bar + q, 1);
@@ -1475,7 +1522,9 @@ constexpr int g2pd_blocks() { return D == 3 && !ST ? 4 : 5; }
 
 // A: grid accumulator type (float, or int64 fixed point read back as float).
 // TX, TY, TZ > 0 (3D): the tile edges as compile-time constants.
-template <int D, int P, class A, int TX = 0, int TY = 0, int TZ = 0>
+// WALLS: every face is a wall (no periodic axis, no outflow, no inflow), so
+// the periodic wrap and the outflow / recycling paths drop out.
+template <int D, int P, class A, int TX = 0, int TY = 0, int TZ = 0, bool WALLS = false>
 __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<float>& pt, const Grid<A, float>& gr,
                                                const uint32_t* __restrict__ cs, Clock* clk, const Reorder& ro,
                                                const int tile)
@@ -1561,10 +1610,10 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             float xi;
-            const int c = span_of<float, P>(G, a, x[a], xi);
+            const int c = span_of<float, P, WALLS>(G, a, x[a], xi);
             csp[a] = c;
             weights1d<P>(__fsub_rn(xi, (float)(c - (P == 2 ? 1 : 0))), w[a], dw[a]);
-            l[a] = wrap_span(G, a, c) - so[a];
+            l[a] = wrap_span<WALLS>(G, a, c) - so[a];
             ok = ok && l[a] >= 0 && l[a] < Ta[a];
         }
         if (!ok) { err |= ERR_TILE; continue; }
@@ -1656,9 +1705,9 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
             vb2 = fmaf(vb[a], vb[a], vb2);
             fz = __fadd_rn(fz, __fsub_rn(xn[a], xn[a]));
             float xi;
-            cn[a] = span_of<float, P>(G, a, xn[a], xi);
+            cn[a] = span_of<float, P, WALLS>(G, a, xn[a], xi);
             if ((unsigned)(cn[a] - csp[a] + 1) > 2u) err |= ERR_CFL;    // more than one span
-            if (!G.per[a]) {
+            if (!WALLS && !G.per[a]) {
                 if (xn[a] < (float)G.lo[a] && G.bc[2 * a] == 3) out = true;
                 if (xn[a] >= (float)G.hi[a] && G.bc[2 * a + 1] == 3) out = true;
             }
@@ -1666,7 +1715,7 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
         if (!(fz == 0.f)) { err |= ERR_NONFINITE; continue; }
         float En_s = En, rn_s = rn, Qn_s = Qn, cpart2 = c2p;
         int sp[3] = {0, 0, 0};
-        if (out && G.inflow_face >= 0) {
+        if (!WALLS && out && G.inflow_face >= 0) {
             const uint32_t gk = pt.gen[k];
             uint32_t c[4] = {gk, 0u, pt.id[k], 0u};
             philox4x32_10(c, (uint32_t)G.seed, (uint32_t)(G.seed >> 32));
@@ -1697,7 +1746,7 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 const float lo = (float)G.lo[a], hi = (float)G.hi[a];
-                if (G.per[a]) {
+                if (!WALLS && G.per[a]) {
                     const float L = __fsub_rn(hi, lo);
                     if (xn[a] < lo) xn[a] = __fadd_rn(xn[a], L);
                     else if (xn[a] >= hi) xn[a] = __fsub_rn(xn[a], L);
@@ -1712,8 +1761,8 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
         }
 #pragma unroll
         for (int a = 0; a < D; ++a) pt.x[a][k] = xn[a];
-        pt.key[k] = record_key(G, ro, clk, key_of<float>(G, sp), out && G.inflow_face >= 0, (uint32_t)k, tile, okey,
-                               err);
+        pt.key[k] = record_key(G, ro, clk, key_of<float>(G, sp), !WALLS && out && G.inflow_face >= 0, (uint32_t)k,
+                               tile, okey, err);
         pt.E[k] = En_s;
         pt.rho[k] = rn_s;
         pt.Q[k] = Qn_s;
@@ -1731,12 +1780,20 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
     }
 }
 
-template <int D, int P, class A, int TX = 0, int TY = 0, int TZ = 0>
+template <int D, int P, class A, int TX = 0, int TY = 0, int TZ = 0, bool WALLS = false>
 __global__ void __launch_bounds__(kG2PDThreads, g2pd_blocks<D, (TX > 0)>()) k_g2pd_fast(Geom G, TileState<float> ts,
                                                                          Grid<A, float> gr, Clock* clk, Reorder ro)
 {
     const int t = blockIdx.x;
-    g2pd_fast_tile<D, P, A, TX, TY, TZ>(G, ts.pt, gr, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, ro, t);
+    g2pd_fast_tile<D, P, A, TX, TY, TZ, WALLS>(G, ts.pt, gr, ts.tpar[t] ? ts.cs[1] : ts.cs[0], clk, ro, t);
+}
+
+// Whether every face of the domain is a wall (the WALLS kernels apply).
+__host__ __device__ inline bool all_walls(const Geom& G)
+{
+    for (int a = 0; a < G.dim; ++a)
+        if (G.per[a] || G.bc[2 * a] != 0 || G.bc[2 * a + 1] != 0) return false;
+    return G.inflow_face < 0;
 }
 
 }  // namespace mpm

@@ -271,20 +271,22 @@ struct AxisSup {
 
 // Span of coordinate x along axis a evaluated in the storage precision R with
 // one rounding per operation: xi = (x - lo) * (1/h); c = floor(xi [+ 1/2]).
-template <class R, int P>
+// WALLS: the caller knows that no axis is periodic.
+template <class R, int P, bool WALLS = false>
 __device__ __forceinline__ int span_of(const Geom& G, int a, R x, R& xi)
 {
     typedef Op<R> O;
     xi = O::mul(O::sub(x, (R)G.lo[a]), (R)G.inv_h);
     R s = (P == 2) ? O::add(xi, (R)0.5) : xi;
     int c = (int)O::flr(s);
-    if (!G.per[a]) c = min(max(c, 0), G.S[a] - 1);
+    if (WALLS || !G.per[a]) c = min(max(c, 0), G.S[a] - 1);
     return c;
 }
 
+template <bool WALLS = false>
 __device__ __forceinline__ int wrap_span(const Geom& G, int a, int c)
 {
-    if (!G.per[a]) return c;
+    if (WALLS || !G.per[a]) return c;
     const int n = G.n[a];
     // spans of positions in [lo, hi] and one span beyond wrap by one period
     int r = c >= n ? c - n : (c < 0 ? c + n : c);

@@ -58,6 +58,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
     return false;
 }
 
+// Asynchronous 4-byte global -> shared copy (completes at cp_async_wait_all
+// of the issuing thread).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Block-wide barrier (id 1, all threads of the block) that also ORs a flag;
 // usable from warp-specialised code paths.
 __device__ __forceinline__ int block_bar_or(int pred)
