@@ -651,17 +651,21 @@ template <int D, int P, bool PER, bool COL, int TX = 0, int TY = 0, int TZ = 0>
 __device__ __forceinline__ void p2g_span_tile(const Geom& G, const Particles<float>& pt, const FieldPtrs& out,
                                               const uint32_t* __restrict__ cs, Clock* clk, const int tile)
 {
-    if (!clk->active) return;
     constexpr bool ST = TX > 0;
     static_assert(!ST || (D == 3 && COL), "static tiles: 3D span columns");
     const int64_t kb = tile_cs0(G, tile);
-    if (cs[kb] == cs[kb + (ST ? TX * TY * TZ : G.Tvol)]) return;
+    // compile-time tiles read the run state and the tile's particle range
+    // while they clear their window, and return (uniformly) after that
+    const int active = clk->active;
+    const uint32_t pb = cs[kb], pe = cs[kb + (ST ? TX * TY * TZ : G.Tvol)];
+    if (!ST && (!active || pb == pe)) return;
     extern __shared__ __align__(16) float sm[];
     constexpr int NS = P + 1, NF = 1 + 2 * D, NYZ = (D == 3) ? NS * NS : NS, NN = NYZ * NS;
     const int W = ST ? (TX + P) * (TY + P) * (TZ + P) : G.Wvol, W0 = G.W[0], W1 = G.W[1];
     for (int i = threadIdx.x; i < (NF * W) >> 2; i += blockDim.x)
         reinterpret_cast<float4*>(sm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = ((NF * W) & ~3) + threadIdx.x; i < NF * W; i += blockDim.x) sm[i] = 0.f;
+    if (ST && (!active || pb == pe)) return;
     __syncthreads();
     int so[3];
     tile_origin(G, tile, so);
@@ -1241,10 +1245,13 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
     typedef K2Cfg<D> C;
     constexpr bool ST = TX > 0;
     static_assert(!ST || D == 3, "static tiles: 3D");
-    if (!clk->active) return;
     const int Tvol = ST ? TX * TY * TZ : G.Tvol;
     const int64_t kb = tile_cs0(G, tile);
-    if (cs[kb] == cs[kb + Tvol]) return;
+    // compile-time tiles read the run state and the tile's particle range
+    // while their window copies fly, and return (uniformly) after those
+    const int active = clk->active;
+    const uint32_t pb = cs[kb], pe = cs[kb + Tvol];
+    if (!ST && (!active || pb == pe)) return;
     extern __shared__ __align__(16) float sm[];
     constexpr int NS = P + 1, NYZ = (D == 3) ? NS * NS : NS;
     const int W = ST ? (TX + P) * (TY + P) * (TZ + P) : G.Wvol;
@@ -1288,6 +1295,7 @@ __device__ __forceinline__ void grid_g2p_span_tile(const Geom& G, const Particle
         }
         for (int i = threadIdx.x; i <= Tvol; i += blockDim.x) cp_async4(tcs + i, cs + kb + i);
         cp_async_wait_all();
+        if (!active || pb == pe) return;
 #pragma unroll 1
         for (int q = 0; q < NI; ++q) {
             const int i = (int)threadIdx.x + q * NT;
@@ -1534,10 +1542,12 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
 {
     constexpr bool ST = TX > 0;
     static_assert(!ST || D == 3, "static tiles: 3D");
-    if (!clk->active) return;
+    // compile-time tiles read the run state and the tile's particle range
+    // while their window loads fly, and return (uniformly) after those
+    const int active = clk->active;
     const uint32_t beg = cs[tile_cs0(G, tile)];
     const uint32_t end = cs[tile_cs0(G, tile) + (ST ? TX * TY * TZ : G.Tvol)];
-    if (beg == end) return;
+    if (!ST && (!active || beg == end)) return;
     // per node: 3D {Vb_x, Vb_y, Vb_z, V2_y} + {V2_x, V2_z}; 2D {Vb_x, Vb_y, V2_x, V2_y}
     extern __shared__ __align__(16) float4 sn[];
     constexpr int NS = P + 1;
@@ -1578,6 +1588,7 @@ __device__ __forceinline__ void g2pd_fast_tile(const Geom& G, const Particles<fl
             sn[i] = make_float4(vb[0], vb[1], m2[0] * im, m2[1] * im);
         }
     }
+    if (ST && (!active || beg == end)) return;
     __syncthreads();
     const float gm1 = (float)(G.gamma - 1.0), gam = (float)G.gamma, ih = (float)G.inv_h, hh = (float)G.h;
     const float c0 = (float)G.c0, c1 = (float)G.c1;
