@@ -510,14 +510,17 @@ def main():
 
 def end_to_end(M, p, args):
     """Same metric through the C ABI from host buffers: create, H2D of the
-    initial state (double arrays, page-locked before the timed region), K
-    steps, D2H of the density field (into a page-locked array) and of the
-    FP64 conservation sums."""
+    initial state (page-locked before the timed region; binary32 arrays
+    through mpm_add_particles_f32 for the FP32 modes, which store it in that
+    precision, doubles for FP64), K steps, D2H of the density field (into a
+    page-locked array) and of the FP64 conservation sums."""
     import dataclasses
     import torch
 
+    f32 = args.precision.startswith("fp32")
+
     def pinned(a):
-        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t = torch.empty(a.shape, dtype=torch.float32 if f32 else torch.float64, pin_memory=True)
         t.numpy()[...] = a
         return t
 
@@ -526,7 +529,7 @@ def end_to_end(M, p, args):
     out = torch.empty(p.n_particles, dtype=torch.float64, pin_memory=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim = M.Simulation.from_problem(q)
+    sim = M.Simulation.from_problem(q, f32=f32)
     sim.step(args.steps)
     rho = sim.read("RHO", out=out.numpy())
     cons = sim.conservation()
@@ -534,7 +537,7 @@ def end_to_end(M, p, args):
     sim.close()
     n = p.n_particles
     d = p.cfg["dim"]
-    h2d = n * (2 * d + 3) * 8 + (p.mask.nbytes + p.normals.nbytes if p.mask is not None else 0)
+    h2d = n * (2 * d + 3) * (4 if f32 else 8) + (p.mask.nbytes + p.normals.nbytes if p.mask is not None else 0)
     d2h = rho.nbytes + cons.nbytes
     return {"value": n * args.steps / (t1 - t0), "unit": "particle-steps/s",
             "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,

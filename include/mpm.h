@@ -138,6 +138,14 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out);
 mpm_status mpm_add_particles(mpm_sim* sim, int64_t n, const double* x, const double* v,
                              const double* mass, const double* rho, const double* e);
 
+/* mpm_add_particles with the initial state in binary32 (Sec. 3 step 2),
+ * for callers whose state is already single precision: the same layout,
+ * checks, errors, numbering and ordering, and half the bytes over the host
+ * link.  The FP32 modes store the values as given; MPM_FP64 widens them
+ * exactly, so either call gives the same state for binary32 values. */
+mpm_status mpm_add_particles_f32(mpm_sim* sim, int64_t n, const float* x, const float* v,
+                                 const float* mass, const float* rho, const float* e);
+
 /* Obstacle nodes (Sec. 2.2, eqs. normali1-2, sdf): node_mask[i] != 0 marks
  * node i; normals is dim x nodes (outward unit normals, used on marked nodes
  * only).  Both host arrays of the full node count.  When the -x or +x face

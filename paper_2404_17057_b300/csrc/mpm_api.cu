@@ -172,6 +172,7 @@ struct Vtbl {
     void (*tile_counts)(mpm_sim* s, uint32_t* counts, cudaStream_t st);
     void (*spread)(mpm_sim* s, const uint32_t* cc, cudaStream_t st);
     void (*from_double)(const double* in, void* out, int64_t n, cudaStream_t st);
+    void (*from_float)(const float* in, void* out, int64_t n, cudaStream_t st);
     cudaError_t (*set_smem)(const Geom& G);
     size_t (*smem)(const Geom& G, int kernel);
     void (*reorder)(mpm_sim* s, cudaStream_t st);
@@ -616,6 +617,10 @@ struct Impl {
     {
         if (n > 0) k_from_double<R><<<nblk(n), kThreads, 0, st>>>(in, (R*)out, n);
     }
+    static void from_float(const float* in, void* out, int64_t n, cudaStream_t st)
+    {
+        if (n > 0) k_from_float<R><<<nblk(n), kThreads, 0, st>>>(in, (R*)out, n);
+    }
     static void compact(mpm_sim* s, int f, int a, void* out, cudaStream_t st)
     {
         const TileState<R> ts = tstate<R>(s, s->cur);
@@ -652,7 +657,7 @@ const Vtbl* vtbl_of()
     typedef Impl<D, P, R, A> I;
     static const Vtbl v = {I::step_kernels, I::keys,    I::gather,          I::cfl_init,
                            I::cons,         I::compact, I::tile_counts,     I::spread,
-                           I::from_double,  I::set_smem, I::smem,           I::reorder,
+                           I::from_double,  I::from_float, I::set_smem, I::smem, I::reorder,
                            sizeof(BatchProb<R, A>), I::bdesc_fill, I::blaunch, I::bset_smem};
     return &v;
 }
@@ -1093,8 +1098,12 @@ mpm_status mpm_create(const mpm_config* cfg, mpm_sim** out)
     return MPM_OK;
 }
 
-mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const double* v, const double* mass,
-                             const double* rho, const double* e)
+namespace {
+
+// mpm_add_particles and mpm_add_particles_f32: the host arrays hold doubles,
+// or floats when f32.
+mpm_status add_particles(mpm_sim* s, int64_t n, const void* x, const void* v, const void* mass, const void* rho,
+                         const void* e, bool f32)
 {
     if (!s) return fail(nullptr, MPM_EINVAL, "sim is NULL");
     if (s->batch) return fail(s, MPM_ESTATE, "the simulation is a member of a batch");
@@ -1131,10 +1140,11 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
         s->vt->compact(s, 7, 0, nb[0].gen, S);
         CK(cudaGetLastError(), "compact");
     }
-    // stage the new doubles on the device, check them there and convert them
+    // stage the new values on the device, check them there and convert them
     // to the storage precision; stream order keeps the staging buffer safe to
     // reuse (each copy into it follows the previous array's kernels)
-    double* stage = (double*)dalloc(s, (size_t)n * sizeof(double));
+    const size_t es = f32 ? sizeof(float) : sizeof(double);
+    void* stage = dalloc(s, (size_t)n * es);
     unsigned* bad = (unsigned*)dalloc(s, sizeof(unsigned));
     if (!stage || !bad) {
         dfree(s, stage);
@@ -1145,23 +1155,29 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
     enum { kBadState = 1, kBadPlace = 2, kBadSeam = 4 };
     // axis >= 0: a position component (inside the domain, below hi on a
     // periodic axis); otherwise a value checked by `mode` that sets `bit`
-    auto up = [&](const double* src, void* dst, int mode, unsigned bit, int axis) -> cudaError_t {
-        cudaError_t r = cudaMemcpyAsync(stage, src, n * sizeof(double), cudaMemcpyHostToDevice, S);
+    auto check = [&](int mode, double lo, double hi, unsigned bit) {
+        if (f32) k_check_values<<<nblk(n), kThreads, 0, S>>>((const float*)stage, n, mode, lo, hi, bit, bad);
+        else k_check_values<<<nblk(n), kThreads, 0, S>>>((const double*)stage, n, mode, lo, hi, bit, bad);
+    };
+    auto up = [&](const void* src, void* dst, int mode, unsigned bit, int axis) -> cudaError_t {
+        cudaError_t r = cudaMemcpyAsync(stage, src, n * es, cudaMemcpyHostToDevice, S);
         if (r != cudaSuccess) return r;
         if (axis < 0) {
-            k_check_values<<<nblk(n), kThreads, 0, S>>>(stage, n, mode, 0.0, 0.0, bit, bad);
+            check(mode, 0.0, 0.0, bit);
         } else {
-            k_check_values<<<nblk(n), kThreads, 0, S>>>(stage, n, 2, G.lo[axis], G.hi[axis], kBadPlace, bad);
-            if (G.per[axis])
-                k_check_values<<<nblk(n), kThreads, 0, S>>>(stage, n, 3, G.lo[axis], G.hi[axis], kBadSeam, bad);
+            check(2, G.lo[axis], G.hi[axis], kBadPlace);
+            if (G.per[axis]) check(3, G.lo[axis], G.hi[axis], kBadSeam);
         }
-        s->vt->from_double(stage, (char*)dst + s->np * rs, n, S);
+        if (f32) s->vt->from_float((const float*)stage, (char*)dst + s->np * rs, n, S);
+        else s->vt->from_double((const double*)stage, (char*)dst + s->np * rs, n, S);
         return cudaGetLastError();
     };
+    // component a of a dim x n SoA host array
+    auto comp = [&](const void* p, int a) { return (const void*)((const char*)p + (size_t)a * n * es); };
     cudaError_t ue = cudaMemsetAsync(bad, 0, sizeof(unsigned), S);
     for (int a = 0; a < d && ue == cudaSuccess; ++a) {
-        ue = up(x + a * n, nb[0].x[a], 2, kBadPlace, a);
-        if (ue == cudaSuccess) ue = up(v + a * n, nb[0].v[a], 0, kBadPlace, -1);
+        ue = up(comp(x, a), nb[0].x[a], 2, kBadPlace, a);
+        if (ue == cudaSuccess) ue = up(comp(v, a), nb[0].v[a], 0, kBadPlace, -1);
     }
     if (ue == cudaSuccess) ue = up(mass, nb[0].M, 1, kBadState, -1);
     if (ue == cudaSuccess) ue = up(rho, nb[0].rho, 1, kBadState, -1);
@@ -1232,6 +1248,20 @@ mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const doubl
     CK(le, "launch");
     CK(se, "synchronize");
     return MPM_OK;
+}
+
+}  // namespace
+
+mpm_status mpm_add_particles(mpm_sim* s, int64_t n, const double* x, const double* v, const double* mass,
+                             const double* rho, const double* e)
+{
+    return add_particles(s, n, x, v, mass, rho, e, false);
+}
+
+mpm_status mpm_add_particles_f32(mpm_sim* s, int64_t n, const float* x, const float* v, const float* mass,
+                                 const float* rho, const float* e)
+{
+    return add_particles(s, n, x, v, mass, rho, e, true);
 }
 
 mpm_status mpm_set_obstacle_mask(mpm_sim* s, const uint8_t* mask, const double* normals)

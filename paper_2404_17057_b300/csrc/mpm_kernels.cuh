@@ -1154,9 +1154,16 @@ __global__ void __launch_bounds__(kConsThreads) k_cons_final(const double* parti
         for (int i = 0; i < 5; ++i) out[i] = sh[i][0];
 }
 
-// Convert host-side doubles to the storage precision.
+// Convert host-side doubles (or floats) to the storage precision.
 template <class R>
 __global__ void k_from_double(const double* in, R* out, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (R)in[i];
+}
+
+template <class R>
+__global__ void k_from_float(const float* in, R* out, int64_t n)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (R)in[i];
@@ -1178,14 +1185,15 @@ __global__ void k_pressure(const R* rho, const R* E, R gm1, R* out, int64_t n)
     if (i < n) out[i] = Op<R>::mul(Op<R>::mul(gm1, rho[i]), E[i]);
 }
 
-// Checks of uploaded particle values; sets `bit` in *bad when one fails.
+// Checks of uploaded particle values (binary64 or binary32, compared in
+// binary64, exactly); sets `bit` in *bad when one fails.
 // mode 0: finite; 1: finite and > 0; 2: lo <= v <= hi; 3: lo <= v < hi.
-__global__ void k_check_values(const double* in, int64_t n, int mode, double lo, double hi, unsigned bit,
-                               unsigned* bad)
+template <class T>
+__global__ void k_check_values(const T* in, int64_t n, int mode, double lo, double hi, unsigned bit, unsigned* bad)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double v = in[i];
+    const double v = (double)in[i];
     bool ok;
     switch (mode) {
     case 0: ok = isfinite(v); break;

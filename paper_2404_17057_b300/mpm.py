@@ -25,7 +25,7 @@ FIELDS = {"X": 0, "V": 1, "M": 2, "RHO": 3, "E": 4, "P": 5, "Q": 6, "ID": 7, "KE
 STATUS = {0: "MPM_OK", 1: "MPM_EINVAL", 2: "MPM_ENOMEM", 3: "MPM_ECUDA", 4: "MPM_ESTATE",
           5: "MPM_ENONFINITE", 6: "MPM_ETIMEOUT", 7: "MPM_EUNSUPPORTED", 8: "MPM_ECFL"}
 
-EXPORTS = ["mpm_create", "mpm_add_particles", "mpm_set_obstacle_mask", "mpm_set_obstacle_profile",
+EXPORTS = ["mpm_create", "mpm_add_particles", "mpm_add_particles_f32", "mpm_set_obstacle_mask", "mpm_set_obstacle_profile",
            "mpm_cfl_dt", "mpm_step", "mpm_step_async", "mpm_sync", "mpm_read_state", "mpm_read_grid_fixed",
            "mpm_field_size", "mpm_conservation", "mpm_sizes", "mpm_profile", "mpm_profile_read", "mpm_stream",
            "mpm_last_error", "mpm_destroy", "mpm_sort_keys_static", "mpm_check_fixed_rounding",
@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH):
     P, vp, i64, d = C.POINTER, C.c_void_p, C.c_int64, C.c_double
     L.mpm_create.argtypes = [P(mpm_config), P(vp)]
     L.mpm_add_particles.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    L.mpm_add_particles_f32.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     L.mpm_set_obstacle_mask.argtypes = [vp, vp, vp]
     L.mpm_set_obstacle_profile.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     L.mpm_cfl_dt.argtypes = [vp, P(d)]
@@ -206,6 +207,13 @@ def mpm_add_particles(h, x, v, mass, rho, e):
     v = np.ascontiguousarray(v, dtype=np.float64)
     mass, rho, e = (np.ascontiguousarray(a, dtype=np.float64) for a in (mass, rho, e))
     _check(load().mpm_add_particles(h, int(mass.shape[0]), _ptr(x), _ptr(v), _ptr(mass), _ptr(rho), _ptr(e)), h)
+
+
+def mpm_add_particles_f32(h, x, v, mass, rho, e):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    mass, rho, e = (np.ascontiguousarray(a, dtype=np.float32) for a in (mass, rho, e))
+    _check(load().mpm_add_particles_f32(h, int(mass.shape[0]), _ptr(x), _ptr(v), _ptr(mass), _ptr(rho), _ptr(e)), h)
 
 
 def mpm_set_obstacle_mask(h, mask, normals):
@@ -383,9 +391,13 @@ class Simulation:
         self._h, self._keep = mpm_create(cfg, stream=stream, torch_memory=torch_memory)
 
     @classmethod
-    def from_problem(cls, prob, **kw):
+    def from_problem(cls, prob, f32=False, **kw):
+        """f32: upload the initial state as binary32 (mpm_add_particles_f32)."""
         s = cls(prob.cfg, **kw)
-        s.add_particles(prob.x, prob.v, prob.mass, prob.rho, prob.e)
+        if f32:
+            s.add_particles_f32(prob.x, prob.v, prob.mass, prob.rho, prob.e)
+        else:
+            s.add_particles(prob.x, prob.v, prob.mass, prob.rho, prob.e)
         if prob.mask is not None:
             s.set_obstacle_mask(prob.mask, prob.normals)
         if getattr(prob, "profile", None):
@@ -398,6 +410,9 @@ class Simulation:
 
     def add_particles(self, x, v, mass, rho, e):
         mpm_add_particles(self._h, x, v, mass, rho, e)
+
+    def add_particles_f32(self, x, v, mass, rho, e):
+        mpm_add_particles_f32(self._h, x, v, mass, rho, e)
 
     def set_obstacle_mask(self, mask, normals):
         mpm_set_obstacle_mask(self._h, mask, normals)
