@@ -182,3 +182,26 @@ def test_cylinder_bow_shock_standoff_on_the_gpu():
     s.close()
     assert abs(np.mean(vals) / ref - 1.0) < 0.2, vals
     assert np.std(vals) < 0.1, vals        # settled
+
+
+def test_blast_256_twenty_steps_keep_mass_and_symmetry():
+    """The 256^3 blast in the benchmark's launch configuration (8x8x8 tiles,
+    FP32) for 20 CFL steps, checked by properties that hold at any size.
+    Particle masses never change, and 2^27 equal binary32 masses sum exactly
+    in binary64 in any order, so the FP64 mass sum stays N M bit for bit.
+    The deposit and the walls are symmetric about the centre, so the total
+    momentum stays zero up to the rounding of the float-atomic sums: below
+    1e-5 of sum M |V|."""
+    p = f32(I.blast(n=256, tile=[8, 8, 8]))
+    g = M.Simulation.from_problem(p)
+    m0 = g.conservation()[0]
+    assert m0 == p.mass.shape[0] * p.mass[0]
+    g.step(20)
+    c = g.conservation()
+    assert c[0] == m0
+    mass, v = g.read("M"), g.read("V")
+    scale = float((mass * np.sqrt((v ** 2).sum(axis=0))).sum())
+    drift = np.abs(c[2:5]).max() / scale
+    print("momentum / sum M|V| after 20 steps:", drift)
+    assert scale > 0 and drift <= 1e-5, (c, scale)
+    g.close()
